@@ -1,0 +1,436 @@
+"""Benchmark of the batched, graph-captured FP64 RK4 level step.
+
+Default workload: one periodic 256^3 box, variable c2 (8 seeded bumps),
+Gaussian pulse, dt = 0.25 h; one benchmark step = 100 RK4 steps (the
+headline single-box workload).  Metric: grid-point RK4 updates per second
+(interior points x RK4 steps / s).  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (no data-path collective); timing is the maximum
+over ranks and `value` counts the updates of all ranks (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 grid-point RK4 updates/s"
+UNIT = "updates/s"
+RK4_STEPS_PER_BENCH_STEP = 100
+N_EDGE = 256
+# algorithmic bytes per interior point per RK4 step of the nested stage form:
+# stage 1 reads y.u (stencil), y.pi, c2 and writes w.u, w.pi (5 doubles);
+# stages 2-4 read w.u (stencil), w.pi, y.u, y.pi, c2 and write 2 (7 doubles)
+BYTES_PER_POINT_STEP = 8 * (5 + 7 + 7 + 7)
+BYTES_PER_POINT_STAGE = BYTES_PER_POINT_STEP / 4
+# FP64 pipe instructions per point per stage (FP64 form): 10 adds + 2 FMAs
+# for the sum, 1 multiply by c2, 2 update FMAs
+FP64_OPS_PER_POINT_STAGE = {"fp64": 15, "fixed": 3}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--arith", choices=["fixed", "fp64"], default="fixed")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the uneven-level, ensemble and adjoint measurements")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.cuh", "descriptors.hpp", "launch.hpp"):
+        with open(os.path.join(ROOT, "paper_1308_1343_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_hash, workload):
+    """DRAM bytes per launch of the stage kernel from the committed ncu
+    summary, or None if it was taken on another version of the kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+            if kv.get("kernel") == kernel_hash and kv.get("workload") == workload:
+                return float(kv["bytes_per_launch"])
+    except OSError:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+
+def _oracle_rate(inst, nsteps):
+    from oracle import oracle
+    cores = len(os.sched_getaffinity(0))
+    used = oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    oracle.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, nsteps)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    n = inst.u.size
+    return n * nsteps / dt, used, dt
+
+
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    from paper_1308_1343_gb300 import workloads as W
+    inst = W.single_box(N_EDGE, seed=2)
+    for _ in range(a.warmup):
+        _oracle_rate(inst, 1)
+    rates, times = [], []
+    used = 1
+    for _ in range(a.steps):
+        r, used, dt = _oracle_rate(inst, 1)
+        rates.append(r)
+        times.append(dt)
+    total_t = sum(times)
+    value = inst.u.size * len(times) / total_t
+    sample = "1 RK4 step of the 256^3 workload per benchmark step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * total_t / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "periodic box 256^3, variable c2, Gaussian pulse, RK4 dt=0.25h",
+                   "points": inst.u.size, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def _time_steps(torch, lev, u, pi, c2, dt, nsteps, mode, reps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        lev.rk4_step(u, pi, c2, dt, nsteps, mode, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lev.sync(stream)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _extras(torch, W, B, Level, arith, stream):
+    out = {}
+    # uneven 64-box level: batched graph vs per-box launches, 50 RK4 steps
+    inst = W.uneven_level()
+    lev = Level.from_instances([inst])
+    lev.set_arith(arith)
+    u, pi = lev.to_device([inst.u]), lev.to_device([inst.pi])
+    c2 = lev.to_device([inst.c2], fill=1.0)
+    n = inst.u.size
+    res = {}
+    for name, mode in (("graph", B.SC_MODE_GRAPH), ("per_box", B.SC_MODE_PER_BOX)):
+        _time_steps(torch, lev, u, pi, c2, inst.dt, 5, mode, 1, stream)
+        t = _time_steps(torch, lev, u, pi, c2, inst.dt, 50, mode, 1, stream)
+        res[name] = n * 50 / t
+    lev.rk4_step(u, pi, c2, inst.dt, 10, B.SC_MODE_TIMED, stream=stream)
+    sm, sl, gm, gl = lev.kernel_times()
+    out["uneven_level"] = {
+        "workload": "512x512x256 periodic domain, 64 bisected boxes, 50 RK4 steps",
+        "boxes": len(inst.boxes), "points": n,
+        "graph_updates_per_s": res["graph"], "per_box_updates_per_s": res["per_box"],
+        "stage_kernel_gbs": BYTES_PER_POINT_STAGE * n * sl / (sm * 1e-3) / 1e9 if sm else None,
+    }
+    del lev, u, pi, c2
+    torch.cuda.empty_cache()
+
+    # ensemble: 256 independent periodic cubes of edge 24..96, 100 RK4 steps
+    insts = W.ensemble()
+    lev = Level.from_instances(insts)
+    lev.set_arith(arith)
+    u = lev.to_device([i.u for i in insts])
+    pi = lev.to_device([i.pi for i in insts])
+    c2 = lev.to_device([i.c2 for i in insts], fill=1.0)
+    dts = [i.dt for i in insts]
+    n = sum(i.u.size for i in insts)
+    lev.autotune(seed=5, budget_ms=3000.0, abort_factor=2.0,
+                 cache_path=os.path.join(ROOT, "paper_1308_1343_gb300", "_build", "tune_cache.txt"), stream=stream)
+    _time_steps(torch, lev, u, pi, c2, dts, 5, B.SC_MODE_GRAPH, 1, stream)
+    t = _time_steps(torch, lev, u, pi, c2, dts, 100, B.SC_MODE_GRAPH, 1, stream)
+    out["ensemble"] = {"workload": "256 periodic cubes, edges 24..96, own c2 and pulse, "
+                                   "100 RK4 steps, autotuned tiles",
+                       "points": n, "graph_updates_per_s": n * 100 / t}
+    del lev, u, pi, c2
+    torch.cuda.empty_cache()
+
+    # adjoint / forward ratio on the 128^3, 200-step differentiation workload
+    inst = W.gradient_problem(128, 4)
+    lev = Level.from_instances([inst])
+    lev.set_arith(arith)
+    u0, pi0 = lev.to_device([inst.u]), lev.to_device([inst.pi])
+    c2 = lev.to_device([inst.c2], fill=1.0)
+    u = u0.clone()
+    pi = pi0.clone()
+    _time_steps(torch, lev, u, pi, c2, inst.dt, 20, B.SC_MODE_GRAPH, 1, stream)
+    u.copy_(u0)
+    pi.copy_(pi0)
+    t_fwd = _time_steps(torch, lev, u, pi, c2, inst.dt, 200, B.SC_MODE_GRAPH, 1, stream)
+    uT = torch.empty_like(u0)
+    seed = torch.empty_like(u0)
+    g = [torch.empty_like(u0) for _ in range(3)]
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lev.forward_tape(u0, pi0, c2, inst.dt, 200, 20, uT, None, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lev.misfit(uT, u0, seed, stream=stream)
+        lev.backward_tape(c2, seed, None, g[0], g[1], g[2], stream=stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    lev.sync(stream)
+    out["adjoint"] = {"workload": "128^3 periodic box, 200 RK4 steps, checkpoints every 20",
+                      "t_forward_s": t_fwd, "t_forward_tape_s": t1 - t0,
+                      "t_backward_s": t2 - t1, "ratio_backward_over_forward": (t2 - t1) / t_fwd,
+                      "ratio_total_over_forward": (t2 - t0) / t_fwd}
+    return out
+
+
+def run_ours(a, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_1308_1343_gb300 import binding as B
+    from paper_1308_1343_gb300 import build as BUILD
+    from paper_1308_1343_gb300 import workloads as W
+    from paper_1308_1343_gb300.level import Level
+
+    torch.cuda.set_device(local)
+    BUILD.build()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    arith = B.SC_ARITH_FIXED if a.arith == "fixed" else B.SC_ARITH_FP64
+    stream = torch.cuda.current_stream()
+    inst = W.single_box(N_EDGE, seed=2)
+    npts = inst.u.size
+    lev = Level.from_instances([inst])
+    lev.set_arith(arith)
+    u0 = lev.to_device([inst.u])
+    pi0 = lev.to_device([inst.pi])
+    c2 = lev.to_device([inst.c2], fill=1.0)
+    u, pi = u0.clone(), pi0.clone()
+    nsub = RK4_STEPS_PER_BENCH_STEP
+
+    for _ in range(a.warmup):
+        lev.rk4_step(u, pi, c2, inst.dt, nsub, B.SC_MODE_GRAPH, stream=stream)
+    lev.sync(stream)
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = "GPU-" + str(getattr(props, "uuid", "")) if getattr(props, "uuid", None) else str(local)
+    clocks = Clocks(gpu_id)
+    launches0 = lev.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        lev.rk4_step(u, pi, c2, inst.dt, nsub, B.SC_MODE_GRAPH, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = e0.elapsed_time(e1) / 1e3
+    clk = clocks.stop()
+    lev.sync(stream)
+    launches = lev.launch_count() - launches0
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    value = npts * nsub * a.steps * ws / t
+
+    # dominant kernel: the stage kernel, timed per launch with CUDA events
+    lev.rk4_step(u, pi, c2, inst.dt, nsub, B.SC_MODE_TIMED, stream=stream)
+    stage_ms, stage_n, gather_ms, gather_n = lev.kernel_times()
+    lev.sync(stream)
+    avg_s = stage_ms / stage_n * 1e-3
+    achieved = BYTES_PER_POINT_STAGE * npts / avg_s / 1e9
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    khash = _kernel_source_hash()
+    traffic = _traffic(khash, "single256")
+    fp64_peak_tflops = None
+    ops = FP64_OPS_PER_POINT_STAGE[a.arith]
+    fp64_achieved = 2 * ops * npts / avg_s / 1e12  # FMA = 2 flops upper estimate
+
+    # end to end through the C ABI with pinned host buffers
+    hu = torch.from_numpy(lev.scatter([inst.u])).pin_memory()
+    hp = torch.from_numpy(lev.scatter([inst.pi])).pin_memory()
+    hc = torch.from_numpy(lev.scatter([inst.c2], fill=1.0)).pin_memory()
+    ou = torch.empty_like(hu).pin_memory()
+    op = torch.empty_like(hp).pin_memory()
+    hun, hpn, hcn, oun, opn = (x.numpy() for x in (hu, hp, hc, ou, op))
+    lev.rk4_step_host(hun, hpn, hcn, inst.dt, nsub, oun, opn, stream=stream)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        lev.rk4_step_host(hun, hpn, hcn, inst.dt, nsub, oun, opn, stream=stream)
+    te2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([te2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te2e = tt.item()
+    fbytes = lev.field_size * 8
+    e2e = {"value": npts * nsub * a.steps * ws / te2e, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * fbytes, "d2h_bytes_per_step": 2 * fbytes}
+
+    extras = {}
+    if not a.no_extras and rank == 0:
+        del hu, hp, hc, ou, op
+        extras = _extras(torch, W, B, Level, arith, stream)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu:
+        r, used, dt = _oracle_rate(inst, 3)
+        cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": "3 RK4 steps of the same 256^3 workload (%.1f s)" % dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "periodic box 256^3, variable c2 (8 seeded bumps), "
+                                   "Gaussian pulse, RK4 dt=0.25h, 100 RK4 steps per step",
+                       "points": npts, "rk4_steps_per_step": nsub,
+                       "arith": a.arith, "mode": "batched persistent launch, CUDA graph per "
+                                                  "RK4 step",
+                       "l2": "inputs larger than L2 (fields 7 x %d MB)" % (fbytes >> 20),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": "fwd_stage_kernel",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm if hbm else None, "traffic": traffic,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                         "bytes_per_launch": BYTES_PER_POINT_STAGE * npts,
+                         "launches": stage_n, "avg_launch_ms": avg_s * 1e3,
+                         "gather_avg_launch_ms": gather_ms / max(gather_n, 1),
+                         "fp64_tflops_est": fp64_achieved,
+                         "hbm_fraction_of_nominal_7900": achieved / 7900.0,
+                         "kernel_hash": khash},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    ws, rank, local = _dist()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+        return
+    run_ours(a, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

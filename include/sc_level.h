@@ -1,0 +1,271 @@
+/*
+ * sc_level.h -- C ABI of the GB300 stencil / RK4 level library
+ * (libsc_level.so).
+ *
+ * A *level* is a set of non-overlapping boxes on a uniform grid whose points
+ * are x0 + n*h with integer n (arXiv 1308.1343, Sec. 2, "Efficient Bounding
+ * Box Algebra": bbox / bboxset).  Boxes belong to *domains*; the boxes of a
+ * domain tile it exactly.  Each box stores its interior points plus ghost
+ * zones of width 2, and the ghost exchange between boxes (periodic images
+ * included) is the communication schedule derived from bboxset intersections
+ * (Sec. 2, list of operations built on the set algebra).
+ *
+ * The library evolves the first-order-in-time scalar wave equation
+ *     du/dt = pi,   dpi/dt = c2(x) * (L u)
+ * with L the 4th-order centred Laplacian
+ *     (L u)_i = sum_d ( -u_{i-2e_d} + 16 u_{i-e_d} - 30 u_i + 16 u_{i+e_d}
+ *                       - u_{i+2e_d} ) / (12 h^2)
+ * (the centred-difference idiom on padded arrays of Sec. 4.3, "Iterators"),
+ * by classic fourth-order Runge-Kutta, and differentiates it (adjoint).
+ * All arithmetic is FP64 on the GPU; the traversal follows Sec. 3's loop
+ * decomposition (tiles, then points within tiles) and its run-time tuning.
+ *
+ * Conventions for every function:
+ *  - Return value: SC_OK (0) or a negative SC_E* code; the matching message
+ *    is available from sc_last_error() on the calling thread.  No function
+ *    aborts the process, and no kernel traps: device-side problems set a
+ *    device error word that the next synchronising call reports as
+ *    SC_EDEVICE.
+ *  - Field buffers are caller-owned DEVICE pointers (e.g. torch tensors) of
+ *    sc_level_field_size() doubles, 16-byte aligned, in the level layout
+ *    below.  The library owns the level object and all of its scratch memory
+ *    (stage arrays, checkpoints, work lists, CUDA graphs).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Work is enqueued asynchronously unless stated.
+ *
+ * Level layout (all boxes of all domains in one buffer, box-major):
+ *  - Box b with interior extent (nx, ny, nz) is stored as a padded box of
+ *    (nx+4) x (ny+4) x (nz+4) points, x fastest, with row pitch
+ *    py = roundup(nx+4, 16) doubles and plane pitch pz = py*(ny+4).
+ *  - The element index of grid point p of box b is
+ *        offset_b + (p.x-lo.x) + (p.y-lo.y)*py + (p.z-lo.z)*pz
+ *    for lo-2 <= p < hi+2 on each axis; offset_b (the interior corner lo)
+ *    is a multiple of 16, so every interior row starts on a 128-byte line.
+ *  - Ghost points are the star-shaped shell: points within 2 of a face
+ *    along exactly one axis.  Edge and corner points of the padded box and
+ *    row padding are never read or written by the library.
+ */
+#ifndef SC_LEVEL_H
+#define SC_LEVEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SC_OK 0
+#define SC_EINVAL (-1)   /* bad argument: boxes overlap / do not tile a domain,
+                            ghost != 2, misaligned or NULL pointer, bad size */
+#define SC_ENOMEM (-2)   /* host or device allocation failed               */
+#define SC_ECUDA (-3)    /* a CUDA runtime call failed                      */
+#define SC_EDEVICE (-4)  /* a kernel set the device error word (e.g. a
+                            non-finite value reached the fixed-point path)  */
+#define SC_ENOTSUP (-5)  /* valid request this build does not support        */
+
+/* ---- arithmetic of the Laplacian sum ----------------------------------- */
+/* SC_ARITH_FP64:  the 13-term sum is evaluated with FP64 adds and FMAs.
+ * SC_ARITH_FIXED: each input is scaled by 2^S (S from the domain-wide
+ *   maximum exponent of the field) and rounded to a 64-bit integer; the
+ *   integer-weighted sum is then exact and is rounded once to FP64.  The
+ *   per-input rounding is below 2^-55 of the domain's maximum |value|, so
+ *   the error in the max norm is smaller than the FP64 sum's.  Non-finite
+ *   inputs set the device error word.  The RK updates are FP64 FMAs in
+ *   both modes. */
+#define SC_ARITH_FP64 0
+#define SC_ARITH_FIXED 1
+
+/* ---- traversal mode of sc_level_rk4_step -------------------------------- */
+#define SC_MODE_GRAPH 0    /* one batched launch per kernel over the whole
+                              level's work list, a CUDA graph per RK4 step  */
+#define SC_MODE_PER_BOX 1  /* one launch per box per kernel, no graph       */
+#define SC_MODE_BATCHED 2  /* batched launches without the graph            */
+#define SC_MODE_TIMED 3    /* batched launches, each stage and gather kernel
+                              bracketed by CUDA events on the stream (see
+                              sc_level_kernel_times); for measurement       */
+
+typedef struct sc_box {
+    int64_t lo[3], hi[3]; /* half-open [lo, hi) in the level's index space */
+    int32_t domain;       /* index into the domain array                    */
+    int32_t reserved;     /* must be 0                                      */
+} sc_box;
+
+typedef struct sc_domain {
+    int64_t lo[3], hi[3]; /* half-open extent of the domain                 */
+    double h;             /* grid spacing (same on all axes)                */
+    uint32_t periodic;    /* bit d set: periodic along axis d (x=1,y=2,z=4) */
+    uint32_t reserved;    /* must be 0                                      */
+} sc_domain;
+
+/* One rectangular ghost copy: for every offset o in [0, ext),
+ * dst_box(dst_lo + o) = src_box(src_lo + o), coordinates in the level's
+ * index space (dst points are ghosts of dst_box, src points interior points
+ * of src_box, equal to the ghost points modulo the periodic domain). */
+typedef struct sc_copy {
+    int32_t src_box, dst_box;
+    int64_t src_lo[3], dst_lo[3], ext[3];
+} sc_copy;
+
+typedef struct sc_level sc_level;
+
+/* Kernel configuration of one box-size class (chosen by sc_level_autotune or
+ * set explicitly).  tile_x, tile_y: points per CTA tile in x and y
+ * (tile_x/2 * tile_y == threads per CTA, see sc_level_set_tuning); tile_z:
+ * depth of the z-run one work item marches through. */
+typedef struct sc_tile {
+    int32_t tile_x, tile_y, tile_z, reserved;
+} sc_tile;
+
+/* ---- level lifetime ----------------------------------------------------- */
+
+/* Build a level from boxes and domains (host only: validates the level with
+ * the bboxset algebra and builds the exchange lists; device state is created
+ * on the first call that takes a stream).  ghost must be 2.  Every box must
+ * lie in its domain, have edges >= 2, and the boxes of each domain must tile
+ * it exactly.  On success *out owns the level (free with sc_level_destroy).
+ * Errors: SC_EINVAL (message names the offending box), SC_ENOMEM. */
+int sc_level_create(const sc_box* boxes, int32_t nboxes, const sc_domain* doms,
+                    int32_t ndoms, int32_t ghost, sc_level** out);
+
+/* Free the level and all library-owned device memory.  Waits for the
+ * device to finish work on the level.  NULL is ignored. */
+void sc_level_destroy(sc_level* level);
+
+/* ---- layout queries (host only) --------------------------------------- */
+
+/* Number of doubles in one field buffer of this level. */
+int sc_level_field_size(const sc_level* level, int64_t* n_doubles);
+
+/* Layout of box `box`: offset = element index of the interior corner lo,
+ * dims = interior extent (nx, ny, nz), pitch = (1, py, pz) in doubles. */
+int sc_level_box_layout(const sc_level* level, int32_t box, int64_t* offset,
+                        int64_t dims[3], int64_t pitch[3]);
+
+int sc_level_num_boxes(const sc_level* level, int32_t* nboxes);
+
+/* Copy the exchange list (all boxes) into out[0..cap); *n receives the total
+ * count (call with cap = 0 to size the buffer).  Order: by destination box,
+ * then by the order the bboxset sweep emits the rectangles. */
+int sc_level_exchange_list(const sc_level* level, sc_copy* out, int64_t cap,
+                           int64_t* n);
+
+/* ---- configuration ----------------------------------------------------- */
+
+/* Select the Laplacian arithmetic (SC_ARITH_*) for all later calls. */
+int sc_level_set_arith(sc_level* level, int32_t arith);
+
+/* Set the tile of one size class (class index as reported by
+ * sc_level_size_classes) and the persistent-grid CTAs per SM (0 = keep).
+ * tile_x in {8, 16, 32, 64, 128}, tile_y such that tile_x/2*tile_y == 256,
+ * tile_z >= 1.  Invalidates captured graphs. */
+int sc_level_set_tuning(sc_level* level, int32_t size_class, const sc_tile* tile,
+                        int32_t ctas_per_sm);
+
+/* Number of box-size classes and the class of each box (boxes are grouped
+ * by interior extent rounded up to a multiple of 8 per axis). */
+int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
+                          int32_t* class_of_box /* nboxes entries or NULL */);
+
+/* Run-time tuning of the batched stage kernel (GPU counterpart of the
+ * paper's random-restart hill climbing, Sec. 3.2): for every size class,
+ * times candidate tiles on scratch fields of this level, moves to better
+ * neighbours, restarts at random with small probability, aborts candidates
+ * that run longer than `abort_factor` x the best time, and keeps the best.
+ * budget_ms bounds the total tuning time.  Results are applied to the level
+ * and, if cache_path is not NULL, merged into that on-disk cache (keyed by
+ * GPU name, SM count, arithmetic and class extent) and reused from it.
+ * Synchronises the stream. */
+int sc_level_autotune(sc_level* level, int32_t seed, double budget_ms,
+                      double abort_factor, const char* cache_path, void* stream);
+
+/* ---- kernels ----------------------------------------------------------- */
+
+/* Fill the ghost points of `field` from the owners' interior points
+ * (bit-exact copies), every box of the level, one batched launch.
+ * Ghosts with no owner (outside a non-periodic domain face) are untouched. */
+int sc_level_fill_ghosts(sc_level* level, double* field, void* stream);
+
+/* out = L u on every interior point (ghosts of u must be filled, e.g. by
+ * sc_level_fill_ghosts).  Ghost and padding entries of out are untouched.
+ * u and out must not overlap. */
+int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
+                             void* stream);
+
+/* Advance (u, pi) by nsteps classic RK4 steps of dt, in place.  dt points to
+ * ndt host doubles: ndt == 1 (one step size) or ndt == number of domains
+ * (step size of each domain).  c2 is read on interior points only.  Ghosts
+ * of u are refreshed internally before every stage; on return the ghosts of
+ * u hold the values of the last stage's input, not of the result.  All
+ * domains must be periodic on every axis (SC_EINVAL otherwise).  mode is one
+ * of SC_MODE_*.  Scratch stage arrays are allocated on the first call. */
+int sc_level_rk4_step(sc_level* level, double* u, double* pi, const double* c2,
+                      const double* dt, int32_t ndt, int32_t nsteps, int32_t mode,
+                      void* stream);
+
+/* Same step, end to end from HOST memory: copies u, pi, c2 (host, ideally
+ * pinned) to library-owned device buffers, runs nsteps steps, and copies
+ * the results to u_out, pi_out (host).  Synchronises the stream. */
+int sc_level_rk4_step_host(sc_level* level, const double* u, const double* pi,
+                           const double* c2, double* u_out, double* pi_out,
+                           const double* dt, int32_t ndt, int32_t nsteps,
+                           void* stream);
+
+/* Misfit loss L = 1/2 sum_interior (u - u_obs)^2 h^3 (h per domain) into
+ * *loss (DEVICE double), and, if seed != NULL, seed = h^3 (u - u_obs) on
+ * interior points (the adjoint seed dL/du).  Deterministic reduction. */
+int sc_level_misfit(sc_level* level, const double* u, const double* u_obs,
+                    double* loss, double* seed, void* stream);
+
+/* Forward pass for differentiation: runs nsteps RK4 steps from (u0, pi0)
+ * (batched launches), keeping the state every ckpt_every steps in
+ * library-owned checkpoint fields (the level's tape, replacing any earlier
+ * tape), and writes the final state to u_T, pi_T (either may be NULL).
+ * Inputs are not modified.  Requires periodic domains.  Device memory:
+ * 2 * ceil(nsteps / ckpt_every) fields for the tape. */
+int sc_level_forward_tape(sc_level* level, const double* u0, const double* pi0,
+                          const double* c2, const double* dt, int32_t ndt,
+                          int32_t nsteps, int32_t ckpt_every, double* u_T,
+                          double* pi_T, void* stream);
+
+/* Reverse sweep over the tape (adjoint method).  Given the adjoint seeds
+ * gu_T, gpi_T = dLoss/d(u_T, pi_T) (interior values; NULL means zero),
+ * writes g_u0, g_pi0 = dLoss/d(u0, pi0) and g_c2 = dLoss/dc2 on interior
+ * points.  Each segment between checkpoints is recomputed forward, recording
+ * L w.u of every stage (4 * ckpt_every fields), then reversed step by step.
+ * The adjoint stage applies A^T(a, b) = (L(c2 * b), a) -- c2 multiplies the
+ * adjoint variable before the symmetric stencil -- in reverse stage order.
+ * c2 must be the pointer (and values) given to sc_level_forward_tape.
+ * SC_EINVAL if there is no tape. */
+int sc_level_backward_tape(sc_level* level, const double* c2, const double* gu_T,
+                           const double* gpi_T, double* g_u0, double* g_pi0,
+                           double* g_c2, void* stream);
+
+/* sc_level_forward_tape followed by sc_level_backward_tape, for seeds that
+ * do not depend on the final state (u_T / pi_T may be NULL). */
+int sc_level_grad(sc_level* level, const double* u0, const double* pi0,
+                  const double* c2, const double* dt, int32_t ndt, int32_t nsteps,
+                  int32_t ckpt_every, const double* gu_T, const double* gpi_T,
+                  double* g_u0, double* g_pi0, double* g_c2, double* u_T,
+                  double* pi_T, void* stream);
+
+/* Wait for the stream and report any device error word (SC_EDEVICE). */
+int sc_level_sync(sc_level* level, void* stream);
+
+/* Per-kernel device times of the last sc_level_rk4_step call made with
+ * SC_MODE_TIMED: summed CUDA-event durations and launch counts of the stage
+ * kernel and of the ghost gather.  Waits for those events. */
+int sc_level_kernel_times(sc_level* level, double* stage_ms, int64_t* stage_launches,
+                          double* gather_ms, int64_t* gather_launches);
+
+/* Number of kernel launches the library enqueued since creation (graph
+ * launches count their kernel nodes).  For measurement bookkeeping. */
+int sc_level_launch_count(const sc_level* level, int64_t* n);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* sc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_LEVEL_H */

@@ -1,0 +1,266 @@
+// Run-time tuning of the stage kernel's tiles, the GPU counterpart of the
+// paper's LoopControl optimiser (arXiv 1308.1343, Sec. 3.2, "Random-Restart
+// Hill-Climbing"):
+//  * a "loop setup" is (kernel, box-size class, arithmetic, GPU); each is
+//    tuned independently, starting from the heuristic default tile;
+//  * hill climbing moves to the fastest neighbour (tile_x one step up or
+//    down, tile_z doubled or halved) while that improves the time;
+//  * at a local optimum it restarts, with small probability, from a random
+//    setting, explores that neighbourhood, and keeps whichever is best;
+//  * a candidate whose first timed run is slower than abort_factor x the
+//    best known time is abandoned at once (cautious exploration);
+//  * results are saved to and restored from an on-disk cache (the paper's
+//    proposed future work on saving tuned parameters, Sec. 3.3).
+#include <algorithm>
+#include <cstdio>
+#include <fstream>
+#include <map>
+#include <random>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "level.hpp"
+
+namespace sc {
+namespace {
+
+struct Cand {
+  int tx, tz;
+  bool operator<(const Cand& o) const { return tx != o.tx ? tx < o.tx : tz < o.tz; }
+  bool operator==(const Cand& o) const { return tx == o.tx && tz == o.tz; }
+};
+
+const int kTx[] = {16, 32, 64, 128};
+
+std::string cache_key(const sc_level* L, const SizeClass& c) {
+  std::ostringstream k;
+  k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|" << c.ext[0] << ","
+    << c.ext[1] << "," << c.ext[2];
+  return k.str();
+}
+
+std::map<std::string, std::pair<Cand, double>> read_cache(const char* path) {
+  std::map<std::string, std::pair<Cand, double>> m;
+  if (!path) return m;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    // key \t tx \t tz \t microseconds
+    std::istringstream is(line);
+    std::string key;
+    Cand c{};
+    double us = 0;
+    if (std::getline(is, key, '\t') && (is >> c.tx >> c.tz >> us)) m[key] = {c, us};
+  }
+  return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, std::pair<Cand, double>>& m) {
+  if (!path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    std::ofstream f(tmp);
+    for (const auto& kv : m)
+      f << kv.first << "\t" << kv.second.first.tx << "\t" << kv.second.first.tz << "\t"
+        << kv.second.second << "\n";
+  }
+  std::rename(tmp.c_str(), path);
+}
+
+struct Timer {
+  sc_level* L;
+  cudaStream_t s;
+  double* W[4];
+  double* c2;
+  cudaEvent_t e0, e1;
+  dev::DItem* ditems = nullptr;
+  size_t cap = 0;
+
+  // Items of the boxes of class `cls` with tile (tx, tz); returns the count.
+  int stage(int cls, const Cand& c) {
+    std::vector<dev::DItem> items;
+    for (size_t b = 0; b < L->boxes.size(); ++b) {
+      if (L->box_class[b] != cls) continue;
+      const sc_box& B = L->boxes[b];
+      const int nx = (int)(B.hi[0] - B.lo[0]), ny = (int)(B.hi[1] - B.lo[1]),
+                nz = (int)(B.hi[2] - B.lo[2]);
+      const int ty = 2 * dev_threads() / c.tx;
+      for (int z0 = 0; z0 < nz; z0 += c.tz)
+        for (int y0 = 0; y0 < ny; y0 += ty)
+          for (int x0 = 0; x0 < nx; x0 += c.tx)
+            items.push_back(dev::DItem{(int)b, x0, y0, z0, std::min(c.tz, nz - z0), c.tx / 2});
+    }
+    if (items.size() > cap) {
+      if (ditems) cudaFree(ditems);
+      cap = items.size() * 2;
+      if (cudaMalloc(&ditems, cap * sizeof(dev::DItem)) != cudaSuccess) return -1;
+    }
+    if (cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(dev::DItem),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return -1;
+    return (int)items.size();
+  }
+  static int dev_threads() { return dev::stage_threads(); }
+
+  // Median time (microseconds) of one stage launch over the class's items;
+  // gives up after the first run if it exceeds `limit`.
+  double time(int cls, const Cand& c, double limit) {
+    const int n = stage(cls, c);
+    if (n <= 0) return 1e30;
+    DeviceState* D = L->dev;
+    const int nd = (int)L->doms.size();
+    dev::FwdArgs a{};
+    a.items = ditems;
+    a.nitems = n;
+    a.ndom = nd;
+    a.boxes = D->boxes;
+    a.wu_in = W[0];
+    a.wp_in = W[1];
+    a.yu = W[2];
+    a.yp = W[3];
+    a.c2 = c2;
+    a.wu_out = W[2];
+    a.wp_out = W[3];
+    a.coef = D->coef;
+    a.emax_in = D->emax;
+    a.emax_out = D->emax + nd;
+    a.emax_clear = D->emax + 2 * nd;
+    a.err = D->err;
+    std::vector<double> ts;
+    for (int r = 0; r < 5; ++r) {
+      cudaEventRecord(e0, s);
+      dev::launch_fwd_stage(L->arith, false, a, D->grid_stage, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ts.push_back(ms * 1e3);
+      if (r == 1 && ts.back() > limit) return ts.back();  // abort the excursion
+    }
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
+  }
+};
+
+std::vector<Cand> neighbours(const Cand& c, int64_t nz) {
+  std::vector<Cand> v;
+  const int n = sizeof(kTx) / sizeof(kTx[0]);
+  for (int i = 0; i < n; ++i)
+    if (kTx[i] == c.tx) {
+      if (i > 0) v.push_back(Cand{kTx[i - 1], c.tz});
+      if (i + 1 < n) v.push_back(Cand{kTx[i + 1], c.tz});
+    }
+  if (c.tz > 4) v.push_back(Cand{c.tx, c.tz / 2});
+  if (c.tz < nz) v.push_back(Cand{c.tx, c.tz * 2});
+  return v;
+}
+
+}  // namespace
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
+                                 double abort_factor, const char* cache_path, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!(abort_factor > 1.0)) return set_error(SC_EINVAL, "abort_factor must be > 1");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  Timer T{L, s};
+  if ((rc = scratch4(L, T.W)) || (rc = get_field(L, "tune.c2", &T.c2))) return rc;
+  const double dt0 = 0.0;
+  if ((rc = set_coef(L, &dt0, 1, s))) return rc;
+  cudaEventCreate(&T.e0);
+  cudaEventCreate(&T.e1);
+  auto cache = read_cache(cache_path);
+  std::mt19937_64 rng((uint64_t)seed);
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  const double per_class = budget_ms / std::max<size_t>(1, L->classes.size());
+  bool changed = false;
+  for (size_t ci = 0; ci < L->classes.size(); ++ci) {
+    SizeClass& C = L->classes[ci];
+    const std::string key = cache_key(L, C);
+    auto hit = cache.find(key);
+    if (hit != cache.end()) {
+      C.tile.tile_x = hit->second.first.tx;
+      C.tile.tile_y = 2 * dev::stage_threads() / hit->second.first.tx;
+      C.tile.tile_z = hit->second.first.tz;
+      changed = true;
+      continue;
+    }
+    std::map<Cand, double> seen;
+    auto eval = [&](const Cand& c, double limit) {
+      auto it = seen.find(c);
+      if (it != seen.end()) return it->second;
+      const double t = T.time((int)ci, c, limit);
+      seen[c] = t;
+      return t;
+    };
+    Cand best{C.tile.tile_x, C.tile.tile_z};
+    double tbest = eval(best, 1e30);
+    Cand cur = best;
+    double tcur = tbest;
+    cudaEvent_t w0, w1;
+    cudaEventCreate(&w0);
+    cudaEventCreate(&w1);
+    cudaEventRecord(w0, s);
+    double spent = 0;
+    while (spent < per_class) {
+      // hill climbing: move to the best improving neighbour
+      Cand nb = cur;
+      double tn = tcur;
+      for (const Cand& c : neighbours(cur, C.ext[2])) {
+        const double t = eval(c, abort_factor * tbest);
+        if (t < tn) {
+          tn = t;
+          nb = c;
+        }
+      }
+      if (nb == cur) {
+        // local optimum: restart from a random setting with small probability
+        if (U(rng) < 0.25) {
+          const int ntx = sizeof(kTx) / sizeof(kTx[0]);
+          Cand r{kTx[rng() % ntx], 4 << (rng() % 6)};
+          const double t = eval(r, abort_factor * tbest);
+          cur = r;
+          tcur = t;
+        } else if (seen.size() >= 24) {
+          break;
+        } else {
+          cur = best;
+          tcur = tbest;
+          if (U(rng) < 0.5) break;
+        }
+      } else {
+        cur = nb;
+        tcur = tn;
+      }
+      if (tcur < tbest) {
+        tbest = tcur;
+        best = cur;
+      }
+      cudaEventRecord(w1, s);
+      cudaEventSynchronize(w1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, w0, w1);
+      spent = ms;
+    }
+    cudaEventDestroy(w0);
+    cudaEventDestroy(w1);
+    C.tile.tile_x = best.tx;
+    C.tile.tile_y = 2 * dev::stage_threads() / best.tx;
+    C.tile.tile_z = best.tz;
+    cache[key] = {best, tbest};
+    changed = true;
+  }
+  if (T.ditems) cudaFree(T.ditems);
+  cudaEventDestroy(T.e0);
+  cudaEventDestroy(T.e1);
+  write_cache(cache_path, cache);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  if (changed) return upload_items(L);
+  return SC_OK;
+}

@@ -1,0 +1,49 @@
+// Plain descriptor structs shared by the host runtime and the kernels.
+#pragma once
+
+namespace sc {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// Descriptors (built on the host, uploaded once per level)
+// ---------------------------------------------------------------------------
+
+struct DBox {
+  long long off;  // element index of the interior corner (0,0,0)
+  long long py;   // row pitch (elements)
+  long long pz;   // plane pitch (elements)
+  int nx, ny, nz; // interior extent
+  int dom;        // domain index
+};
+
+struct DItem {
+  int box;
+  int x0, y0, z0;  // tile origin (interior coordinates of the box)
+  int nzr;         // number of planes of the z-run
+  int txh;         // threads per tile row; tile is (2*txh) x (NT/txh) points
+};
+
+// A rectangle of points of one field, for gathers and reductions.
+struct DRect {
+  long long src, dst;        // element index of the first point (dst unused
+                             // by reductions)
+  long long spy, spz;        // source pitches
+  long long dpy, dpz;        // destination pitches
+  int ex, ey, ez;            // extent
+  int dom;                   // domain of the points
+};
+
+// A chunk of up to CHUNK consecutive points of one rectangle.
+struct DChunk {
+  int rect;
+  int first;  // index of the first point within the rectangle (x fastest)
+};
+
+constexpr int kChunk = 1024;
+
+// Error bits of the device error word.
+constexpr unsigned kErrNonFinite = 1u;   // Inf/NaN reached the fixed-point path
+constexpr unsigned kErrScale = 2u;       // an input exceeded its domain bound
+
+}  // namespace dev
+}  // namespace sc

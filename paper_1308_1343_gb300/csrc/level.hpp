@@ -1,0 +1,107 @@
+// Internal host-side representation of a level (not part of the C ABI).
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sc_level.h"
+#include "descriptors.hpp"
+#include "launch.hpp"
+
+struct sc_level;
+
+namespace sc {
+
+int set_error(int code, const std::string& msg);
+int ensure_device(sc_level* L);
+int get_field(sc_level* L, const std::string& name, double** p);
+int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s);
+int scratch4(sc_level* L, double* W[4]);
+int upload_items(sc_level* L);
+
+struct SizeClass {
+  std::array<int64_t, 3> ext;  // interior extent rounded up to a multiple of 8
+  sc_tile tile;
+};
+
+// Device-side state, created lazily on the first call that takes a stream.
+struct DeviceState {
+  int device = -1;
+  int sms = 0;
+  std::string gpu_name;
+  cudaStream_t capture = nullptr;
+
+  dev::DBox* boxes = nullptr;
+  dev::DItem* items = nullptr;
+  int nitems = 0;
+  std::vector<int> box_items;  // per-box item ranges [b], [b+1]
+
+  // ghost exchange as rectangles + chunks (sorted by destination box)
+  dev::DRect* grects = nullptr;
+  dev::DChunk* gchunks = nullptr;
+  int ngchunks = 0;
+  std::vector<int> box_gchunks;
+  // interior rectangles (one per box) + chunks
+  dev::DRect* irects = nullptr;
+  dev::DChunk* ichunks = nullptr;
+  int nichunks = 0;
+  // interior + the six ghost slabs of every box (all points the stencil reads)
+  dev::DRect* srects = nullptr;
+  dev::DChunk* schunks = nullptr;
+  int nschunks = 0;
+
+  dev::StageCoef* coef = nullptr;  // [4][ndom]
+  std::vector<double> coef_dt;     // dt per domain the coefficients were built for
+  double* inv12h2 = nullptr;       // [ndom]
+  double* h3 = nullptr;            // [ndom]
+  unsigned* emax = nullptr;        // forward ring [4][ndom]
+  unsigned* emax_adj = nullptr;    // adjoint ring [4][ndom]
+  unsigned* err = nullptr;
+  double* partial = nullptr;       // [nichunks]
+  double* pinned = nullptr;        // host staging for small uploads
+  size_t pinned_size = 0;
+
+  // scratch fields, library-owned
+  std::map<std::string, double*> fields;
+  std::map<std::string, size_t> field_count;
+
+  // captured RK4 step graphs keyed by (u, pi, c2, arith, version)
+  std::map<std::tuple<const void*, const void*, const void*, int, int>,
+           std::pair<cudaGraphExec_t, int>>
+      graphs;
+  // per-kernel CUDA-event timing (mode SC_MODE_TIMED): kind -> event pairs
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;  // 0 = stage kernel, 1 = ghost gather, 2 = other
+  int grid_stage = 0;  // persistent grid of the stage kernels
+  int grid_small = 0;  // grid of the gather / reduction kernels
+};
+
+}  // namespace sc
+
+struct sc_level {
+  std::vector<sc_box> boxes;
+  std::vector<sc_domain> doms;
+  std::vector<int64_t> off, py, pz, storage;
+  int64_t field_size = 0;
+  std::vector<sc_copy> copies;
+  std::vector<int> box_class;
+  std::vector<sc::SizeClass> classes;
+  int arith = SC_ARITH_FIXED;
+  int ctas_per_sm = 0;
+  int version = 0;  // bumps when items change (invalidates graphs)
+  int64_t launches = 0;
+  bool all_periodic = true;
+  // tape of the last sc_level_forward_tape
+  bool tape_valid = false;
+  int tape_nsteps = 0, tape_ckpt = 1;
+  const double* tape_c2 = nullptr;
+  std::vector<double> tape_dt;
+  sc::DeviceState* dev = nullptr;
+};

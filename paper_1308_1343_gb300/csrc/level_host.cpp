@@ -1,0 +1,372 @@
+// Host-only part of the C ABI: level construction and validation with the
+// bboxset algebra, the level layout, the ghost-exchange list, size classes,
+// and the bboxset entry points.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sc_bboxset.h"
+#include "../../include/sc_level.h"
+#include "bboxset.hpp"
+#include "level.hpp"
+
+namespace sc {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+void release_device(sc_level* L);  // runtime.cu
+
+static BBox3 to_box(const int64_t* lo, const int64_t* hi) {
+  BBox3 b;
+  for (int d = 0; d < 3; ++d) {
+    b.lo[d] = lo[d];
+    b.hi[d] = hi[d];
+  }
+  return b;
+}
+
+static int64_t roundup(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
+
+// Ghost region of one box: the star-shaped shell
+// (union_d expand_d(box, g)) minus the box.
+static BBoxSet3 star_shell(const BBox3& b, int g) {
+  BBoxSet3 B = BBoxSet3::box(b);
+  BBoxSet3 u;
+  for (int d = 0; d < 3; ++d) {
+    int64_t lo_by[3] = {0, 0, 0}, hi_by[3] = {0, 0, 0};
+    lo_by[d] = hi_by[d] = g;
+    u = u | B.expanded(lo_by, hi_by);
+  }
+  return u - B;
+}
+
+// The exchange list: for every box b and every box o of the same domain and
+// every periodic image s, the rectangles of shell(b) & shift(o, s * L), each
+// copied from o's interior point p - s * L (the communication schedule the
+// paper derives from bboxset intersections, Sec. 2).
+static void build_exchange(sc_level* L) {
+  const int nb = (int)L->boxes.size();
+  L->copies.clear();
+  for (int b = 0; b < nb; ++b) {
+    const sc_box& B = L->boxes[b];
+    const sc_domain& D = L->doms[B.domain];
+    const BBox3 bb = to_box(B.lo, B.hi);
+    const BBoxSet3 shell = star_shell(bb, 2);
+    BBox3 reach = bb;
+    for (int d = 0; d < 3; ++d) {
+      reach.lo[d] -= 2;
+      reach.hi[d] += 2;
+    }
+    int64_t len[3];
+    for (int d = 0; d < 3; ++d) len[d] = D.hi[d] - D.lo[d];
+    for (int o = 0; o < nb; ++o) {
+      const sc_box& O = L->boxes[o];
+      if (O.domain != B.domain) continue;
+      for (int sz = -1; sz <= 1; ++sz)
+        for (int sy = -1; sy <= 1; ++sy)
+          for (int sx = -1; sx <= 1; ++sx) {
+            const int s[3] = {sx, sy, sz};
+            bool ok = true;
+            for (int d = 0; d < 3; ++d)
+              if (s[d] != 0 && !(D.periodic & (1u << d))) ok = false;
+            if (!ok) continue;
+            int64_t v[3];
+            BBox3 ob = to_box(O.lo, O.hi);
+            for (int d = 0; d < 3; ++d) {
+              v[d] = s[d] * len[d];
+              ob.lo[d] += v[d];
+              ob.hi[d] += v[d];
+            }
+            // bounding-box test before the set intersection
+            bool overlap = true;
+            for (int d = 0; d < 3; ++d)
+              if (ob.hi[d] <= reach.lo[d] || ob.lo[d] >= reach.hi[d]) overlap = false;
+            if (!overlap) continue;
+            const BBoxSet3 I = shell & BBoxSet3::box(ob);
+            for (const BBox3& r : I.boxes()) {
+              sc_copy c;
+              c.src_box = o;
+              c.dst_box = b;
+              for (int d = 0; d < 3; ++d) {
+                c.dst_lo[d] = r.lo[d];
+                c.src_lo[d] = r.lo[d] - v[d];
+                c.ext[d] = r.hi[d] - r.lo[d];
+              }
+              L->copies.push_back(c);
+            }
+          }
+    }
+  }
+}
+
+static sc_tile default_tile(const std::array<int64_t, 3>& ext) {
+  sc_tile t{};
+  const int64_t nx = ext[0];
+  t.tile_x = nx <= 16 ? 16 : (nx <= 32 ? 32 : 64);
+  t.tile_y = 2 * 256 / t.tile_x;
+  t.tile_z = 32;
+  return t;
+}
+
+static void build_classes(sc_level* L) {
+  L->classes.clear();
+  L->box_class.assign(L->boxes.size(), 0);
+  std::map<std::array<int64_t, 3>, int> idx;
+  for (size_t b = 0; b < L->boxes.size(); ++b) {
+    std::array<int64_t, 3> e;
+    for (int d = 0; d < 3; ++d) e[d] = roundup(L->boxes[b].hi[d] - L->boxes[b].lo[d], 8);
+    auto it = idx.find(e);
+    if (it == idx.end()) {
+      it = idx.emplace(e, (int)L->classes.size()).first;
+      L->classes.push_back(SizeClass{e, default_tile(e)});
+    }
+    L->box_class[b] = it->second;
+  }
+}
+
+static int validate(const sc_box* boxes, int32_t nboxes, const sc_domain* doms,
+                    int32_t ndoms) {
+  if (nboxes <= 0 || !boxes) return set_error(SC_EINVAL, "level needs at least one box");
+  if (ndoms <= 0 || !doms) return set_error(SC_EINVAL, "level needs at least one domain");
+  for (int32_t d = 0; d < ndoms; ++d) {
+    const sc_domain& D = doms[d];
+    if (!(D.h > 0.0)) return set_error(SC_EINVAL, "domain " + std::to_string(d) + ": h <= 0");
+    if (D.reserved != 0 || (D.periodic & ~7u))
+      return set_error(SC_EINVAL, "domain " + std::to_string(d) + ": reserved bits set");
+    for (int a = 0; a < 3; ++a)
+      if (D.hi[a] - D.lo[a] < 2)
+        return set_error(SC_EINVAL, "domain " + std::to_string(d) + ": extent < 2");
+  }
+  std::vector<std::vector<int>> per(ndoms);
+  for (int32_t b = 0; b < nboxes; ++b) {
+    const sc_box& B = boxes[b];
+    const std::string nm = "box " + std::to_string(b);
+    if (B.domain < 0 || B.domain >= ndoms) return set_error(SC_EINVAL, nm + ": bad domain");
+    if (B.reserved != 0) return set_error(SC_EINVAL, nm + ": reserved field set");
+    const sc_domain& D = doms[B.domain];
+    for (int a = 0; a < 3; ++a) {
+      if (B.hi[a] - B.lo[a] < 2) return set_error(SC_EINVAL, nm + ": edge < 2");
+      if (B.hi[a] - B.lo[a] > (1 << 24)) return set_error(SC_EINVAL, nm + ": edge too large");
+      if (B.lo[a] < D.lo[a] || B.hi[a] > D.hi[a])
+        return set_error(SC_EINVAL, nm + ": not inside its domain");
+    }
+    per[B.domain].push_back(b);
+  }
+  // each domain is tiled exactly: union == domain and no overlap
+  for (int32_t d = 0; d < ndoms; ++d) {
+    const sc_domain& D = doms[d];
+    if (per[d].empty()) return set_error(SC_EINVAL, "domain " + std::to_string(d) + " has no box");
+    BBoxSet3 u;
+    int64_t total = 0;
+    for (int b : per[d]) {
+      const BBoxSet3 s = BBoxSet3::box(boxes[b].lo, boxes[b].hi);
+      const BBoxSet3 common = u & s;
+      if (!common.empty())
+        return set_error(SC_EINVAL, "box " + std::to_string(b) + " overlaps another box of domain " +
+                                        std::to_string(d));
+      u = u | s;
+      total += s.size();
+    }
+    const BBoxSet3 dom = BBoxSet3::box(D.lo, D.hi);
+    if (u != dom)
+      return set_error(SC_EINVAL, "boxes of domain " + std::to_string(d) + " do not tile it");
+    (void)total;
+  }
+  return SC_OK;
+}
+
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+const char* sc_last_error(void) { return g_last_error.c_str(); }
+
+int sc_level_create(const sc_box* boxes, int32_t nboxes, const sc_domain* doms, int32_t ndoms,
+                    int32_t ghost, sc_level** out) {
+  if (!out) return set_error(SC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (ghost != 2) return set_error(SC_EINVAL, "ghost width must be 2");
+  int rc = validate(boxes, nboxes, doms, ndoms);
+  if (rc) return rc;
+  sc_level* L = new (std::nothrow) sc_level();
+  if (!L) return set_error(SC_ENOMEM, "out of host memory");
+  try {
+    L->boxes.assign(boxes, boxes + nboxes);
+    L->doms.assign(doms, doms + ndoms);
+    for (const auto& D : L->doms)
+      if (D.periodic != 7u) L->all_periodic = false;
+    // layout: interior corner of every box on a 16-double (128-byte) line
+    int64_t base = 14;
+    for (const auto& B : L->boxes) {
+      const int64_t nx = B.hi[0] - B.lo[0], ny = B.hi[1] - B.lo[1], nz = B.hi[2] - B.lo[2];
+      const int64_t py = roundup(nx + 4, 16), pz = py * (ny + 4), st = pz * (nz + 4);
+      L->py.push_back(py);
+      L->pz.push_back(pz);
+      L->storage.push_back(st);
+      L->off.push_back(base + 2 + 2 * py + 2 * pz);
+      base += st;
+    }
+    L->field_size = base + 2;
+    build_exchange(L);
+    build_classes(L);
+  } catch (const std::bad_alloc&) {
+    delete L;
+    return set_error(SC_ENOMEM, "out of host memory");
+  }
+  *out = L;
+  return SC_OK;
+}
+
+void sc_level_destroy(sc_level* L) {
+  if (!L) return;
+  release_device(L);
+  delete L;
+}
+
+int sc_level_field_size(const sc_level* L, int64_t* n) {
+  if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
+  *n = L->field_size;
+  return SC_OK;
+}
+
+int sc_level_num_boxes(const sc_level* L, int32_t* n) {
+  if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
+  *n = (int32_t)L->boxes.size();
+  return SC_OK;
+}
+
+int sc_level_box_layout(const sc_level* L, int32_t b, int64_t* offset, int64_t dims[3],
+                        int64_t pitch[3]) {
+  if (!L || !offset || !dims || !pitch) return set_error(SC_EINVAL, "NULL argument");
+  if (b < 0 || b >= (int32_t)L->boxes.size()) return set_error(SC_EINVAL, "box out of range");
+  *offset = L->off[b];
+  for (int d = 0; d < 3; ++d) dims[d] = L->boxes[b].hi[d] - L->boxes[b].lo[d];
+  pitch[0] = 1;
+  pitch[1] = L->py[b];
+  pitch[2] = L->pz[b];
+  return SC_OK;
+}
+
+int sc_level_exchange_list(const sc_level* L, sc_copy* out, int64_t cap, int64_t* n) {
+  if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
+  if (cap > 0 && !out) return set_error(SC_EINVAL, "out is NULL");
+  *n = (int64_t)L->copies.size();
+  const int64_t m = std::min<int64_t>(cap, *n);
+  if (m > 0) std::memcpy(out, L->copies.data(), (size_t)m * sizeof(sc_copy));
+  return SC_OK;
+}
+
+int sc_level_size_classes(const sc_level* L, int32_t* nclasses, int32_t* class_of_box) {
+  if (!L || !nclasses) return set_error(SC_EINVAL, "NULL argument");
+  *nclasses = (int32_t)L->classes.size();
+  if (class_of_box)
+    for (size_t b = 0; b < L->boxes.size(); ++b) class_of_box[b] = L->box_class[b];
+  return SC_OK;
+}
+
+int sc_level_set_arith(sc_level* L, int32_t arith) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (arith != SC_ARITH_FP64 && arith != SC_ARITH_FIXED)
+    return set_error(SC_EINVAL, "unknown arithmetic");
+  if (L->arith == arith) return SC_OK;
+  L->arith = arith;
+  if (L->dev) return upload_items(L);  // occupancy (grid) depends on the arithmetic
+  return SC_OK;
+}
+
+int sc_level_launch_count(const sc_level* L, int64_t* n) {
+  if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
+  *n = L->launches;
+  return SC_OK;
+}
+
+// ---- bboxset entry points ------------------------------------------------
+
+static int read_set(const int64_t* a, int64_t na, BBoxSet3* s) {
+  if (na < 0 || (na > 0 && !a)) return set_error(SC_EINVAL, "bad box array");
+  BBoxSet3 r;
+  for (int64_t i = 0; i < na; ++i) {
+    for (int d = 0; d < 3; ++d)
+      if (a[6 * i + d] > a[6 * i + 3 + d]) return set_error(SC_EINVAL, "box with lo > hi");
+    r = r | BBoxSet3::box(a + 6 * i, a + 6 * i + 3);
+  }
+  *s = std::move(r);
+  return SC_OK;
+}
+
+static int write_boxes(const BBoxSet3& s, int64_t* out, int64_t cap, int64_t* n) {
+  const std::vector<BBox3> bs = s.boxes();
+  *n = (int64_t)bs.size();
+  if (cap > 0 && !out) return set_error(SC_EINVAL, "out is NULL");
+  for (int64_t i = 0; i < std::min<int64_t>(cap, *n); ++i)
+    for (int d = 0; d < 3; ++d) {
+      out[6 * i + d] = bs[i].lo[d];
+      out[6 * i + 3 + d] = bs[i].hi[d];
+    }
+  return SC_OK;
+}
+
+int sc_bboxset_op(int32_t op, const int64_t* a, int64_t na, const int64_t* b, int64_t nb,
+                  int64_t* out, int64_t cap, int64_t* n) {
+  if (!n) return set_error(SC_EINVAL, "n is NULL");
+  BBoxSet3 A, B;
+  int rc = read_set(a, na, &A);
+  if (rc) return rc;
+  rc = read_set(b, nb, &B);
+  if (rc) return rc;
+  SetOp o;
+  switch (op) {
+    case SC_SET_UNION: o = SetOp::Union; break;
+    case SC_SET_INTERSECTION: o = SetOp::Intersection; break;
+    case SC_SET_DIFFERENCE: o = SetOp::Difference; break;
+    case SC_SET_XOR: o = SetOp::Xor; break;
+    default: return set_error(SC_EINVAL, "unknown set operation");
+  }
+  return write_boxes(BBoxSet3::binop(A, B, o), out, cap, n);
+}
+
+int sc_bboxset_derivative(const int64_t* a, int64_t na, int64_t* pts, int64_t cap, int64_t* n) {
+  if (!n) return set_error(SC_EINVAL, "n is NULL");
+  BBoxSet3 A;
+  int rc = read_set(a, na, &A);
+  if (rc) return rc;
+  std::vector<std::array<int64_t, 3>> p;
+  A.derivative_points(p);
+  *n = (int64_t)p.size();
+  if (cap > 0 && !pts) return set_error(SC_EINVAL, "pts is NULL");
+  for (int64_t i = 0; i < std::min<int64_t>(cap, *n); ++i)
+    for (int d = 0; d < 3; ++d) pts[3 * i + d] = p[i][d];
+  return SC_OK;
+}
+
+int sc_bboxset_expand_shift(const int64_t* a, int64_t na, const int64_t lo_by[3],
+                            const int64_t hi_by[3], const int64_t v[3], int64_t* out,
+                            int64_t cap, int64_t* n) {
+  if (!n || !lo_by || !hi_by || !v) return set_error(SC_EINVAL, "NULL argument");
+  for (int d = 0; d < 3; ++d)
+    if (lo_by[d] < 0 || hi_by[d] < 0) return set_error(SC_EINVAL, "negative expansion");
+  BBoxSet3 A;
+  int rc = read_set(a, na, &A);
+  if (rc) return rc;
+  return write_boxes(A.expanded(lo_by, hi_by).shifted(v), out, cap, n);
+}
+
+int sc_bboxset_size(const int64_t* a, int64_t na, int64_t* npoints) {
+  if (!npoints) return set_error(SC_EINVAL, "NULL argument");
+  BBoxSet3 A;
+  int rc = read_set(a, na, &A);
+  if (rc) return rc;
+  *npoints = A.size();
+  return SC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,798 @@
+// Device side of the C ABI: descriptor upload, kernel enqueueing, the RK4
+// step (per-box launches, batched launches, or a CUDA graph per step), the
+// end-to-end host entry point, the misfit, and the checkpointed adjoint.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "level.hpp"
+
+namespace sc {
+
+using dev::DBox;
+using dev::DChunk;
+using dev::DItem;
+using dev::DRect;
+using dev::StageCoef;
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return set_error(SC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SC_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <class T>
+int upload(T** dst, const std::vector<T>& v) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (v.empty()) return SC_OK;
+  SC_CUDA(cudaMalloc(dst, v.size() * sizeof(T)));
+  SC_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SC_OK;
+}
+
+void add_chunks(int rect, int64_t n, std::vector<DChunk>& out) {
+  for (int64_t f = 0; f < n; f += dev::kChunk) out.push_back(DChunk{rect, (int)f});
+}
+
+// Work items: every box cut into (tile_x, tile_y, tile_z) items of its class,
+// box-major, then z, y, x.
+void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>& box_items) {
+  items.clear();
+  box_items.assign(L->boxes.size() + 1, 0);
+  for (size_t b = 0; b < L->boxes.size(); ++b) {
+    box_items[b] = (int)items.size();
+    const sc_box& B = L->boxes[b];
+    const sc_tile& t = L->classes[L->box_class[b]].tile;
+    const int nx = (int)(B.hi[0] - B.lo[0]), ny = (int)(B.hi[1] - B.lo[1]),
+              nz = (int)(B.hi[2] - B.lo[2]);
+    for (int z0 = 0; z0 < nz; z0 += t.tile_z)
+      for (int y0 = 0; y0 < ny; y0 += t.tile_y)
+        for (int x0 = 0; x0 < nx; x0 += t.tile_x)
+          items.push_back(DItem{(int)b, x0, y0, z0, std::min(t.tile_z, nz - z0), t.tile_x / 2});
+  }
+  box_items[L->boxes.size()] = (int)items.size();
+}
+
+}  // namespace
+
+int upload_items(sc_level* L) {
+  DeviceState* D = L->dev;
+  std::vector<DItem> items;
+  build_items(L, items, D->box_items);
+  int rc = upload(&D->items, items);
+  if (rc) return rc;
+  D->nitems = (int)items.size();
+  int occ = 0;
+  SC_CUDA(dev::stage_occupancy(L->arith, &occ));
+  const int per_sm = L->ctas_per_sm > 0 ? L->ctas_per_sm : std::max(1, occ);
+  D->grid_stage = D->sms * per_sm;
+  for (auto& kv : D->graphs) cudaGraphExecDestroy(kv.second.first);
+  D->graphs.clear();
+  L->version++;
+  return SC_OK;
+}
+
+void release_device(sc_level* L) {
+  DeviceState* D = L->dev;
+  if (!D) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != D->device) cudaSetDevice(D->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : D->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (auto& pr : D->ev_pool) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (auto& kv : D->fields) cudaFree(kv.second);
+  void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->irects, D->ichunks,
+                  D->srects, D->schunks, D->coef, D->inv12h2, D->h3, D->emax,
+                  D->emax_adj, D->err, D->partial};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (D->pinned) cudaFreeHost(D->pinned);
+  if (D->capture) cudaStreamDestroy(D->capture);
+  if (cur != D->device && cur >= 0) cudaSetDevice(cur);
+  delete D;
+  L->dev = nullptr;
+}
+
+int ensure_device(sc_level* L) {
+  int cur = -1;
+  SC_CUDA(cudaGetDevice(&cur));
+  if (L->dev) {
+    if (L->dev->device != cur)
+      return set_error(SC_EINVAL, "level was set up on another device");
+    return SC_OK;
+  }
+  DeviceState* D = new DeviceState();
+  L->dev = D;
+  D->device = cur;
+  cudaDeviceProp p;
+  SC_CUDA(cudaGetDeviceProperties(&p, cur));
+  D->sms = p.multiProcessorCount;
+  D->gpu_name = p.name;
+  D->grid_small = D->sms * 8;
+  SC_CUDA(cudaStreamCreateWithFlags(&D->capture, cudaStreamNonBlocking));
+
+  const int nb = (int)L->boxes.size(), nd = (int)L->doms.size();
+  std::vector<DBox> boxes(nb);
+  for (int b = 0; b < nb; ++b) {
+    const sc_box& B = L->boxes[b];
+    boxes[b] = DBox{L->off[b], L->py[b], L->pz[b], (int)(B.hi[0] - B.lo[0]),
+                    (int)(B.hi[1] - B.lo[1]), (int)(B.hi[2] - B.lo[2]), B.domain};
+  }
+  int rc = upload(&D->boxes, boxes);
+  if (rc) return rc;
+
+  auto index_of = [&](int b, const int64_t p[3]) {
+    const sc_box& B = L->boxes[b];
+    return L->off[b] + (p[0] - B.lo[0]) + (p[1] - B.lo[1]) * L->py[b] +
+           (p[2] - B.lo[2]) * L->pz[b];
+  };
+  // ghost copies, chunked, grouped by destination box
+  std::vector<DRect> grects;
+  std::vector<DChunk> gchunks;
+  D->box_gchunks.assign(nb + 1, 0);
+  {
+    size_t c = 0;
+    for (int b = 0; b < nb; ++b) {
+      D->box_gchunks[b] = (int)gchunks.size();
+      for (; c < L->copies.size() && L->copies[c].dst_box == b; ++c) {
+        const sc_copy& C = L->copies[c];
+        DRect r;
+        r.src = index_of(C.src_box, C.src_lo);
+        r.dst = index_of(C.dst_box, C.dst_lo);
+        r.spy = L->py[C.src_box];
+        r.spz = L->pz[C.src_box];
+        r.dpy = L->py[C.dst_box];
+        r.dpz = L->pz[C.dst_box];
+        r.ex = (int)C.ext[0];
+        r.ey = (int)C.ext[1];
+        r.ez = (int)C.ext[2];
+        r.dom = L->boxes[b].domain;
+        grects.push_back(r);
+        add_chunks((int)grects.size() - 1, C.ext[0] * C.ext[1] * C.ext[2], gchunks);
+      }
+    }
+    D->box_gchunks[nb] = (int)gchunks.size();
+  }
+  rc = upload(&D->grects, grects);
+  if (!rc) rc = upload(&D->gchunks, gchunks);
+  if (rc) return rc;
+  D->ngchunks = (int)gchunks.size();
+
+  // interior rectangles, and interior + six ghost slabs
+  std::vector<DRect> irects, srects;
+  std::vector<DChunk> ichunks, schunks;
+  for (int b = 0; b < nb; ++b) {
+    const sc_box& B = L->boxes[b];
+    int64_t n[3];
+    for (int d = 0; d < 3; ++d) n[d] = B.hi[d] - B.lo[d];
+    DRect r{};
+    r.src = r.dst = L->off[b];
+    r.spy = r.dpy = L->py[b];
+    r.spz = r.dpz = L->pz[b];
+    r.ex = (int)n[0];
+    r.ey = (int)n[1];
+    r.ez = (int)n[2];
+    r.dom = B.domain;
+    irects.push_back(r);
+    add_chunks((int)irects.size() - 1, n[0] * n[1] * n[2], ichunks);
+    srects.push_back(r);
+    add_chunks((int)srects.size() - 1, n[0] * n[1] * n[2], schunks);
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side) {
+        int64_t p[3] = {B.lo[0], B.lo[1], B.lo[2]};
+        p[d] = side ? B.hi[d] : B.lo[d] - 2;
+        DRect s = r;
+        s.src = s.dst = index_of(b, p);
+        int e[3] = {(int)n[0], (int)n[1], (int)n[2]};
+        e[d] = 2;
+        s.ex = e[0];
+        s.ey = e[1];
+        s.ez = e[2];
+        srects.push_back(s);
+        add_chunks((int)srects.size() - 1, (int64_t)e[0] * e[1] * e[2], schunks);
+      }
+  }
+  rc = upload(&D->irects, irects);
+  if (!rc) rc = upload(&D->ichunks, ichunks);
+  if (!rc) rc = upload(&D->srects, srects);
+  if (!rc) rc = upload(&D->schunks, schunks);
+  if (rc) return rc;
+  D->nichunks = (int)ichunks.size();
+  D->nschunks = (int)schunks.size();
+
+  std::vector<double> inv(nd), h3(nd);
+  for (int d = 0; d < nd; ++d) {
+    const double h = L->doms[d].h;
+    inv[d] = 1.0 / (12.0 * h * h);
+    h3[d] = h * h * h;
+  }
+  rc = upload(&D->inv12h2, inv);
+  if (!rc) rc = upload(&D->h3, h3);
+  if (rc) return rc;
+  SC_CUDA(cudaMalloc(&D->coef, sizeof(StageCoef) * 4 * nd));
+  SC_CUDA(cudaMalloc(&D->emax, sizeof(unsigned) * 4 * nd));
+  SC_CUDA(cudaMalloc(&D->emax_adj, sizeof(unsigned) * 4 * nd));
+  SC_CUDA(cudaMemset(D->emax, 0, sizeof(unsigned) * 4 * nd));
+  SC_CUDA(cudaMemset(D->emax_adj, 0, sizeof(unsigned) * 4 * nd));
+  SC_CUDA(cudaMalloc(&D->err, sizeof(unsigned)));
+  SC_CUDA(cudaMemset(D->err, 0, sizeof(unsigned)));
+  SC_CUDA(cudaMalloc(&D->partial, sizeof(double) * std::max(1, D->nichunks)));
+  D->pinned_size = sizeof(StageCoef) * 4 * nd + 64;
+  SC_CUDA(cudaMallocHost(&D->pinned, D->pinned_size));
+  return upload_items(L);
+}
+
+// Library-owned field buffer `name` (field_size doubles, zeroed once).
+int get_field(sc_level* L, const std::string& name, double** p) {
+  DeviceState* D = L->dev;
+  auto it = D->fields.find(name);
+  if (it != D->fields.end()) {
+    *p = it->second;
+    return SC_OK;
+  }
+  double* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(double) * L->field_size);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SC_ENOMEM, "device allocation of scratch field '" + name + "' failed");
+  }
+  SC_CUDA(cudaMemset(q, 0, sizeof(double) * L->field_size));
+  D->fields[name] = q;
+  *p = q;
+  return SC_OK;
+}
+
+// Per (stage, domain) coefficients for step sizes dt (ndt == 1 or ndom).
+int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s) {
+  DeviceState* D = L->dev;
+  const int nd = (int)L->doms.size();
+  if (!dt || (ndt != 1 && ndt != nd)) return set_error(SC_EINVAL, "dt must have 1 or ndom entries");
+  std::vector<double> want(nd);
+  for (int d = 0; d < nd; ++d) {
+    want[d] = dt[ndt == 1 ? 0 : d];
+    if (!(want[d] > 0.0) && want[d] != 0.0) return set_error(SC_EINVAL, "dt must be >= 0");
+  }
+  if (want == D->coef_dt) return SC_OK;
+  static const double c[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  // wait for earlier work that reads the pinned staging buffer
+  SC_CUDA(cudaStreamSynchronize(s));
+  StageCoef* h = reinterpret_cast<StageCoef*>(D->pinned);
+  for (int st = 0; st < 4; ++st)
+    for (int d = 0; d < nd; ++d) {
+      const double hh = L->doms[d].h;
+      const double g = c[st] * want[d];
+      h[st * nd + d] = StageCoef{g, g / (12.0 * hh * hh), 1.0 / (12.0 * hh * hh), 0.0};
+    }
+  SC_CUDA(cudaMemcpyAsync(D->coef, h, sizeof(StageCoef) * 4 * nd, cudaMemcpyHostToDevice, s));
+  D->coef_dt = want;
+  return SC_OK;
+}
+
+static bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// ---- enqueueing ------------------------------------------------------------
+
+struct Enq {
+  sc_level* L;
+  cudaStream_t s;
+  int64_t* count;
+  bool per_box;
+  bool timed = false;
+};
+
+// Event pair around one launch when timing is on.
+struct TimedLaunch {
+  const Enq& q;
+  cudaEvent_t e1 = nullptr;
+  TimedLaunch(const Enq& q_, int kind) : q(q_) {
+    if (!q.timed) return;
+    DeviceState* D = q.L->dev;
+    if (D->ev_used == D->ev_pool.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      D->ev_pool.emplace_back(a, b);
+    }
+    auto& pr = D->ev_pool[D->ev_used++];
+    D->ev_kind.push_back(kind);
+    cudaEventRecord(pr.first, q.s);
+    e1 = pr.second;
+  }
+  ~TimedLaunch() {
+    if (e1) cudaEventRecord(e1, q.s);
+  }
+};
+
+static cudaError_t enq_fill(const Enq& q, double* f) {
+  DeviceState* D = q.L->dev;
+  if (!q.per_box) {
+    (*q.count)++;
+    TimedLaunch t(q, 1);
+    return dev::launch_gather(D->grects, D->gchunks, D->ngchunks, f, D->grid_small, q.s);
+  }
+  for (size_t b = 0; b + 1 < D->box_gchunks.size(); ++b) {
+    const int n = D->box_gchunks[b + 1] - D->box_gchunks[b];
+    if (n <= 0) continue;
+    (*q.count)++;
+    TimedLaunch t(q, 1);
+    cudaError_t e = dev::launch_gather(D->grects, D->gchunks + D->box_gchunks[b], n, f,
+                                       D->grid_small, q.s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t enq_maxexp(const Enq& q, const double* f, unsigned* slot, bool star) {
+  DeviceState* D = q.L->dev;
+  (*q.count)++;
+  if (star)
+    return dev::launch_maxexp(D->srects, D->schunks, D->nschunks, f, slot, D->err,
+                              D->grid_small, q.s);
+  return dev::launch_maxexp(D->irects, D->ichunks, D->nichunks, f, slot, D->err, D->grid_small,
+                            q.s);
+}
+
+static cudaError_t enq_fwd(const Enq& q, dev::FwdArgs a, bool record) {
+  DeviceState* D = q.L->dev;
+  if (!q.per_box) {
+    a.items = D->items;
+    a.nitems = D->nitems;
+    (*q.count)++;
+    TimedLaunch t(q, 0);
+    return dev::launch_fwd_stage(q.L->arith, record, a, D->grid_stage, q.s);
+  }
+  for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
+    a.items = D->items + D->box_items[b];
+    a.nitems = D->box_items[b + 1] - D->box_items[b];
+    (*q.count)++;
+    TimedLaunch t(q, 0);
+    cudaError_t e = dev::launch_fwd_stage(q.L->arith, record, a, D->grid_stage, q.s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One RK4 step in nested form on (u, pi), stage scratch Wa, Wb.  If lapw is
+// not NULL, stage s also records L w_{s-1}.u into lapw[s].
+static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c2,
+                            double* const* W, double* const* lapw) {
+  DeviceState* D = q.L->dev;
+  const int nd = (int)q.L->doms.size();
+  double* in_u[4] = {u, W[0], W[2], W[0]};
+  double* in_p[4] = {pi, W[1], W[3], W[1]};
+  double* out_u[4] = {W[0], W[2], W[0], u};
+  double* out_p[4] = {W[1], W[3], W[1], pi};
+  for (int s = 0; s < 4; ++s) {
+    cudaError_t e = enq_fill(q, in_u[s]);
+    if (e != cudaSuccess) return e;
+    dev::FwdArgs a{};
+    a.ndom = nd;
+    a.boxes = D->boxes;
+    a.wu_in = in_u[s];
+    a.wp_in = in_p[s];
+    a.yu = u;
+    a.yp = pi;
+    a.c2 = c2;
+    a.wu_out = out_u[s];
+    a.wp_out = out_p[s];
+    a.lapw = lapw ? lapw[s] : nullptr;
+    a.coef = D->coef + s * nd;
+    a.emax_in = D->emax + (s % 4) * nd;
+    a.emax_out = D->emax + ((s + 1) % 4) * nd;
+    a.emax_clear = D->emax + ((s + 2) % 4) * nd;
+    a.err = D->err;
+    e = enq_fwd(q, a, lapw != nullptr);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Exponent prologue of a run of fixed-point steps: ring cleared, slot 0 =
+// max exponent of u.
+static cudaError_t enq_prologue(const Enq& q, const double* u) {
+  if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
+  DeviceState* D = q.L->dev;
+  cudaError_t e =
+      cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
+  if (e != cudaSuccess) return e;
+  return enq_maxexp(q, u, D->emax, false);
+}
+
+int scratch4(sc_level* L, double* W[4]) {
+  const char* names[4] = {"Wa.u", "Wa.pi", "Wb.u", "Wb.pi"};
+  for (int i = 0; i < 4; ++i) {
+    int rc = get_field(L, names[i], &W[i]);
+    if (rc) return rc;
+  }
+  return SC_OK;
+}
+
+static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int nsteps, int mode,
+                     cudaStream_t s) {
+  DeviceState* D = L->dev;
+  double* W[4];
+  int rc = scratch4(L, W);
+  if (rc) return rc;
+  Enq q{L, s, &L->launches, mode == SC_MODE_PER_BOX};
+  if (mode == SC_MODE_TIMED) {
+    q.timed = true;
+    D->ev_used = 0;
+    D->ev_kind.clear();
+  }
+  SC_CUDA(enq_prologue(q, u));
+  if (mode != SC_MODE_GRAPH) {
+    for (int n = 0; n < nsteps; ++n) SC_CUDA(enq_step(q, u, pi, c2, W, nullptr));
+    return SC_OK;
+  }
+  auto key = std::make_tuple((const void*)u, (const void*)pi, (const void*)c2, L->arith,
+                             L->version);
+  auto it = D->graphs.find(key);
+  if (it == D->graphs.end()) {
+    if (D->graphs.size() >= 16) {  // bounded cache: drop the oldest-keyed graphs
+      SC_CUDA(cudaStreamSynchronize(s));
+      for (auto& kv : D->graphs) cudaGraphExecDestroy(kv.second.first);
+      D->graphs.clear();
+    }
+    int64_t nodes = 0;
+    Enq cq{L, D->capture, &nodes, false};
+    SC_CUDA(cudaStreamBeginCapture(D->capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enq_step(cq, u, pi, c2, W, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(D->capture, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "capture of the RK4 step");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    it = D->graphs.emplace(key, std::make_pair(ex, (int)nodes)).first;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    SC_CUDA(cudaGraphLaunch(it->second.first, s));
+    L->launches += it->second.second;
+  }
+  return SC_OK;
+}
+
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+int sc_level_fill_ghosts(sc_level* L, double* field, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!aligned16(field)) return set_error(SC_EINVAL, "field must be a 16-byte aligned pointer");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  Enq q{L, (cudaStream_t)stream, &L->launches, false};
+  SC_CUDA(enq_fill(q, field));
+  return SC_OK;
+}
+
+int sc_level_apply_laplacian(sc_level* L, const double* u, double* out, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!aligned16(u) || !aligned16(out))
+    return set_error(SC_EINVAL, "fields must be 16-byte aligned pointers");
+  if (u == out) return set_error(SC_EINVAL, "u and out must not overlap");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  DeviceState* D = L->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  Enq q{L, s, &L->launches, false};
+  const int nd = (int)L->doms.size();
+  if (L->arith == SC_ARITH_FIXED) {
+    SC_CUDA(cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * nd, s));
+    SC_CUDA(enq_maxexp(q, u, D->emax, true));
+  }
+  dev::LapArgs a{D->items, D->nitems, nd, D->boxes, u, out, D->inv12h2, D->emax, D->err};
+  L->launches++;
+  SC_CUDA(dev::launch_lap(L->arith, a, D->grid_stage, s));
+  return SC_OK;
+}
+
+int sc_level_rk4_step(sc_level* L, double* u, double* pi, const double* c2, const double* dt,
+                      int32_t ndt, int32_t nsteps, int32_t mode, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!aligned16(u) || !aligned16(pi) || !aligned16(c2))
+    return set_error(SC_EINVAL, "u, pi, c2 must be 16-byte aligned device pointers");
+  if (nsteps < 0) return set_error(SC_EINVAL, "nsteps < 0");
+  if (mode != SC_MODE_GRAPH && mode != SC_MODE_PER_BOX && mode != SC_MODE_BATCHED &&
+      mode != SC_MODE_TIMED)
+    return set_error(SC_EINVAL, "unknown mode");
+  if (!L->all_periodic)
+    return set_error(SC_EINVAL, "rk4_step needs domains periodic on every axis");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = set_coef(L, dt, ndt, s);
+  if (rc) return rc;
+  if (nsteps == 0) return SC_OK;
+  return run_steps(L, u, pi, c2, nsteps, mode, s);
+}
+
+int sc_level_rk4_step_host(sc_level* L, const double* u, const double* pi, const double* c2,
+                           double* u_out, double* pi_out, const double* dt, int32_t ndt,
+                           int32_t nsteps, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!u || !pi || !c2 || !u_out || !pi_out) return set_error(SC_EINVAL, "NULL host buffer");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  double *du, *dp, *dc;
+  if ((rc = get_field(L, "host.u", &du)) || (rc = get_field(L, "host.pi", &dp)) ||
+      (rc = get_field(L, "host.c2", &dc)))
+    return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * L->field_size;
+  SC_CUDA(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(dp, pi, bytes, cudaMemcpyHostToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(dc, c2, bytes, cudaMemcpyHostToDevice, s));
+  rc = sc_level_rk4_step(L, du, dp, dc, dt, ndt, nsteps, SC_MODE_GRAPH, stream);
+  if (rc) return rc;
+  SC_CUDA(cudaMemcpyAsync(u_out, du, bytes, cudaMemcpyDeviceToHost, s));
+  SC_CUDA(cudaMemcpyAsync(pi_out, dp, bytes, cudaMemcpyDeviceToHost, s));
+  return sc_level_sync(L, stream);
+}
+
+int sc_level_misfit(sc_level* L, const double* u, const double* u_obs, double* loss,
+                    double* seed, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!aligned16(u) || !aligned16(u_obs) || !loss || (seed && !aligned16(seed)))
+    return set_error(SC_EINVAL, "bad pointer");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  DeviceState* D = L->dev;
+  L->launches += 2;
+  SC_CUDA(dev::launch_misfit(D->irects, D->ichunks, D->nichunks, u, u_obs, seed, D->h3,
+                             D->partial, loss, D->grid_small, (cudaStream_t)stream));
+  return SC_OK;
+}
+
+int sc_level_sync(sc_level* L, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!L->dev) return SC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* h = reinterpret_cast<unsigned*>(L->dev->pinned) +
+                (L->dev->pinned_size / sizeof(unsigned) - 4);
+  SC_CUDA(cudaMemcpyAsync(h, L->dev->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  SC_CUDA(cudaStreamSynchronize(s));
+  const unsigned e = *h;
+  if (e) {
+    SC_CUDA(cudaMemset(L->dev->err, 0, sizeof(unsigned)));
+    std::string m = "device error word set:";
+    if (e & dev::kErrNonFinite) m += " non-finite value in the fixed-point Laplacian;";
+    if (e & dev::kErrScale) m += " input above its domain's exponent bound;";
+    return set_error(SC_EDEVICE, m);
+  }
+  return SC_OK;
+}
+
+// Forward sweep keeping a checkpoint every K steps (the tape of the level).
+int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, const double* c2,
+                          const double* dt, int32_t ndt, int32_t nsteps, int32_t ckpt_every,
+                          double* u_T, double* pi_T, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!aligned16(u0) || !aligned16(pi0) || !aligned16(c2) || (u_T && !aligned16(u_T)) ||
+      (pi_T && !aligned16(pi_T)))
+    return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
+  if (nsteps < 0 || ckpt_every < 1) return set_error(SC_EINVAL, "nsteps < 0 or ckpt_every < 1");
+  if (!L->all_periodic) return set_error(SC_EINVAL, "needs domains periodic on every axis");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  DeviceState* D = L->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = set_coef(L, dt, ndt, s);
+  if (rc) return rc;
+  const int K = ckpt_every;
+  const int nck = (nsteps + K - 1) / K;
+  const size_t bytes = sizeof(double) * L->field_size;
+  double *W[4], *Su, *Sp;
+  if ((rc = scratch4(L, W)) || (rc = get_field(L, "S.u", &Su)) ||
+      (rc = get_field(L, "S.pi", &Sp)))
+    return rc;
+  std::vector<double*> cku(nck), ckp(nck);
+  for (int c = 0; c < nck; ++c)
+    if ((rc = get_field(L, "ck.u." + std::to_string(c), &cku[c])) ||
+        (rc = get_field(L, "ck.pi." + std::to_string(c), &ckp[c])))
+      return rc;
+  L->tape_valid = false;
+  Enq q{L, s, &L->launches, false};
+  SC_CUDA(cudaMemcpyAsync(Su, u0, bytes, cudaMemcpyDeviceToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(Sp, pi0, bytes, cudaMemcpyDeviceToDevice, s));
+  for (int c = 0; c < nck; ++c) {
+    const int len = std::min(K, nsteps - c * K);
+    SC_CUDA(cudaMemcpyAsync(cku[c], Su, bytes, cudaMemcpyDeviceToDevice, s));
+    SC_CUDA(cudaMemcpyAsync(ckp[c], Sp, bytes, cudaMemcpyDeviceToDevice, s));
+    SC_CUDA(enq_prologue(q, Su));
+    for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, nullptr));
+  }
+  if (u_T) SC_CUDA(cudaMemcpyAsync(u_T, Su, bytes, cudaMemcpyDeviceToDevice, s));
+  if (pi_T) SC_CUDA(cudaMemcpyAsync(pi_T, Sp, bytes, cudaMemcpyDeviceToDevice, s));
+  L->tape_valid = true;
+  L->tape_nsteps = nsteps;
+  L->tape_ckpt = K;
+  L->tape_c2 = c2;
+  L->tape_dt = D->coef_dt;
+  return SC_OK;
+}
+
+// Reverse sweep over the tape of the last sc_level_forward_tape.
+int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
+                           const double* gpi_T, double* g_u0, double* g_pi0, double* g_c2,
+                           void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!L->tape_valid) return set_error(SC_EINVAL, "no forward tape: call sc_level_forward_tape");
+  if (c2 != L->tape_c2) return set_error(SC_EINVAL, "c2 differs from the taped forward's");
+  if (!aligned16(g_u0) || !aligned16(g_pi0) || !aligned16(g_c2) || (gu_T && !aligned16(gu_T)) ||
+      (gpi_T && !aligned16(gpi_T)))
+    return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  DeviceState* D = L->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nd = (int)L->doms.size();
+  rc = set_coef(L, L->tape_dt.data(), nd, s);
+  if (rc) return rc;
+  const int nsteps = L->tape_nsteps, K = L->tape_ckpt;
+  const int nck = (nsteps + K - 1) / K;
+  const size_t bytes = sizeof(double) * L->field_size;
+  double *W[4], *Su, *Sp, *Yu, *Yp, *Za, *Zb, *L1, *L2, *L3;
+  if ((rc = scratch4(L, W)) || (rc = get_field(L, "S.u", &Su)) ||
+      (rc = get_field(L, "S.pi", &Sp)) || (rc = get_field(L, "Y.u", &Yu)) ||
+      (rc = get_field(L, "Y.pi", &Yp)) || (rc = get_field(L, "Za", &Za)) ||
+      (rc = get_field(L, "Zb", &Zb)) || (rc = get_field(L, "L1", &L1)) ||
+      (rc = get_field(L, "L2", &L2)) || (rc = get_field(L, "L3", &L3)))
+    return rc;
+  std::vector<double*> cku(nck), ckp(nck), lapw(4 * std::min(K, std::max(nsteps, 1)));
+  for (int c = 0; c < nck; ++c)
+    if ((rc = get_field(L, "ck.u." + std::to_string(c), &cku[c])) ||
+        (rc = get_field(L, "ck.pi." + std::to_string(c), &ckp[c])))
+      return rc;
+  for (size_t j = 0; j < lapw.size(); ++j)
+    if ((rc = get_field(L, "lapw." + std::to_string(j), &lapw[j]))) return rc;
+
+  Enq q{L, s, &L->launches, false};
+  const bool fixed = L->arith == SC_ARITH_FIXED;
+  // adjoint seeds, z_4 = c2 * ybar.pi
+  if (gu_T)
+    SC_CUDA(cudaMemcpyAsync(Yu, gu_T, bytes, cudaMemcpyDeviceToDevice, s));
+  else
+    SC_CUDA(cudaMemsetAsync(Yu, 0, bytes, s));
+  if (gpi_T)
+    SC_CUDA(cudaMemcpyAsync(Yp, gpi_T, bytes, cudaMemcpyDeviceToDevice, s));
+  else
+    SC_CUDA(cudaMemsetAsync(Yp, 0, bytes, s));
+  SC_CUDA(cudaMemsetAsync(g_c2, 0, bytes, s));
+  SC_CUDA(cudaMemsetAsync(D->emax_adj, 0, sizeof(unsigned) * 4 * nd, s));
+  L->launches++;
+  SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yp, Za,
+                          fixed ? D->emax_adj : nullptr, D->grid_small, s));
+
+  auto slot = [&](int t) { return D->emax_adj + (t % 4) * nd; };
+  for (int c = nck - 1; c >= 0; --c) {
+    const int len = std::min(K, nsteps - c * K);
+    SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
+    SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
+    SC_CUDA(enq_prologue(q, Su));
+    for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, lapw.data() + 4 * n));
+    for (int n = len - 1; n >= 0; --n) {
+      double* zin[3] = {Za, Zb, Za};
+      double* zout[3] = {Zb, Za, Zb};
+      const double* lin[3] = {Yu, L3, L2};
+      double* lout[3] = {L3, L2, L1};
+      for (int t = 0; t < 3; ++t) {
+        SC_CUDA(enq_fill(q, zin[t]));
+        dev::AdjArgs a{};
+        a.items = D->items;
+        a.nitems = D->nitems;
+        a.ndom = nd;
+        a.boxes = D->boxes;
+        a.z_in = zin[t];
+        a.lam_u = lin[t];
+        a.c2 = c2;
+        a.lam_out = lout[t];
+        a.z_out = zout[t];
+        a.coef = D->coef + (3 - t) * nd;
+        a.emax_in = slot(t);
+        a.emax_out = slot(t + 1);
+        a.emax_clear = slot(t + 2);
+        a.err = D->err;
+        L->launches++;
+        SC_CUDA(dev::launch_adj_stage(L->arith, a, D->grid_stage, s));
+      }
+      SC_CUDA(enq_fill(q, Zb));
+      dev::AdjLastArgs b{};
+      b.items = D->items;
+      b.nitems = D->nitems;
+      b.ndom = nd;
+      b.boxes = D->boxes;
+      b.z_in = Zb;
+      b.l1 = L1;
+      b.l2 = L2;
+      b.l3 = L3;
+      b.yu = Yu;
+      b.yp = Yp;
+      b.c2 = c2;
+      b.lapw1 = lapw[4 * n + 0];
+      b.lapw2 = lapw[4 * n + 1];
+      b.lapw3 = lapw[4 * n + 2];
+      b.lapw4 = lapw[4 * n + 3];
+      b.c2bar = g_c2;
+      b.z_out = Za;
+      b.coef = D->coef;
+      b.emax_in = slot(3);
+      b.emax_out = slot(4);
+      b.emax_clear = slot(5);
+      b.err = D->err;
+      L->launches++;
+      SC_CUDA(dev::launch_adj_last(L->arith, b, D->grid_stage, s));
+    }
+  }
+  SC_CUDA(cudaMemcpyAsync(g_u0, Yu, bytes, cudaMemcpyDeviceToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(g_pi0, Yp, bytes, cudaMemcpyDeviceToDevice, s));
+  return SC_OK;
+}
+
+int sc_level_grad(sc_level* L, const double* u0, const double* pi0, const double* c2,
+                  const double* dt, int32_t ndt, int32_t nsteps, int32_t ckpt_every,
+                  const double* gu_T, const double* gpi_T, double* g_u0, double* g_pi0,
+                  double* g_c2, double* u_T, double* pi_T, void* stream) {
+  int rc = sc_level_forward_tape(L, u0, pi0, c2, dt, ndt, nsteps, ckpt_every, u_T, pi_T,
+                                 stream);
+  if (rc) return rc;
+  return sc_level_backward_tape(L, c2, gu_T, gpi_T, g_u0, g_pi0, g_c2, stream);
+}
+
+int sc_level_kernel_times(sc_level* L, double* stage_ms, int64_t* stage_launches,
+                          double* gather_ms, int64_t* gather_launches) {
+  if (!L || !stage_ms || !stage_launches || !gather_ms || !gather_launches)
+    return set_error(SC_EINVAL, "NULL argument");
+  *stage_ms = *gather_ms = 0.0;
+  *stage_launches = *gather_launches = 0;
+  DeviceState* D = L->dev;
+  if (!D) return SC_OK;
+  for (size_t i = 0; i < D->ev_used; ++i) {
+    SC_CUDA(cudaEventSynchronize(D->ev_pool[i].second));
+    float ms = 0.f;
+    SC_CUDA(cudaEventElapsedTime(&ms, D->ev_pool[i].first, D->ev_pool[i].second));
+    if (D->ev_kind[i] == 0) {
+      *stage_ms += ms;
+      ++*stage_launches;
+    } else if (D->ev_kind[i] == 1) {
+      *gather_ms += ms;
+      ++*gather_launches;
+    }
+  }
+  return SC_OK;
+}
+
+int sc_level_set_tuning(sc_level* L, int32_t cls, const sc_tile* t, int32_t ctas_per_sm) {
+  if (!L || !t) return set_error(SC_EINVAL, "NULL argument");
+  if (cls < 0 || cls >= (int32_t)L->classes.size()) return set_error(SC_EINVAL, "bad class");
+  const int tx = t->tile_x;
+  if (tx != 16 && tx != 32 && tx != 64 && tx != 128)
+    return set_error(SC_EINVAL, "tile_x must be 16, 32, 64 or 128");
+  if ((tx / 2) * t->tile_y != dev::stage_threads())
+    return set_error(SC_EINVAL, "tile_x/2 * tile_y must equal 256");
+  if (t->tile_z < 1) return set_error(SC_EINVAL, "tile_z must be >= 1");
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return set_error(SC_EINVAL, "ctas_per_sm in [0, 8]");
+  L->classes[cls].tile = *t;
+  L->classes[cls].tile.reserved = 0;
+  if (ctas_per_sm > 0) L->ctas_per_sm = ctas_per_sm;
+  if (L->dev) return upload_items(L);
+  return SC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bars: ghost copies bit-exact; u and pi within 1e-12 relative max norm of
+the oracle after the stated steps; decomposition independence and the three
+launch modes bit-identical; full-size checks on the 256^3 and 512x512x256
+workloads in the benchmark's launch configuration (graph mode)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1308_1343_gb300 import workloads as W
+
+from gpu_helpers import make_level, rel_err, run_gpu, upload
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1308_1343_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1308_1343_gb300 import binding
+    return binding
+
+
+def _sigma(t):
+    return (15.0 - 16.0 * np.cos(t) + np.cos(2 * t)) / 6.0
+
+
+# ----------------------------------------------------------------------------
+# ghost exchange
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("levels", [0, 2, 4])
+def test_fill_ghosts_bit_exact(orc, levels):
+    import torch
+    n = (40, 36, 24)
+    boxes = W.bisect_boxes(n, levels, 11)
+    inst = W.Instance(W.Domain(n, 0.1), np.zeros(1), np.zeros(1), np.zeros(1), 0.1,
+                      boxes=boxes)
+    lev = make_level([inst])
+    g = np.random.default_rng(levels).normal(size=(n[2], n[1], n[0]))
+    f = lev.to_device([g], fill=np.nan)
+    lev.fill_ghosts(f)
+    torch.cuda.synchronize()
+    got = lev.padded_boxes(f)
+    want = lev.padded_boxes(lev.scatter([g], fill=np.nan))
+    orc.fill_ghosts([lo + hi for lo, hi in boxes], (0, 0, 0) + n, 7, want)
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
+# ----------------------------------------------------------------------------
+# Laplacian: polynomial exactness and oracle parity, both arithmetic forms
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_laplacian_polynomial_exact(orc, arith):
+    import torch
+    from paper_1308_1343_gb300.level import Level
+    nx, ny, nz = 37, 19, 13  # ragged against every tile shape
+    h = 0.1
+    lev = Level([((0, 0, 0), (nx, ny, nz), 0)], [dict(hi=(nx, ny, nz), h=h, periodic=0)])
+    lev.set_arith(arith)
+    x = h * np.arange(-2, nx + 2) - 0.3
+    y = h * np.arange(-2, ny + 2) + 0.2
+    z = h * np.arange(-2, nz + 2) - 0.1
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    f = X ** 5 - 2 * Y ** 4 * X + Z ** 3 * Y ** 2 + X * Y * Z + 3.0
+    lap = 20 * X ** 3 - 24 * Y ** 2 * X + 2 * Z ** 3 + 6 * Z * Y ** 2
+    buf = np.full(lev.field_size, np.nan)
+    lev._box_view(buf, 0)[:] = f
+    u = torch.from_numpy(buf).cuda()
+    out = lev.new_field(np.nan)
+    lev.apply_laplacian(u, out)
+    lev.sync()
+    got = lev.gather(out)[0]
+    want = lap[2:-2, 2:-2, 2:-2]
+    assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+    ref = orc.lap_padded(f, h)
+    assert rel_err(got, ref) <= 1e-13
+
+
+# ----------------------------------------------------------------------------
+# RK4 parity
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_plane_wave_32_twenty_steps(orc, arith):
+    inst = W.plane_wave(32)
+    _, u, pi = run_gpu([inst], 20, arith, 0)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 20)
+    assert rel_err(u[0], ou) <= TOL
+    assert rel_err(pi[0], op) <= TOL
+    h, dt = inst.dom.h, inst.dt
+    mu = sum(_sigma(2 * np.pi * k * h) for k in (1, 2, 3)) / h ** 2
+    z2 = dt * dt * mu
+    a, b = 1 - z2 / 2 + z2 * z2 / 24, 1 - z2 / 6
+    M = np.array([[a, b * dt], [-b * dt * mu, a]])
+    ab = np.linalg.matrix_power(M, 20) @ np.array([1.0, 0.0])
+    assert rel_err(u[0], ab[0] * inst.u) <= TOL
+    assert rel_err(pi[0], ab[1] * inst.u) <= TOL
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_ragged_bumpy_box_all_modes(orc, arith):
+    dom = W.Domain((40, 36, 28), 1.0 / 36)
+    inst = W.bumpy_instance(dom, 2)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, dom.h, inst.dt, 6)
+    res = {}
+    for mode in (0, 1, 2):
+        _, u, pi = run_gpu([inst], 6, arith, mode)
+        assert rel_err(u[0], ou) <= TOL, mode
+        assert rel_err(pi[0], op) <= TOL, mode
+        res[mode] = (u[0], pi[0])
+    for mode in (1, 2):
+        assert np.array_equal(res[mode][0], res[0][0])
+        assert np.array_equal(res[mode][1], res[0][1])
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_uneven_level_matches_oracle_and_single_box(orc, arith):
+    inst = W.uneven_level(n=(128, 128, 64), h=1.0 / 64, levels=6, seed=3, box_seed=30)
+    assert len(inst.boxes) == 64
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 4)
+    _, u, pi = run_gpu([inst], 4, arith, 0)
+    assert rel_err(u[0], ou) <= TOL
+    assert rel_err(pi[0], op) <= TOL
+    one = W.Instance(inst.dom, inst.u, inst.pi, inst.c2, inst.dt)
+    _, u1, p1 = run_gpu([one], 4, arith, 0)
+    assert np.array_equal(u[0], u1[0]) and np.array_equal(pi[0], p1[0])
+    _, u2, p2 = run_gpu([inst], 4, arith, 1)
+    assert np.array_equal(u[0], u2[0]) and np.array_equal(pi[0], p2[0])
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_ensemble_per_domain_dt(orc, arith):
+    insts = [W.bumpy_instance(W.Domain((n, n, n), 1.0 / n), 5000 + i)
+             for i, n in enumerate((24, 32, 40, 24, 56, 48))]
+    _, u, pi = run_gpu(insts, 5, arith, 0)
+    for i, inst in enumerate(insts):
+        ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 5)
+        assert rel_err(u[i], ou) <= TOL, i
+        assert rel_err(pi[i], op) <= TOL, i
+
+
+def test_host_entry_point_matches_device_path():
+    inst = W.bumpy_instance(W.Domain((24, 20, 16), 1.0 / 20), 8)
+    lev, u, pi = run_gpu([inst], 3, 1, 0)
+    hu = lev.scatter([inst.u])
+    hp = lev.scatter([inst.pi])
+    hc = lev.scatter([inst.c2], fill=1.0)
+    ou, op = lev.rk4_step_host(hu, hp, hc, inst.dt, 3)
+    assert np.array_equal(lev.gather(ou)[0], u[0])
+    assert np.array_equal(lev.gather(op)[0], pi[0])
+
+
+def test_autotune_keeps_results(tmp_path):
+    import torch
+    inst = W.uneven_level(n=(64, 64, 32), h=1.0 / 32, levels=3, seed=3, box_seed=30)
+    lev, u0, p0 = run_gpu([inst], 3, 1, 0)
+    cache = str(tmp_path / "tune.txt")
+    lev.autotune(seed=1, budget_ms=300.0, abort_factor=2.0, cache_path=cache)
+    assert os.path.getsize(cache) > 0
+    _, u1, p1 = run_gpu([inst], 3, 1, 0, lev=lev)
+    assert np.array_equal(u0[0], u1[0]) and np.array_equal(p0[0], p1[0])
+    lev.autotune(seed=2, budget_ms=300.0, abort_factor=2.0, cache_path=cache)  # cache hit
+    torch.cuda.synchronize()
+
+
+def test_nonfinite_input_is_reported(B):
+    import torch
+    inst = W.plane_wave(16)
+    lev = make_level([inst])
+    lev.set_arith(1)
+    u = upload(lev, [inst.u])
+    u[lev.layout[0][0] + 5] = float("nan")
+    pi = upload(lev, [inst.pi])
+    c2 = upload(lev, [inst.c2], fill=1.0)
+    lev.rk4_step(u, pi, c2, inst.dt, 1)
+    with pytest.raises(B.ScError) as e:
+        lev.sync()
+    assert e.value.code == B.SC_EDEVICE
+    lev.sync()  # the error word was cleared
+    torch.cuda.synchronize()
+
+
+def test_launch_count_grows():
+    inst = W.plane_wave(16)
+    lev, _, _ = run_gpu([inst], 2, 1, 0)
+    assert lev.launch_count() >= 2 * 8
+
+
+# ----------------------------------------------------------------------------
+# full-size checks in the benchmark's launch configuration
+# ----------------------------------------------------------------------------
+
+def test_full_256_plane_wave_closed_form_100_steps():
+    inst = W.plane_wave(256)
+    _, u, pi = run_gpu([inst], 100, 1, 0)
+    h, dt = inst.dom.h, inst.dt
+    mu = sum(_sigma(2 * np.pi * k * h) for k in (1, 2, 3)) / h ** 2
+    z2 = dt * dt * mu
+    a, b = 1 - z2 / 2 + z2 * z2 / 24, 1 - z2 / 6
+    M = np.array([[a, b * dt], [-b * dt * mu, a]])
+    ab = np.linalg.matrix_power(M, 100) @ np.array([1.0, 0.0])
+    assert rel_err(u[0], ab[0] * inst.u) <= TOL
+    assert rel_err(pi[0], ab[1] * inst.u) <= TOL
+
+
+def test_full_256_bumpy_vs_oracle(orc):
+    inst = W.single_box(256, seed=2)
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 2)
+    finally:
+        orc.set_threads(1)
+    _, u, pi = run_gpu([inst], 2, 1, 0)
+    assert rel_err(u[0], ou) <= TOL
+    assert rel_err(pi[0], op) <= TOL
+
+
+def test_full_uneven_level_vs_oracle(orc):
+    inst = W.uneven_level()
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 1)
+    finally:
+        orc.set_threads(1)
+    _, u, pi = run_gpu([inst], 1, 1, 0)
+    assert rel_err(u[0], ou) <= TOL
+    assert rel_err(pi[0], op) <= TOL
