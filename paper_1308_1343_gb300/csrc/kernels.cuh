@@ -82,7 +82,9 @@ struct Fp64 {
   using T2 = double2;
   static constexpr bool kFixed = false;
   int S = 0;  // unused
-  __device__ __forceinline__ T2 conv(double2 v, unsigned&) const { return v; }
+  // m0, m1: whether each value is one the stencil may read (unused here:
+  // values outside the star are loaded but never used)
+  __device__ __forceinline__ T2 conv(double2 v, bool, bool, unsigned&) const { return v; }
   __device__ __forceinline__ static T2 zero() { return make_double2(0.0, 0.0); }
   // r = 16 s1 - s2 - 90 c: the unscaled 12 h^2 L u
   __device__ __forceinline__ static T lap(T c, T xm1, T xp1, T ym1, T yp1, T zm1, T zp1,
@@ -99,8 +101,11 @@ struct Fixed {
   using T2 = longlong2;
   static constexpr bool kFixed = true;
   int S = 0;
-  __device__ __forceinline__ T2 conv(double2 v, unsigned& err) const {
-    return make_longlong2(to_fix(v.x, S, err), to_fix(v.y, S, err));
+  // Values outside the star of the box (edge and corner points of the padded
+  // box, row padding) are never used; they are not converted, so whatever the
+  // caller left there cannot raise the error word.
+  __device__ __forceinline__ T2 conv(double2 v, bool m0, bool m1, unsigned& err) const {
+    return make_longlong2(m0 ? to_fix(v.x, S, err) : 0ll, m1 ? to_fix(v.y, S, err) : 0ll);
   }
   __device__ __forceinline__ static T2 zero() { return make_longlong2(0, 0); }
   __device__ __forceinline__ static T lap(T c, T xm1, T xp1, T ym1, T yp1, T zm1, T zp1,
@@ -151,9 +156,19 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
   const double* col = F + colOff;
   const long long pz = bx.pz;
 
+  // a point is read by some stencil iff it lies outside the interior along
+  // at most one axis, and there within the ghost width: out() is 0 inside,
+  // 1 in the ghost range [-2, 0) or [n, n+2), 2 beyond (row padding)
+  auto out = [](int c, int n) -> int {
+    return (unsigned)c < (unsigned)n ? 0 : ((c >= -2 && c < n + 2) ? 1 : 2);
+  };
+  const int oy = out(gy, bx.ny);
+  const int ox0 = out(gx, bx.nx), ox1 = out(gx + 1, bx.nx);
   auto ldcol = [&](int k) -> T2 {
     if (!colLoad) return A::zero();
-    return arith.conv(ld2(col + (long long)k * pz), err);
+    const int oz = out(k, bx.nz);
+    return arith.conv(ld2(col + (long long)k * pz), ox0 + oy + oz <= 1, ox1 + oy + oz <= 1,
+                      err);
   };
 
   T2 q0 = ldcol(it.z0 - 2), q1 = ldcol(it.z0 - 1), q2 = ldcol(it.z0), q3 = ldcol(it.z0 + 1);
@@ -181,8 +196,11 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
       }
       const int ax = it.x0 + hx, ay = it.y0 + hy;
       T2 v = A::zero();
-      if (ax < bx.nx + 2 && ay < bx.ny + 2)
-        v = arith.conv(ld2(F + bx.off + ax + (long long)ay * bx.py + (long long)k * pz), err);
+      if (ax < bx.nx + 2 && ay < bx.ny + 2) {
+        const int o = out(ay, bx.ny) + out(k, bx.nz);
+        v = arith.conv(ld2(F + bx.off + ax + (long long)ay * bx.py + (long long)k * pz),
+                       out(ax, bx.nx) + o <= 1, out(ax + 1, bx.nx) + o <= 1, err);
+      }
       *reinterpret_cast<T2*>(buf + (hy + 2) * W + hx + 2) = v;
     }
     __syncthreads();

@@ -88,8 +88,27 @@ def test_laplacian_polynomial_exact(orc, arith):
     got = lev.gather(out)[0]
     want = lap[2:-2, 2:-2, 2:-2]
     assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+    # two FP64 evaluation orders of the same 13-term sum differ by at most a
+    # few units of rounding of the sum of |terms|: bound 32 eps sum|w u|/(12h^2)
     ref = orc.lap_padded(f, h)
-    assert rel_err(got, ref) <= 1e-13
+    A = np.abs(f)
+    c = (slice(2, -2),) * 3
+    s_abs = 90 * A[c]
+    for ax in range(3):
+        for off, w in ((1, 16), (2, 1)):
+            for sgn in (-1, 1):
+                sl = [slice(2, -2)] * 3
+                sl[ax] = slice(2 + sgn * off, A.shape[ax] - 2 + sgn * off)
+                s_abs = s_abs + w * A[tuple(sl)]
+    bound = 32 * np.finfo(float).eps * s_abs / (12 * h * h)
+    if arith == 1:
+        # fixed-point form: each input is rounded to the grid 2^-S <= 2^-55 * 2M
+        # (M = max |u| over the values read), i.e. an absolute error of at
+        # most 2^-55 M per input, 192 M 2^-55 for the weighted sum
+        M = np.abs(f[2:-2, 2:-2, :]).max()
+        M = max(M, np.abs(f[2:-2, :, 2:-2]).max(), np.abs(f[:, 2:-2, 2:-2]).max())
+        bound = bound + 192 * 2.0 ** -55 * M / (12 * h * h)
+    assert np.all(np.abs(got - ref) <= bound)
 
 
 # ----------------------------------------------------------------------------
