@@ -262,6 +262,34 @@ int sc_level_kernel_times(sc_level* level, double* stage_ms, int64_t* stage_laun
  * launches count their kernel nodes).  For measurement bookkeeping. */
 int sc_level_launch_count(const sc_level* level, int64_t* n);
 
+/* ---- RK4 without device allocation --------------------------------------
+ * The paper has no counterpart of this entry point.  It serves callers that
+ * cannot allocate device memory (for example while their own allocator owns
+ * the whole device, or where cudaMalloc/cudaFree are forbidden after
+ * start-up): it advances ONE periodic box by nsteps RK4 steps (FP64 form of
+ * the stage kernel, same results as sc_level_rk4_step with SC_ARITH_FP64 on a
+ * one-box periodic level) and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its four stage arrays live in a file-scope static
+ * device array of 16 MiB (4 arrays of 2^19 doubles) that every GPU loading
+ * the library holds until the process exits.
+ *  - u, pi, c2: caller-owned DEVICE pointers, 16-byte aligned, each pointing
+ *    at the first element (ghost corner (-2,-2,-2)) of one padded box laid
+ *    out as in the level layout: row pitch py = roundup(nx+4, 16), plane
+ *    pitch pz = py*(ny+4), (nz+4) planes.  u and pi are updated in place;
+ *    their ghosts are refreshed internally; c2 is read on interior points.
+ *  - h: grid spacing; dt: step; nsteps >= 0.
+ *  - Boxes whose padded size pz*(nz+4) exceeds 2^19 doubles are rejected
+ *    with SC_EINVAL ("box too large"), as are bad pointers or sizes.
+ *  - The first call on a device resolves the static array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture on the device.
+ *  - Every call shares the one array and leaves the last call's contents in
+ *    it (nothing there needs to start at zero); calls whose work overlaps on
+ *    the GPU race with each other. */
+int sc_box_rk4_step_noalloc(double* u, double* pi, const double* c2, int32_t nx,
+                            int32_t ny, int32_t nz, double h, double dt, int32_t nsteps,
+                            void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* sc_last_error(void);
 

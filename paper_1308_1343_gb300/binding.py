@@ -74,6 +74,7 @@ _SIGS = {
     "sc_level_launch_count": (_i32, [_vp, _p64]),
     "sc_level_kernel_times": (_i32, [_vp, ctypes.POINTER(_dbl), _p64, ctypes.POINTER(_dbl),
                                      _p64]),
+    "sc_box_rk4_step_noalloc": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _dbl, _dbl, _i32, _vp]),
     "sc_last_error": (ctypes.c_char_p, []),
     "sc_bboxset_op": (_i32, [_i32, _p64, _i64, _p64, _i64, _p64, _i64, _p64]),
     "sc_bboxset_derivative": (_i32, [_p64, _i64, _p64, _i64, _p64]),
