@@ -67,10 +67,10 @@ extern "C" {
 /* ---- arithmetic of the Laplacian sum ----------------------------------- */
 /* SC_ARITH_FP64:  the 13-term sum is evaluated with FP64 adds and FMAs.
  * SC_ARITH_FIXED: each input is scaled by 2^S (S from the domain-wide
- *   maximum exponent of the field) and rounded to a 64-bit integer; the
+ *   maximum exponent of the field) and truncated to a 64-bit integer; the
  *   integer-weighted sum is then exact and is rounded once to FP64.  The
- *   per-input rounding is below 2^-55 of the domain's maximum |value|, so
- *   the error in the max norm is smaller than the FP64 sum's.  Non-finite
+ *   per-input error is below 2^-54 of the domain's maximum |value|, so
+ *   the error in the max norm is about that of the FP64 sum.  Non-finite
  *   inputs set the device error word.  The RK updates are FP64 FMAs in
  *   both modes. */
 #define SC_ARITH_FP64 0
@@ -157,7 +157,7 @@ int sc_level_set_arith(sc_level* level, int32_t arith);
 
 /* Set the tile of one size class (class index as reported by
  * sc_level_size_classes) and the persistent-grid CTAs per SM (0 = keep).
- * tile_x in {8, 16, 32, 64, 128}, tile_y such that tile_x/2*tile_y == 256,
+ * tile_x in {16, 32, 64}, tile_y such that tile_x/2*tile_y == 256,
  * tile_z >= 1.  Invalidates captured graphs. */
 int sc_level_set_tuning(sc_level* level, int32_t size_class, const sc_tile* tile,
                         int32_t ctas_per_sm);

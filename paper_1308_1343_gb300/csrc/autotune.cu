@@ -31,7 +31,7 @@ struct Cand {
   bool operator==(const Cand& o) const { return tx == o.tx && tz == o.tz; }
 };
 
-const int kTx[] = {16, 32, 64, 128};
+const int kTx[] = {16, 32, 64};
 
 std::string cache_key(const sc_level* L, const SizeClass& c) {
   std::ostringstream k;
@@ -71,7 +71,7 @@ void write_cache(const char* path, const std::map<std::string, std::pair<Cand, d
 struct Timer {
   sc_level* L;
   cudaStream_t s;
-  double* W[4];
+  double* W[6];
   double* c2;
   cudaEvent_t e0, e1;
   dev::DItem* ditems = nullptr;
@@ -120,6 +120,8 @@ struct Timer {
     a.yu = W[2];
     a.yp = W[3];
     a.c2 = c2;
+    a.q = c2;
+    a.qk = 0;
     a.wu_out = W[2];
     a.wp_out = W[3];
     a.coef = D->coef;

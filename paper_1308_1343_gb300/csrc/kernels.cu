@@ -97,6 +97,33 @@ __global__ void __launch_bounds__(256) mul_kernel(const DRect* __restrict__ rect
   }
 }
 
+// q_a = c2 * fac[2 dom], q_b = c2 * fac[2 dom + 1] on interior points: the
+// wave speed pre-scaled by dt / (12 h^2) and (dt/3) / (12 h^2) for the
+// stage kernels of one run of steps.
+__global__ void __launch_bounds__(256) qprep_kernel(const DRect* __restrict__ rects,
+                                                    const DChunk* __restrict__ chunks,
+                                                    int nchunks, const double* __restrict__ c2,
+                                                    double* qa, double* qb,
+                                                    const double* __restrict__ fac) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const DChunk ch = chunks[c];
+    const DRect r = rects[ch.rect];
+    const double fa = fac[2 * r.dom], fb = fac[2 * r.dom + 1];
+    const int n = r.ex * r.ey * r.ez;
+    const int end = min(ch.first + kChunk, n);
+    for (int p = ch.first + threadIdx.x; p < end; p += blockDim.x) {
+      const int x = p % r.ex;
+      const int t = p / r.ex;
+      const int y = t % r.ey;
+      const int z = t / r.ey;
+      const long long i = r.src + x + y * r.spy + z * r.spz;
+      const double v = c2[i];
+      qa[i] = v * fa;
+      qb[i] = v * fb;
+    }
+  }
+}
+
 // Misfit: per chunk, 1/2 sum (u - uo)^2 h^3 into partial[c] (fixed-order
 // tree), and seed = h^3 (u - uo).
 __global__ void __launch_bounds__(256) misfit_kernel(const DRect* __restrict__ rects,
@@ -158,16 +185,13 @@ __device__ __forceinline__ A make_arith(const unsigned* emax_in, int dom, unsign
   if (A::kFixed) {
     const unsigned E = emax_in[dom];
     if (E >= 0x7ffu) err |= kErrNonFinite;
-    a.S = 1077 - (int)min(E, 0x7feu);
+    // E >= 64 keeps every rescaled sum a normal number (fields below
+    // 2^-958 are then represented to 2^-1013 absolute)
+    a.E = (int)min(max(E, 64u), 0x7feu);
   }
   return a;
 }
 
-// scale of the unscaled sum r: 2^-S for the fixed form, 1 otherwise
-template <class A>
-__device__ __forceinline__ double unscale(const A& a, double x) {
-  return A::kFixed ? ldexp(x, -a.S) : x;
-}
 
 __device__ __forceinline__ void clear_slot(unsigned* slot, int ndom) {
   if (slot && blockIdx.x == 0)
@@ -178,41 +202,37 @@ __device__ __forceinline__ void clear_slot(unsigned* slot, int ndom) {
 // Forward stage: w_out = (y.u + g w_in.pi, y.pi + g c2 L w_in.u)
 // ---------------------------------------------------------------------------
 
-template <bool FIXED, bool RECORD>
+template <class A, bool RECORD>
 struct FwdEpi {
-  const double* __restrict__ wp_in;
-  const double* yu;
-  const double* yp;
-  const double* __restrict__ c2;
+  static constexpr int NF = 4;  // w_in.pi, y.u, y.pi, q (= c2 dt / (12 h^2), pre-scaled)
+  const double* f[NF];
   double* wu_out;
   double* wp_out;
   double* __restrict__ lapw;
-  double g, kap, lw;
-  double2 wp, u0, p0, c;
+  A arith;
+  int qk;          // stage factor 2^qk applied to q (1/4, 1/2, 1; 1/3 lives in q)
+  double g, lw;    // g_s; L w scale for recording
   unsigned emax;
 
-  __device__ __forceinline__ void prefetch(long long i) {
-    wp = ld2(wp_in + i);
-    u0 = ld2(yu + i);
-    p0 = ld2(yp + i);
-    c = ld2(c2 + i);
-  }
-  __device__ __forceinline__ void point(long long i, double rA, double rB, bool, bool actB) {
+  __device__ __forceinline__ void point(long long i, const double2* pw, typename A::T rA,
+                                        typename A::T rB, bool actB) {
+    const double2 wp = pw[0], u0 = pw[1], p0 = pw[2], q = pw[3];
+    const double dA = arith.scaled(rA, qk), dB = arith.scaled(rB, qk);
     double2 un, pn;
     un.x = fma(g, wp.x, u0.x);
     un.y = fma(g, wp.y, u0.y);
-    pn.x = fma(kap, c.x * rA, p0.x);
-    pn.y = fma(kap, c.y * rB, p0.y);
+    pn.x = fma(q.x, dA, p0.x);
+    pn.y = fma(q.y, dB, p0.y);
     if (actB) {
       st2(wu_out + i, un);
       st2(wp_out + i, pn);
-      if (RECORD) st2(lapw + i, make_double2(rA * lw, rB * lw));
+      if (RECORD) st2(lapw + i, make_double2(dA * lw, dB * lw));
     } else {
       wu_out[i] = un.x;
       wp_out[i] = pn.x;
-      if (RECORD) lapw[i] = rA * lw;
+      if (RECORD) lapw[i] = dA * lw;
     }
-    if (FIXED) {
+    if (A::kFixed) {
       emax = max(emax, biased_exp(un.x));
       if (actB) emax = max(emax, biased_exp(un.y));
     }
@@ -220,8 +240,8 @@ struct FwdEpi {
 };
 
 template <class A, bool RECORD>
-__global__ void __launch_bounds__(NT) fwd_stage_kernel(FwdArgs a) {
-  __shared__ __align__(16) typename A::T smem[2 * TileSmem<NT>::kMaxElems];
+__global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
+  __shared__ Smem<NT, A, 4> smem;
   __shared__ unsigned red[NT / 32];
   if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
   unsigned err = 0;
@@ -230,9 +250,8 @@ __global__ void __launch_bounds__(NT) fwd_stage_kernel(FwdArgs a) {
     const DBox bx = a.boxes[it.box];
     const StageCoef cf = a.coef[bx.dom];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    FwdEpi<A::kFixed, RECORD> epi{a.wp_in, a.yu, a.yp, a.c2, a.wu_out, a.wp_out, a.lapw,
-                                  cf.gamma, unscale(arith, cf.kappa),
-                                  unscale(arith, cf.inv12h2)};
+    FwdEpi<A, RECORD> epi{{a.wp_in, a.yu, a.yp, a.q}, a.wu_out, a.wp_out, a.lapw, arith,
+                          a.qk, cf.gamma, cf.inv12h2 * exp2_int(-a.qk)};
     epi.emax = 0;
     run_item<NT>(it, bx, a.wu_in, arith, smem, err, epi);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
@@ -244,27 +263,32 @@ __global__ void __launch_bounds__(NT) fwd_stage_kernel(FwdArgs a) {
 // out = L u
 // ---------------------------------------------------------------------------
 
+template <class A>
 struct LapEpi {
+  static constexpr int NF = 0;
+  const double* f[1];
   double* out;
+  A arith;
   double lw;
-  __device__ __forceinline__ void prefetch(long long) {}
-  __device__ __forceinline__ void point(long long i, double rA, double rB, bool, bool actB) {
+  __device__ __forceinline__ void point(long long i, const double2*, typename A::T rA,
+                                        typename A::T rB, bool actB) {
+    const double dA = arith.scaled(rA, 0) * lw, dB = arith.scaled(rB, 0) * lw;
     if (actB)
-      st2(out + i, make_double2(rA * lw, rB * lw));
+      st2(out + i, make_double2(dA, dB));
     else
-      out[i] = rA * lw;
+      out[i] = dA;
   }
 };
 
 template <class A>
-__global__ void __launch_bounds__(NT) lap_kernel(LapArgs a) {
-  __shared__ __align__(16) typename A::T smem[2 * TileSmem<NT>::kMaxElems];
+__global__ void __launch_bounds__(NT, 4) lap_kernel(LapArgs a) {
+  __shared__ Smem<NT, A, 0> smem;
   unsigned err = 0;
   for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
     const DItem it = a.items[i];
     const DBox bx = a.boxes[it.box];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    LapEpi epi{a.out, unscale(arith, a.inv12h2[bx.dom])};
+    LapEpi<A> epi{{nullptr}, a.out, arith, a.inv12h2[bx.dom]};
     run_item<NT>(it, bx, a.u, arith, smem, err, epi);
   }
   if (err) atomicOr(a.err, err);
@@ -283,21 +307,19 @@ __global__ void __launch_bounds__(NT) lap_kernel(LapArgs a) {
 // for the next (earlier) step.
 // ---------------------------------------------------------------------------
 
-template <bool FIXED>
+template <class A>
 struct AdjEpi {
-  const double* __restrict__ lam_u;
-  const double* __restrict__ c2;
+  static constexpr int NF = 2;  // lam_s.u, c2
+  const double* f[NF];
   double* __restrict__ lam_out;
   double* __restrict__ z_out;
+  A arith;
   double g, kap;
-  double2 l, c;
   unsigned emax;
-  __device__ __forceinline__ void prefetch(long long i) {
-    l = ld2(lam_u + i);
-    c = ld2(c2 + i);
-  }
-  __device__ __forceinline__ void point(long long i, double rA, double rB, bool, bool actB) {
-    const double2 lo = make_double2(kap * rA, kap * rB);
+  __device__ __forceinline__ void point(long long i, const double2* pw, typename A::T rA,
+                                        typename A::T rB, bool actB) {
+    const double2 l = pw[0], c = pw[1];
+    const double2 lo = make_double2(kap * arith.scaled(rA, 0), kap * arith.scaled(rB, 0));
     const double2 zo = make_double2(c.x * (g * l.x), c.y * (g * l.y));
     if (actB) {
       st2(lam_out + i, lo);
@@ -306,7 +328,7 @@ struct AdjEpi {
       lam_out[i] = lo.x;
       z_out[i] = zo.x;
     }
-    if (FIXED) {
+    if (A::kFixed) {
       emax = max(emax, biased_exp(zo.x));
       if (actB) emax = max(emax, biased_exp(zo.y));
     }
@@ -314,8 +336,8 @@ struct AdjEpi {
 };
 
 template <class A>
-__global__ void __launch_bounds__(NT) adj_stage_kernel(AdjArgs a) {
-  __shared__ __align__(16) typename A::T smem[2 * TileSmem<NT>::kMaxElems];
+__global__ void __launch_bounds__(NT, 4) adj_stage_kernel(AdjArgs a) {
+  __shared__ Smem<NT, A, 2> smem;
   __shared__ unsigned red[NT / 32];
   if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
   unsigned err = 0;
@@ -324,8 +346,7 @@ __global__ void __launch_bounds__(NT) adj_stage_kernel(AdjArgs a) {
     const DBox bx = a.boxes[it.box];
     const StageCoef cf = a.coef[bx.dom];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    AdjEpi<A::kFixed> epi{a.lam_u, a.c2, a.lam_out, a.z_out, cf.gamma,
-                          unscale(arith, cf.kappa)};
+    AdjEpi<A> epi{{a.lam_u, a.c2}, a.lam_out, a.z_out, arith, cf.gamma, cf.kappa};
     epi.emax = 0;
     run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
@@ -333,11 +354,10 @@ __global__ void __launch_bounds__(NT) adj_stage_kernel(AdjArgs a) {
   if (err) atomicOr(a.err, err);
 }
 
-template <bool FIXED>
+template <class A>
 struct AdjLastEpi {
-  const double* __restrict__ l1;
-  const double* __restrict__ l2;
-  const double* __restrict__ l3;
+  static constexpr int NF = 4;  // lam_1.u, lam_2.u, lam_3.u, lam_4.u (streamed)
+  const double* f[NF];
   double* yu;
   double* yp;
   const double* __restrict__ c2;
@@ -347,20 +367,9 @@ struct AdjLastEpi {
   const double* __restrict__ w4;  // L w_3.u  (forward stage 4)
   double* cb;
   double* __restrict__ z_out;
+  A arith;
   double g1, g2, g3, g4, kap1;
-  double2 a1, a2, a3, u4, p4;
   unsigned emax;
-  __device__ __forceinline__ void prefetch(long long i) {
-    a1 = ld2(l1 + i);
-    a2 = ld2(l2 + i);
-    a3 = ld2(l3 + i);
-    u4 = ld2(yu + i);
-    p4 = ld2(yp + i);
-  }
-  __device__ __forceinline__ double2 combine_u(double2 l0) const {
-    return make_double2(((u4.x + a3.x) + (a2.x + a1.x)) + l0.x,
-                        ((u4.y + a3.y) + (a2.y + a1.y)) + l0.y);
-  }
   __device__ __forceinline__ double pi_one(double p, double u, double b3, double b2,
                                            double b1) const {
     return p + fma(g4, u, fma(g3, b3, fma(g2, b2, g1 * b1)));
@@ -370,9 +379,13 @@ struct AdjLastEpi {
     // g4 lam4.pi Lw3 + g3 (g4 lam4.u) Lw2 + g2 (g3 lam3.u) Lw1 + g1 (g2 lam2.u) Lw0
     return fma(g4 * p, q4, fma(g3 * (g4 * u), q3, fma(g2 * (g3 * b3), q2, g1 * (g2 * b2) * q1)));
   }
-  __device__ __forceinline__ void point(long long i, double rA, double rB, bool, bool actB) {
-    const double2 l0 = make_double2(kap1 * rA, kap1 * rB);
-    const double2 un = combine_u(l0);
+  __device__ __forceinline__ void point(long long i, const double2* pw, typename A::T rA,
+                                        typename A::T rB, bool actB) {
+    const double2 a1 = pw[0], a2 = pw[1], a3 = pw[2], u4 = pw[3];
+    const double2 p4 = ld2(yp + i);
+    const double2 l0 = make_double2(kap1 * arith.scaled(rA, 0), kap1 * arith.scaled(rB, 0));
+    const double2 un = make_double2(((u4.x + a3.x) + (a2.x + a1.x)) + l0.x,
+                                    ((u4.y + a3.y) + (a2.y + a1.y)) + l0.y);
     const double2 pn = make_double2(pi_one(p4.x, u4.x, a3.x, a2.x, a1.x),
                                     pi_one(p4.y, u4.y, a3.y, a2.y, a1.y));
     const double2 q4 = ld2(w4 + i), q3 = ld2(w3 + i), q2 = ld2(w2 + i), q1 = ld2(w1 + i);
@@ -393,7 +406,7 @@ struct AdjLastEpi {
       cb[i] = cn.x;
       z_out[i] = zo.x;
     }
-    if (FIXED) {
+    if (A::kFixed) {
       emax = max(emax, biased_exp(zo.x));
       if (actB) emax = max(emax, biased_exp(zo.y));
     }
@@ -402,7 +415,7 @@ struct AdjLastEpi {
 
 template <class A>
 __global__ void __launch_bounds__(NT) adj_last_kernel(AdjLastArgs a) {
-  __shared__ __align__(16) typename A::T smem[2 * TileSmem<NT>::kMaxElems];
+  __shared__ Smem<NT, A, 4> smem;
   __shared__ unsigned red[NT / 32];
   if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
   unsigned err = 0;
@@ -411,11 +424,11 @@ __global__ void __launch_bounds__(NT) adj_last_kernel(AdjLastArgs a) {
     const DBox bx = a.boxes[it.box];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
     const int d = bx.dom, nd = a.ndom;
-    AdjLastEpi<A::kFixed> epi{a.l1, a.l2, a.l3, a.yu, a.yp, a.c2, a.lapw1, a.lapw2,
-                              a.lapw3, a.lapw4, a.c2bar, a.z_out,
+    AdjLastEpi<A> epi{{a.l1, a.l2, a.l3, a.yu}, a.yu, a.yp, a.c2, a.lapw1, a.lapw2,
+                      a.lapw3, a.lapw4, a.c2bar, a.z_out, arith,
                               a.coef[0 * nd + d].gamma, a.coef[1 * nd + d].gamma,
                               a.coef[2 * nd + d].gamma, a.coef[3 * nd + d].gamma,
-                              unscale(arith, a.coef[0 * nd + d].kappa)};
+                      a.coef[0 * nd + d].kappa};
     epi.emax = 0;
     run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
@@ -454,6 +467,14 @@ cudaError_t launch_mul(const DRect* rects, const DChunk* chunks, int nchunks, co
   return cudaGetLastError();
 }
 
+cudaError_t launch_qprep(const DRect* rects, const DChunk* chunks, int nchunks,
+                         const double* c2, double* qa, double* qb, const double* fac, int grid,
+                         cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  qprep_kernel<<<min(grid, nchunks), 256, 0, s>>>(rects, chunks, nchunks, c2, qa, qb, fac);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
                           const double* u, const double* uo, double* seed, const double* h3,
                           double* partial, double* loss, int grid, cudaStream_t s) {
@@ -464,9 +485,33 @@ cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
   return cudaGetLastError();
 }
 
+// Four 46 KB CTAs per SM need the largest shared-memory carveout.
+template <class K>
+void prefer_shared(K kernel) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+}
+
+static void set_carveouts() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  prefer_shared(fwd_stage_kernel<Fixed, true>);
+  prefer_shared(fwd_stage_kernel<Fixed, false>);
+  prefer_shared(fwd_stage_kernel<Fp64, true>);
+  prefer_shared(fwd_stage_kernel<Fp64, false>);
+  prefer_shared(adj_stage_kernel<Fixed>);
+  prefer_shared(adj_stage_kernel<Fp64>);
+  prefer_shared(adj_last_kernel<Fixed>);
+  prefer_shared(adj_last_kernel<Fp64>);
+  prefer_shared(lap_kernel<Fixed>);
+  prefer_shared(lap_kernel<Fp64>);
+}
+
 cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
                              cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
+  set_carveouts();
   grid = min(grid, a.nitems);
   if (arith == 1) {
     if (record)
@@ -484,6 +529,7 @@ cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
 
 cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
+  set_carveouts();
   grid = min(grid, a.nitems);
   if (arith == 1)
     lap_kernel<Fixed><<<grid, NT, 0, s>>>(a);
@@ -494,6 +540,7 @@ cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_adj_stage(int arith, const AdjArgs& a, int grid, cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
+  set_carveouts();
   grid = min(grid, a.nitems);
   if (arith == 1)
     adj_stage_kernel<Fixed><<<grid, NT, 0, s>>>(a);
@@ -515,6 +562,7 @@ cudaError_t launch_adj_last(int arith, const AdjLastArgs& a, int grid, cudaStrea
 int stage_threads() { return NT; }
 
 cudaError_t stage_occupancy(int arith, int* blocks_per_sm) {
+  set_carveouts();
   if (arith == 1)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         blocks_per_sm, fwd_stage_kernel<Fixed, false>, NT, 0);

@@ -13,18 +13,24 @@
 // the paper's masked iteration does for vector tails (Sec. 4.3): points
 // outside the box are loaded only where they are ghosts, and never stored.
 //
+// Latency hiding is a one-plane software pipeline: while plane k is
+// computed, the column value of plane k+3 and the halo of plane k+1 are in
+// flight to registers, and the pointwise fields of plane k+1 are in flight
+// to shared memory by cp.async (no registers held); nothing loaded in an
+// iteration is consumed in the same iteration.
+//
 // The Laplacian's 13-point integer-weighted sum has two arithmetic forms:
 //  * Fp64:  FP64 adds and FMAs.
-//  * Fixed: every input x is first rounded to the integer round(x * 2^S),
-//    with S = 1077 - E and E the largest biased exponent of the field on
-//    the box's domain, so |x| * 2^S < 2^55; the weighted sum (weights
-//    16, -1, -90; sum of |weights| = 192 < 2^8) is then exact in int64 and
-//    is rounded to FP64 once.  This moves the sum from GB300's narrow FP64
-//    pipe to the integer pipes; only the RK updates stay FP64 FMAs.
+//  * Fixed: every input x is first turned into the integer
+//    trunc(x * 2^S), S = 1077 - E, with E the largest biased exponent of
+//    the field on the box's domain, so |x| * 2^S < 2^55; the weighted sum
+//    (weights 16, -1, -90; sum of |weights| = 192 < 2^8) is then exact in
+//    int64 and is rounded to FP64 once.  Each input is off by less than
+//    2^-S <= 2^-54 * max|x|.  This moves the sum from GB300's narrow FP64
+//    pipe to the integer pipes; the RK updates stay FP64 FMAs.
 #pragma once
 
 #include <cstdint>
-#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "descriptors.hpp"
@@ -42,35 +48,55 @@ __device__ __forceinline__ double2 ld2(const double* p) {
 __device__ __forceinline__ void st2(double* p, double2 v) {
   *reinterpret_cast<double2*>(p) = v;
 }
-// Streaming load for data read once in this pass.
-__device__ __forceinline__ double2 ld2_stream(const double* p) {
-  return __ldcs(reinterpret_cast<const double2*>(p));
-}
 
 __device__ __forceinline__ unsigned biased_exp(double x) {
   return (unsigned)((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
-// round(x * 2^S) for |x| < 2^(E-1022), S = 1077 - E, without FP64
-// instructions: unpack the significand and shift it into place (round half
-// away from zero).  Zero and subnormal inputs give 0.  An input above the
-// domain bound (shift > 2) is clamped and flagged.
-__device__ __forceinline__ long long to_fix(double x, int S, unsigned& err) {
+// 16-byte asynchronous global -> shared copy (bypasses L1)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// wait until at most one committed group of this thread is still pending
+__device__ __forceinline__ void cp_async_wait_one() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// 64-bit logical right shift whose amount saturates: >= 64 gives 0.
+__device__ __forceinline__ unsigned long long shr_sat(unsigned long long v, unsigned r) {
+  unsigned long long d;
+  asm("shr.b64 %0, %1, %2;" : "=l"(d) : "l"(v), "r"(r));
+  return d;
+}
+
+// trunc(x * 2^S), S = 1077 - E, for |x| < 2^(E-1022), with integer
+// instructions only and no branches: the significand, shifted left by 2, is
+// shifted right by E - e (e the exponent of x), so an input with e == E
+// lands just below 2^55.  Zero and subnormal inputs give 0, and so does any
+// input with use == false (values the stencil never reads).  An input above
+// the domain bound (e > E) is clamped and flags kErrScale.
+__device__ __forceinline__ long long to_fix(double x, int E, bool use, unsigned& err) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-  const int sh = e + S - 1075;
-  unsigned long long v;
-  if (sh >= 0) {
-    if (sh > 2) err |= kErrScale;
-    v = m << (sh > 2 ? 2 : sh);
-  } else {
-    const int r = -sh;
-    v = r >= 64 ? 0ull : (((m >> (r - 1)) + 1ull) >> 1);
-  }
-  if (e == 0) v = 0ull;
-  const long long s = (long long)v;
-  return (long long)(b >> 63) ? -s : s;
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned long long m = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2;
+  const int r = E - e;
+  err |= (use && r < 0) ? kErrScale : 0u;
+  const long long v = (long long)shr_sat(m, (unsigned)max(r, 0));
+  const long long z = (use && e != 0) ? v : 0ll;
+  return (hi >> 31) ? -z : z;
+}
+
+// 2^k as a double for -1022 <= k <= 1023
+__device__ __forceinline__ double exp2_int(int k) {
+  return __longlong_as_double((long long)(1023 + k) << 52);
 }
 
 // ---------------------------------------------------------------------------
@@ -81,7 +107,7 @@ struct Fp64 {
   using T = double;
   using T2 = double2;
   static constexpr bool kFixed = false;
-  int S = 0;  // unused
+  int E = 0;  // unused
   // m0, m1: whether each value is one the stencil may read (unused here:
   // values outside the star are loaded but never used)
   __device__ __forceinline__ T2 conv(double2 v, bool, bool, unsigned&) const { return v; }
@@ -94,53 +120,79 @@ struct Fp64 {
     return fma(-90.0, c, fma(16.0, s1, -s2));
   }
   __device__ __forceinline__ static double to_double(T r) { return r; }
+  // r * 2^(k - S) with S = 0: an exact power-of-two multiply
+  __device__ __forceinline__ double scaled(T r, int k) const { return r * exp2_int(k); }
 };
 
 struct Fixed {
   using T = long long;
   using T2 = longlong2;
   static constexpr bool kFixed = true;
-  int S = 0;
+  int E = 0;  // domain exponent bound of the stencil field
   // Values outside the star of the box (edge and corner points of the padded
   // box, row padding) are never used; they are not converted, so whatever the
   // caller left there cannot raise the error word.
   __device__ __forceinline__ T2 conv(double2 v, bool m0, bool m1, unsigned& err) const {
-    return make_longlong2(m0 ? to_fix(v.x, S, err) : 0ll, m1 ? to_fix(v.y, S, err) : 0ll);
+    return make_longlong2(to_fix(v.x, E, m0, err), to_fix(v.y, E, m1, err));
   }
   __device__ __forceinline__ static T2 zero() { return make_longlong2(0, 0); }
   __device__ __forceinline__ static T lap(T c, T xm1, T xp1, T ym1, T yp1, T zm1, T zp1,
                                           T xm2, T xp2, T ym2, T yp2, T zm2, T zp2) {
-    const long long s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
-    const long long s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
+    const long long s1 = xm1 + xp1 + ym1 + yp1 + zm1 + zp1;
+    const long long s2 = xm2 + xp2 + ym2 + yp2 + zm2 + zp2;
     return s1 * 16 - s2 - c * 90;
   }
   __device__ __forceinline__ static double to_double(T r) { return __ll2double_rn(r); }
+  // r * 2^(k - S) rounded once: the conversion's exponent is adjusted on the
+  // integer pipe (E >= 64 keeps it normal for every |r| >= 1).
+  __device__ __forceinline__ double scaled(T r, int k) const {
+    const long long bits = __double_as_longlong(__ll2double_rn(r)) +
+                           ((long long)(k - (1077 - E)) << 52);
+    return r == 0 ? 0.0 : __longlong_as_double(bits);
+  }
 };
 
 // ---------------------------------------------------------------------------
 // The traversal
 // ---------------------------------------------------------------------------
 
-// Shared-memory tile: two buffers of (TX+4) x (TY+4) values, TX = 2*txh,
-// TY = NT/txh, txh in {8, 16, 32, 64}; the extreme shapes bound the size.
+// Shared memory of one CTA: two (TX+4) x (TY+4) stencil tiles, TX = 2*txh,
+// TY = NT/txh, txh in {8, 16, 32} (the 64 x 8 tile bounds the size), and
+// two planes of NF pointwise fields (one 16-byte pair per thread and field).
 template <int NT>
 struct TileSmem {
-  static constexpr int kA = (2 * 64 + 4) * (NT / 64 + 4);
+  static constexpr int kA = (2 * 32 + 4) * (NT / 32 + 4);
   static constexpr int kB = (2 * 8 + 4) * (NT / 8 + 4);
   static constexpr int kMaxElems = kA > kB ? kA : kB;
 };
 
-// Walk one work item.  `F` is the stencil field (its ghosts filled).  For
-// every plane k, epi.prefetch(idx) is called first (idx = element index of
-// this thread's first point on plane k), then epi.point(idx, rA, rB, actA,
-// actB) with the unscaled sums r = 12 h^2 (L F) at both points, converted to
-// double.
+template <int NT, class A, int NF>
+struct Smem {
+  typename A::T tile[2 * TileSmem<NT>::kMaxElems];
+  double2 pw[2][NF > 0 ? NF : 1][NT];
+};
+
+// a point is read by some stencil iff it lies outside the interior along at
+// most one axis, and there within the ghost width: 0 inside, 1 in the ghost
+// range [-2, 0) or [n, n+2), 2 beyond (row padding)
+__device__ __forceinline__ int out_of(int c, int n) {
+  return (unsigned)c < (unsigned)n ? 0 : ((c >= -2 && c < n + 2) ? 1 : 2);
+}
+
+// Walk one work item.  `F` is the stencil field (its ghosts filled).  The
+// epilogue names Epi::NF pointwise fields (epi.f[0..NF)) that the traversal
+// streams into shared memory; for every plane k it calls
+//   epi.point(idx, pw, rA, rB, actB)
+// on the threads owning interior points, with idx the element index of the
+// thread's first point, pw[f] its pair of field f, and rA, rB the unscaled
+// sums r = 12 h^2 (L F) at both points in the policy's integer or FP64 form.
 template <int NT, class A, class Epi>
 __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
                                          const double* __restrict__ F, A arith,
-                                         typename A::T* smem, unsigned& err, Epi& epi) {
+                                         Smem<NT, A, Epi::NF>& sm, unsigned& err, Epi& epi) {
   using T = typename A::T;
   using T2 = typename A::T2;
+  constexpr int NF = Epi::NF;
   const int txh = it.txh;
   const int TY = NT / txh;
   const int TX = 2 * txh;
@@ -152,57 +204,94 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
   const bool colLoad = (gx < bx.nx + 2) && (gy < bx.ny + 2);
   const bool actA = (gx < bx.nx) && (gy < bx.ny);
   const bool actB = (gx + 1 < bx.nx) && (gy < bx.ny);
-  const long long colOff = bx.off + gx + (long long)gy * bx.py;
-  const double* col = F + colOff;
   const long long pz = bx.pz;
+  // element index of the thread's pair on plane 0; columns outside the
+  // padded box read the box's interior corner instead (in bounds, masked
+  // off below, never used)
+  const long long colOff = colLoad ? bx.off + gx + (long long)gy * bx.py : bx.off;
+  const int oy = out_of(gy, bx.ny);
+  const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
 
-  // a point is read by some stencil iff it lies outside the interior along
-  // at most one axis, and there within the ghost width: out() is 0 inside,
-  // 1 in the ghost range [-2, 0) or [n, n+2), 2 beyond (row padding)
-  auto out = [](int c, int n) -> int {
-    return (unsigned)c < (unsigned)n ? 0 : ((c >= -2 && c < n + 2) ? 1 : 2);
-  };
-  const int oy = out(gy, bx.ny);
-  const int ox0 = out(gx, bx.nx), ox1 = out(gx + 1, bx.nx);
-  auto ldcol = [&](int k) -> T2 {
-    if (!colLoad) return A::zero();
-    const int oz = out(k, bx.nz);
-    return arith.conv(ld2(col + (long long)k * pz), ox0 + oy + oz <= 1, ox1 + oy + oz <= 1,
-                      err);
-  };
-
-  T2 q0 = ldcol(it.z0 - 2), q1 = ldcol(it.z0 - 1), q2 = ldcol(it.z0), q3 = ldcol(it.z0 + 1);
+  // this thread's halo pair of the plane tile, if any (at most one: the
+  // halo of a tile has 4 txh + 2 TY <= NT pairs for every allowed shape)
   const int nhalo = 4 * txh + 2 * TY;
-  const int rowSelf = (ly + 2) * W + 2 * lx + 2;
-
-  for (int kk = 0; kk < it.nzr; ++kk) {
-    const int k = it.z0 + kk;
-    const T2 q4 = ldcol(k + 2);
-    const long long idx = colOff + (long long)k * pz;
-    if (actA) epi.prefetch(idx);
-    T* buf = smem + (kk & 1) * bufElems;
-    *reinterpret_cast<T2*>(buf + rowSelf) = q2;
-    for (int h = tid; h < nhalo; h += NT) {
-      int hx, hy;
-      if (h < 4 * txh) {
-        const int r = h / txh;
-        hx = 2 * (h - r * txh);
-        hy = r < 2 ? r - 2 : TY + r - 2;
-      } else {
-        const int j = h - 4 * txh;
-        const int side = j / TY;
-        hy = j - side * TY;
-        hx = side ? TX : -2;
-      }
-      const int ax = it.x0 + hx, ay = it.y0 + hy;
-      T2 v = A::zero();
-      if (ax < bx.nx + 2 && ay < bx.ny + 2) {
-        const int o = out(ay, bx.ny) + out(k, bx.nz);
-        v = arith.conv(ld2(F + bx.off + ax + (long long)ay * bx.py + (long long)k * pz),
-                       out(ax, bx.nx) + o <= 1, out(ax + 1, bx.nx) + o <= 1, err);
-      }
-      *reinterpret_cast<T2*>(buf + (hy + 2) * W + hx + 2) = v;
+  const bool hasH = tid < nhalo;
+  int hs = 0;                 // smem index of the pair
+  long long hg = bx.off;      // element index of the pair on plane 0
+  int hx0 = 2, hx1 = 2;       // outside counts (>= 2: masked off)
+  if (hasH) {
+    int hx, hy;
+    if (tid < 4 * txh) {
+      const int r = tid / txh;
+      hx = 2 * (tid - r * txh);
+      hy = r < 2 ? r - 2 : TY + r - 2;
+    } else {
+      const int j = tid - 4 * txh;
+      const int side = j / TY;
+      hy = j - side * TY;
+      hx = side ? TX : -2;
     }
+    const int ax = it.x0 + hx, ay = it.y0 + hy;
+    hs = (hy + 2) * W + hx + 2;
+    if (ax < bx.nx + 2 && ay < bx.ny + 2) {
+      hg = bx.off + ax + (long long)ay * bx.py;
+      const int o = out_of(ay, bx.ny);
+      hx0 = out_of(ax, bx.nx) + o;
+      hx1 = out_of(ax + 1, bx.nx) + o;
+    }
+  }
+  auto conv_at = [&](double2 raw, int k) -> T2 {
+    const int oz = out_of(k, bx.nz);
+    return arith.conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
+  };
+
+  // running element offsets (advance by one plane per iteration)
+  long long oc = colOff + (long long)(it.z0 + 2) * pz;  // next column load
+  long long oh = hg + (long long)it.z0 * pz;            // next halo load
+  long long op = colOff + (long long)it.z0 * pz;        // next pointwise stage
+  long long oi = op;                                    // current plane
+  auto stage_pw = [&](int buf) {
+    if (actA) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cp_async16(&sm.pw[buf][f][tid], epi.f[f] + op);
+    }
+    cp_async_commit();
+    op += pz;
+  };
+
+  T2 qa = conv_at(ld2(F + oc - 4 * pz), it.z0 - 2);
+  T2 qb = conv_at(ld2(F + oc - 3 * pz), it.z0 - 1);
+  T2 qc = conv_at(ld2(F + oc - 2 * pz), it.z0);
+  T2 qd = conv_at(ld2(F + oc - pz), it.z0 + 1);
+  T2 qe;
+  double2 rc = ld2(F + oc);  // raw column of plane k+2
+  oc += pz;
+  double2 rh = ld2(F + oh);  // raw halo pair of plane k
+  oh += pz;
+  stage_pw(0);
+
+  const int rowSelf = (ly + 2) * W + 2 * lx + 2;
+  // one plane: m2..p1 hold planes k-2..k+1; p2 receives plane k+2
+  auto plane = [&](int kk, const T2& m2, const T2& m1, const T2& c0, const T2& p1, T2& p2) {
+    const int k = it.z0 + kk;
+    p2 = conv_at(rc, k + 2);
+    T* buf = sm.tile + (kk & 1) * bufElems;
+    *reinterpret_cast<T2*>(buf + rowSelf) = c0;
+    if (hasH) {
+      const int oz = out_of(k, bx.nz);
+      *reinterpret_cast<T2*>(buf + hs) = arith.conv(rh, hx0 + oz <= 1, hx1 + oz <= 1, err);
+    }
+    // issue the next plane's loads before waiting on this one
+    if (kk + 1 < it.nzr) {
+      rc = ld2(F + oc);
+      oc += pz;
+      rh = ld2(F + oh);
+      oh += pz;
+      stage_pw((kk + 1) & 1);
+    } else {
+      cp_async_commit();
+    }
+    cp_async_wait_one();
     __syncthreads();
     if (actA) {
       const T* row = buf + rowSelf;
@@ -213,17 +302,31 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
       const T2 yp1 = *reinterpret_cast<const T2*>(row + W);
       const T2 yp2 = *reinterpret_cast<const T2*>(row + 2 * W);
       // point A at x, point B at x+1
-      const T rA = A::lap(q2.x, xm.y, q2.y, ym1.x, yp1.x, q1.x, q3.x,
-                          xm.x, xp.x, ym2.x, yp2.x, q0.x, q4.x);
-      const T rB = A::lap(q2.y, q2.x, xp.x, ym1.y, yp1.y, q1.y, q3.y,
-                          xm.y, xp.y, ym2.y, yp2.y, q0.y, q4.y);
-      epi.point(idx, A::to_double(rA), A::to_double(rB), actA, actB);
+      const T rA = A::lap(c0.x, xm.y, c0.y, ym1.x, yp1.x, m1.x, p1.x,
+                          xm.x, xp.x, ym2.x, yp2.x, m2.x, p2.x);
+      const T rB = A::lap(c0.y, c0.x, xp.x, ym1.y, yp1.y, m1.y, p1.y,
+                          xm.y, xp.y, ym2.y, yp2.y, m2.y, p2.y);
+      double2 pw[NF > 0 ? NF : 1];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) pw[f] = sm.pw[kk & 1][f][tid];
+      epi.point(oi, pw, rA, rB, actB);
     }
-    q0 = q1;
-    q1 = q2;
-    q2 = q3;
-    q3 = q4;
+    oi += pz;
+  };
+  // unrolled by the queue length so the five z-values never move
+  for (int kk = 0;;) {
+    plane(kk, qa, qb, qc, qd, qe);
+    if (++kk >= it.nzr) break;
+    plane(kk, qb, qc, qd, qe, qa);
+    if (++kk >= it.nzr) break;
+    plane(kk, qc, qd, qe, qa, qb);
+    if (++kk >= it.nzr) break;
+    plane(kk, qd, qe, qa, qb, qc);
+    if (++kk >= it.nzr) break;
+    plane(kk, qe, qa, qb, qc, qd);
+    if (++kk >= it.nzr) break;
   }
+  cp_async_wait_all();
   __syncthreads();  // the next item reuses the buffers
 }
 

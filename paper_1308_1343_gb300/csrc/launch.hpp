@@ -32,6 +32,8 @@ struct FwdArgs {
   double* wu_out;
   double* wp_out;
   double* lapw;  // recorded L w_in.u (adjoint checkpoints) or nullptr
+  const double* q;  // c2 dt/(12 h^2) or c2 (dt/3)/(12 h^2), pre-scaled per run
+  int qk;           // stage factor 2^qk on q
   const StageCoef* coef;  // [ndom] of this stage
   const unsigned* emax_in;
   unsigned* emax_out;
@@ -101,6 +103,9 @@ cudaError_t launch_maxexp(const DRect* rects, const DChunk* chunks, int nchunks,
 cudaError_t launch_mul(const DRect* rects, const DChunk* chunks, int nchunks, const double* a,
                        const double* b, double* out, unsigned* emax, int grid,
                        cudaStream_t s);
+cudaError_t launch_qprep(const DRect* rects, const DChunk* chunks, int nchunks,
+                         const double* c2, double* qa, double* qb, const double* fac, int grid,
+                         cudaStream_t s);
 cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
                           const double* u, const double* uo, double* seed, const double* h3,
                           double* partial, double* loss, int grid, cudaStream_t s);

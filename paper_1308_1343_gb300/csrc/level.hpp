@@ -22,7 +22,7 @@ int set_error(int code, const std::string& msg);
 int ensure_device(sc_level* L);
 int get_field(sc_level* L, const std::string& name, double** p);
 int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s);
-int scratch4(sc_level* L, double* W[4]);
+int scratch4(sc_level* L, double* W[6]);
 int upload_items(sc_level* L);
 
 struct SizeClass {
@@ -59,6 +59,7 @@ struct DeviceState {
   dev::StageCoef* coef = nullptr;  // [4][ndom]
   std::vector<double> coef_dt;     // dt per domain the coefficients were built for
   double* inv12h2 = nullptr;       // [ndom]
+  double* qfac = nullptr;          // [ndom][2]: dt/(12 h^2), (dt/3)/(12 h^2)
   double* h3 = nullptr;            // [ndom]
   unsigned* emax = nullptr;        // forward ring [4][ndom]
   unsigned* emax_adj = nullptr;    // adjoint ring [4][ndom]

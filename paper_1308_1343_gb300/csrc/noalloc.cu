@@ -77,21 +77,14 @@ __global__ void __launch_bounds__(256) noalloc_fill_kernel(double* f, dev::DBox 
 }
 
 struct NoAllocEpi {
-  const double* wp_in;
-  const double* yu;
-  const double* yp;
-  const double* c2;
+  static constexpr int NF = 4;  // w_in.pi, y.u, y.pi, c2
+  const double* f[NF];
   double* wu_out;
   double* wp_out;
   double g, kap;
-  double2 wp, u0, p0, c;
-  __device__ __forceinline__ void prefetch(long long i) {
-    wp = dev::ld2(wp_in + i);
-    u0 = dev::ld2(yu + i);
-    p0 = dev::ld2(yp + i);
-    c = dev::ld2(c2 + i);
-  }
-  __device__ __forceinline__ void point(long long i, double rA, double rB, bool, bool actB) {
+  __device__ __forceinline__ void point(long long i, const double2* pw, double rA, double rB,
+                                        bool actB) {
+    const double2 wp = pw[0], u0 = pw[1], p0 = pw[2], c = pw[3];
     double2 un, pn;
     un.x = fma(g, wp.x, u0.x);
     un.y = fma(g, wp.y, u0.y);
@@ -109,10 +102,10 @@ struct NoAllocEpi {
 
 // One nested-RK4 stage over the box; work items are derived from the block
 // index instead of being read from a list.
-__global__ void __launch_bounds__(kNT) noalloc_stage_kernel(
+__global__ void __launch_bounds__(kNT, 4) noalloc_stage_kernel(
     dev::DBox bx, int txh, int tz, const double* wu_in, const double* wp_in, const double* yu,
     const double* yp, const double* c2, double* wu_out, double* wp_out, double g, double kap) {
-  __shared__ __align__(16) double smem[2 * dev::TileSmem<kNT>::kMaxElems];
+  __shared__ dev::Smem<kNT, dev::Fp64, 4> smem;
   const int tx = 2 * txh, ty = kNT / txh;
   const int ntx = (bx.nx + tx - 1) / tx, nty = (bx.ny + ty - 1) / ty, ntz = (bx.nz + tz - 1) / tz;
   const int nitems = ntx * nty * ntz;
@@ -120,7 +113,7 @@ __global__ void __launch_bounds__(kNT) noalloc_stage_kernel(
   for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
     const int ix = i % ntx, iy = (i / ntx) % nty, iz = i / (ntx * nty);
     dev::DItem it{0, ix * tx, iy * ty, iz * tz, min(tz, bx.nz - iz * tz), txh};
-    NoAllocEpi epi{wp_in, yu, yp, c2, wu_out, wp_out, g, kap};
+    NoAllocEpi epi{{wp_in, yu, yp, c2}, wu_out, wp_out, g, kap};
     dev::run_item<kNT>(it, bx, wu_in, dev::Fp64{}, smem, err, epi);
   }
 }

@@ -94,7 +94,7 @@ void release_device(sc_level* L) {
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
   void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->irects, D->ichunks,
-                  D->srects, D->schunks, D->coef, D->inv12h2, D->h3, D->emax,
+                  D->srects, D->schunks, D->coef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -222,6 +222,7 @@ int ensure_device(sc_level* L) {
   if (!rc) rc = upload(&D->h3, h3);
   if (rc) return rc;
   SC_CUDA(cudaMalloc(&D->coef, sizeof(StageCoef) * 4 * nd));
+  SC_CUDA(cudaMalloc(&D->qfac, sizeof(double) * 2 * nd));
   SC_CUDA(cudaMalloc(&D->emax, sizeof(unsigned) * 4 * nd));
   SC_CUDA(cudaMalloc(&D->emax_adj, sizeof(unsigned) * 4 * nd));
   SC_CUDA(cudaMemset(D->emax, 0, sizeof(unsigned) * 4 * nd));
@@ -229,7 +230,7 @@ int ensure_device(sc_level* L) {
   SC_CUDA(cudaMalloc(&D->err, sizeof(unsigned)));
   SC_CUDA(cudaMemset(D->err, 0, sizeof(unsigned)));
   SC_CUDA(cudaMalloc(&D->partial, sizeof(double) * std::max(1, D->nichunks)));
-  D->pinned_size = sizeof(StageCoef) * 4 * nd + 64;
+  D->pinned_size = sizeof(StageCoef) * 4 * nd + sizeof(double) * 2 * nd + 64;
   SC_CUDA(cudaMallocHost(&D->pinned, D->pinned_size));
   return upload_items(L);
 }
@@ -276,6 +277,13 @@ int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s) {
       h[st * nd + d] = StageCoef{g, g / (12.0 * hh * hh), 1.0 / (12.0 * hh * hh), 0.0};
     }
   SC_CUDA(cudaMemcpyAsync(D->coef, h, sizeof(StageCoef) * 4 * nd, cudaMemcpyHostToDevice, s));
+  double* qf = reinterpret_cast<double*>(h + 4 * nd);
+  for (int d = 0; d < nd; ++d) {
+    const double hh = L->doms[d].h;
+    qf[2 * d] = want[d] / (12.0 * hh * hh);
+    qf[2 * d + 1] = (want[d] / 3.0) / (12.0 * hh * hh);
+  }
+  SC_CUDA(cudaMemcpyAsync(D->qfac, qf, sizeof(double) * 2 * nd, cudaMemcpyHostToDevice, s));
   D->coef_dt = want;
   return SC_OK;
 }
@@ -370,6 +378,10 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
                             double* const* W, double* const* lapw) {
   DeviceState* D = q.L->dev;
   const int nd = (int)q.L->doms.size();
+  // stage factors c_s = 1/4, 1/3, 1/2, 1: powers of two fold into the
+  // exponent of the Laplacian; 1/3 is in the second pre-scaled array
+  const double* qarr[4] = {W[4], W[5], W[4], W[4]};
+  const int qk[4] = {-2, 0, -1, 0};
   double* in_u[4] = {u, W[0], W[2], W[0]};
   double* in_p[4] = {pi, W[1], W[3], W[1]};
   double* out_u[4] = {W[0], W[2], W[0], u};
@@ -388,6 +400,8 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
     a.wu_out = out_u[s];
     a.wp_out = out_p[s];
     a.lapw = lapw ? lapw[s] : nullptr;
+    a.q = qarr[s];
+    a.qk = qk[s];
     a.coef = D->coef + s * nd;
     a.emax_in = D->emax + (s % 4) * nd;
     a.emax_out = D->emax + ((s + 1) % 4) * nd;
@@ -399,20 +413,26 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
   return cudaSuccess;
 }
 
-// Exponent prologue of a run of fixed-point steps: ring cleared, slot 0 =
-// max exponent of u.
-static cudaError_t enq_prologue(const Enq& q, const double* u) {
-  if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
+// Prologue of a run of steps: the pre-scaled wave speed q = c2 * dt/(12 h^2)
+// (and the 1/3 variant) in W[4], W[5]; for the fixed form, the exponent ring
+// cleared and slot 0 = max exponent of u.
+static cudaError_t enq_prologue(const Enq& q, const double* u, const double* c2,
+                                double* const* W) {
   DeviceState* D = q.L->dev;
-  cudaError_t e =
-      cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
+  (*q.count)++;
+  cudaError_t e = dev::launch_qprep(D->irects, D->ichunks, D->nichunks, c2, W[4], W[5],
+                                    D->qfac, D->grid_small, q.s);
+  if (e != cudaSuccess) return e;
+  if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
+  e = cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
   if (e != cudaSuccess) return e;
   return enq_maxexp(q, u, D->emax, false);
 }
 
-int scratch4(sc_level* L, double* W[4]) {
-  const char* names[4] = {"Wa.u", "Wa.pi", "Wb.u", "Wb.pi"};
-  for (int i = 0; i < 4; ++i) {
+// Stage scratch: Wa.u, Wa.pi, Wb.u, Wb.pi and the two pre-scaled wave speeds.
+int scratch4(sc_level* L, double* W[6]) {
+  const char* names[6] = {"Wa.u", "Wa.pi", "Wb.u", "Wb.pi", "q.a", "q.b"};
+  for (int i = 0; i < 6; ++i) {
     int rc = get_field(L, names[i], &W[i]);
     if (rc) return rc;
   }
@@ -422,7 +442,7 @@ int scratch4(sc_level* L, double* W[4]) {
 static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int nsteps, int mode,
                      cudaStream_t s) {
   DeviceState* D = L->dev;
-  double* W[4];
+  double* W[6];
   int rc = scratch4(L, W);
   if (rc) return rc;
   Enq q{L, s, &L->launches, mode == SC_MODE_PER_BOX};
@@ -431,7 +451,7 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     D->ev_used = 0;
     D->ev_kind.clear();
   }
-  SC_CUDA(enq_prologue(q, u));
+  SC_CUDA(enq_prologue(q, u, c2, W));
   if (mode != SC_MODE_GRAPH) {
     for (int n = 0; n < nsteps; ++n) SC_CUDA(enq_step(q, u, pi, c2, W, nullptr));
     return SC_OK;
@@ -598,7 +618,7 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
   const int K = ckpt_every;
   const int nck = (nsteps + K - 1) / K;
   const size_t bytes = sizeof(double) * L->field_size;
-  double *W[4], *Su, *Sp;
+  double *W[6], *Su, *Sp;
   if ((rc = scratch4(L, W)) || (rc = get_field(L, "S.u", &Su)) ||
       (rc = get_field(L, "S.pi", &Sp)))
     return rc;
@@ -615,7 +635,7 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(cku[c], Su, bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(ckp[c], Sp, bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su));
+    SC_CUDA(enq_prologue(q, Su, c2, W));
     for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, nullptr));
   }
   if (u_T) SC_CUDA(cudaMemcpyAsync(u_T, Su, bytes, cudaMemcpyDeviceToDevice, s));
@@ -648,7 +668,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
   const int nsteps = L->tape_nsteps, K = L->tape_ckpt;
   const int nck = (nsteps + K - 1) / K;
   const size_t bytes = sizeof(double) * L->field_size;
-  double *W[4], *Su, *Sp, *Yu, *Yp, *Za, *Zb, *L1, *L2, *L3;
+  double *W[6], *Su, *Sp, *Yu, *Yp, *Za, *Zb, *L1, *L2, *L3;
   if ((rc = scratch4(L, W)) || (rc = get_field(L, "S.u", &Su)) ||
       (rc = get_field(L, "S.pi", &Sp)) || (rc = get_field(L, "Y.u", &Yu)) ||
       (rc = get_field(L, "Y.pi", &Yp)) || (rc = get_field(L, "Za", &Za)) ||
@@ -685,7 +705,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su));
+    SC_CUDA(enq_prologue(q, Su, c2, W));
     for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, lapw.data() + 4 * n));
     for (int n = len - 1; n >= 0; --n) {
       double* zin[3] = {Za, Zb, Za};
@@ -782,8 +802,8 @@ int sc_level_set_tuning(sc_level* L, int32_t cls, const sc_tile* t, int32_t ctas
   if (!L || !t) return set_error(SC_EINVAL, "NULL argument");
   if (cls < 0 || cls >= (int32_t)L->classes.size()) return set_error(SC_EINVAL, "bad class");
   const int tx = t->tile_x;
-  if (tx != 16 && tx != 32 && tx != 64 && tx != 128)
-    return set_error(SC_EINVAL, "tile_x must be 16, 32, 64 or 128");
+  if (tx != 16 && tx != 32 && tx != 64)
+    return set_error(SC_EINVAL, "tile_x must be 16, 32 or 64");
   if ((tx / 2) * t->tile_y != dev::stage_threads())
     return set_error(SC_EINVAL, "tile_x/2 * tile_y must equal 256");
   if (t->tile_z < 1) return set_error(SC_EINVAL, "tile_z must be >= 1");

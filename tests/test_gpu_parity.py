@@ -102,12 +102,12 @@ def test_laplacian_polynomial_exact(orc, arith):
                 s_abs = s_abs + w * A[tuple(sl)]
     bound = 32 * np.finfo(float).eps * s_abs / (12 * h * h)
     if arith == 1:
-        # fixed-point form: each input is rounded to the grid 2^-S <= 2^-55 * 2M
-        # (M = max |u| over the values read), i.e. an absolute error of at
-        # most 2^-55 M per input, 192 M 2^-55 for the weighted sum
+        # fixed-point form: each input is truncated to the grid 2^-S <= 2^-54 M
+        # (M = max |u| over the values read), i.e. an absolute error below
+        # 2^-54 M per input, 192 M 2^-54 for the weighted sum
         M = np.abs(f[2:-2, 2:-2, :]).max()
         M = max(M, np.abs(f[2:-2, :, 2:-2]).max(), np.abs(f[:, 2:-2, 2:-2]).max())
-        bound = bound + 192 * 2.0 ** -55 * M / (12 * h * h)
+        bound = bound + 192 * 2.0 ** -54 * M / (12 * h * h)
     assert np.all(np.abs(got - ref) <= bound)
 
 
