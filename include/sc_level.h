@@ -123,7 +123,7 @@ typedef struct sc_tile {
  * the bboxset algebra and builds the exchange lists; device state is created
  * on the first call that takes a stream).  ghost must be 2.  Every box must
  * lie in its domain, have edges >= 2, and the boxes of each domain must tile
- * it exactly.  On success *out owns the level (free with sc_level_destroy).
+ * it exactly; one field of the level must hold fewer than 2^31 doubles.  On success *out owns the level (free with sc_level_destroy).
  * Errors: SC_EINVAL (message names the offending box), SC_ENOMEM. */
 int sc_level_create(const sc_box* boxes, int32_t nboxes, const sc_domain* doms,
                     int32_t ndoms, int32_t ghost, sc_level** out);

@@ -77,19 +77,23 @@ struct Timer {
   dev::DItem* ditems = nullptr;
   size_t cap = 0;
 
-  // Items of the boxes of class `cls` with tile (tx, tz); returns the count.
+  // Items of the whole level with the current tiles, except class `cls`
+  // which gets (tx, tz): the candidate is timed in the launch it will run in
+  // (coordinate descent over the classes).  Returns the item count.
   int stage(int cls, const Cand& c) {
     std::vector<dev::DItem> items;
     for (size_t b = 0; b < L->boxes.size(); ++b) {
-      if (L->box_class[b] != cls) continue;
       const sc_box& B = L->boxes[b];
       const int nx = (int)(B.hi[0] - B.lo[0]), ny = (int)(B.hi[1] - B.lo[1]),
                 nz = (int)(B.hi[2] - B.lo[2]);
-      const int ty = 2 * dev_threads() / c.tx;
-      for (int z0 = 0; z0 < nz; z0 += c.tz)
+      const bool mine = L->box_class[b] == cls;
+      const int tx = mine ? c.tx : L->classes[L->box_class[b]].tile.tile_x;
+      const int tz = mine ? c.tz : L->classes[L->box_class[b]].tile.tile_z;
+      const int ty = 2 * dev_threads() / tx;
+      for (int z0 = 0; z0 < nz; z0 += tz)
         for (int y0 = 0; y0 < ny; y0 += ty)
-          for (int x0 = 0; x0 < nx; x0 += c.tx)
-            items.push_back(dev::DItem{(int)b, x0, y0, z0, std::min(c.tz, nz - z0), c.tx / 2});
+          for (int x0 = 0; x0 < nx; x0 += tx)
+            items.push_back(dev::DItem{(int)b, x0, y0, z0, std::min(tz, nz - z0), tx / 2});
     }
     if (items.size() > cap) {
       if (ditems) cudaFree(ditems);
@@ -103,8 +107,8 @@ struct Timer {
   }
   static int dev_threads() { return dev::stage_threads(); }
 
-  // Median time (microseconds) of one stage launch over the class's items;
-  // gives up after the first run if it exceeds `limit`.
+  // Median time (microseconds) of one stage launch over the level's items;
+  // gives up after the second run if it exceeds `limit`.
   double time(int cls, const Cand& c, double limit) {
     const int n = stage(cls, c);
     if (n <= 0) return 1e30;
@@ -189,6 +193,7 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
       C.tile.tile_x = hit->second.first.tx;
       C.tile.tile_y = 2 * dev::stage_threads() / hit->second.first.tx;
       C.tile.tile_z = hit->second.first.tz;
+      C.fixed = true;
       changed = true;
       continue;
     }
@@ -254,6 +259,7 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
     C.tile.tile_x = best.tx;
     C.tile.tile_y = 2 * dev::stage_threads() / best.tx;
     C.tile.tile_z = best.tz;
+    C.fixed = true;
     cache[key] = {best, tbest};
     changed = true;
   }

@@ -214,7 +214,7 @@ struct FwdEpi {
   double g, lw;    // g_s; L w scale for recording
   unsigned emax;
 
-  __device__ __forceinline__ void point(long long i, const double2* pw, typename A::T rA,
+  __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
                                         typename A::T rB, bool actB) {
     const double2 wp = pw[0], u0 = pw[1], p0 = pw[2], q = pw[3];
     const double dA = arith.scaled(rA, qk), dB = arith.scaled(rB, qk);
@@ -270,7 +270,7 @@ struct LapEpi {
   double* out;
   A arith;
   double lw;
-  __device__ __forceinline__ void point(long long i, const double2*, typename A::T rA,
+  __device__ __forceinline__ void point(int i, const double2*, typename A::T rA,
                                         typename A::T rB, bool actB) {
     const double dA = arith.scaled(rA, 0) * lw, dB = arith.scaled(rB, 0) * lw;
     if (actB)
@@ -316,7 +316,7 @@ struct AdjEpi {
   A arith;
   double g, kap;
   unsigned emax;
-  __device__ __forceinline__ void point(long long i, const double2* pw, typename A::T rA,
+  __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
                                         typename A::T rB, bool actB) {
     const double2 l = pw[0], c = pw[1];
     const double2 lo = make_double2(kap * arith.scaled(rA, 0), kap * arith.scaled(rB, 0));
@@ -379,7 +379,7 @@ struct AdjLastEpi {
     // g4 lam4.pi Lw3 + g3 (g4 lam4.u) Lw2 + g2 (g3 lam3.u) Lw1 + g1 (g2 lam2.u) Lw0
     return fma(g4 * p, q4, fma(g3 * (g4 * u), q3, fma(g2 * (g3 * b3), q2, g1 * (g2 * b2) * q1)));
   }
-  __device__ __forceinline__ void point(long long i, const double2* pw, typename A::T rA,
+  __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
                                         typename A::T rB, bool actB) {
     const double2 a1 = pw[0], a2 = pw[1], a3 = pw[2], u4 = pw[3];
     const double2 p4 = ld2(yp + i);

@@ -79,19 +79,19 @@ __device__ __forceinline__ unsigned long long shr_sat(unsigned long long v, unsi
 // trunc(x * 2^S), S = 1077 - E, for |x| < 2^(E-1022), with integer
 // instructions only and no branches: the significand, shifted left by 2, is
 // shifted right by E - e (e the exponent of x), so an input with e == E
-// lands just below 2^55.  Zero and subnormal inputs give 0, and so does any
-// input with use == false (values the stencil never reads).  An input above
-// the domain bound (e > E) is clamped and flags kErrScale.
+// lands just below 2^55.  Inputs with use == false (values the stencil never
+// reads) get a shift of 64 and give 0; so do zero and subnormal inputs
+// (e == 0, and E >= 64 is guaranteed by the caller).  An input above the
+// domain bound (e > E) is clamped and flags kErrScale.
 __device__ __forceinline__ long long to_fix(double x, int E, bool use, unsigned& err) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(b >> 32);
   const int e = (int)((hi >> 20) & 0x7ffu);
   const unsigned long long m = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2;
-  const int r = E - e;
-  err |= (use && r < 0) ? kErrScale : 0u;
+  const int r = use ? E - e : 64;
+  err |= r < 0 ? kErrScale : 0u;
   const long long v = (long long)shr_sat(m, (unsigned)max(r, 0));
-  const long long z = (use && e != 0) ? v : 0ll;
-  return (hi >> 31) ? -z : z;
+  return (hi >> 31) ? -v : v;
 }
 
 // 2^k as a double for -1022 <= k <= 1023
@@ -204,11 +204,12 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
   const bool colLoad = (gx < bx.nx + 2) && (gy < bx.ny + 2);
   const bool actA = (gx < bx.nx) && (gy < bx.ny);
   const bool actB = (gx + 1 < bx.nx) && (gy < bx.ny);
-  const long long pz = bx.pz;
-  // element index of the thread's pair on plane 0; columns outside the
-  // padded box read the box's interior corner instead (in bounds, masked
-  // off below, never used)
-  const long long colOff = colLoad ? bx.off + gx + (long long)gy * bx.py : bx.off;
+  const int pz = (int)bx.pz;
+  // element index of the thread's pair on plane 0 (32-bit: a field holds
+  // fewer than 2^31 doubles); columns outside the padded box read the box's
+  // interior corner instead (in bounds, masked off below, never used)
+  const int off0 = (int)bx.off, py = (int)bx.py;
+  const int colOff = colLoad ? off0 + gx + gy * py : off0;
   const int oy = out_of(gy, bx.ny);
   const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
 
@@ -217,7 +218,7 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
   const int nhalo = 4 * txh + 2 * TY;
   const bool hasH = tid < nhalo;
   int hs = 0;                 // smem index of the pair
-  long long hg = bx.off;      // element index of the pair on plane 0
+  int hg = off0;              // element index of the pair on plane 0
   int hx0 = 2, hx1 = 2;       // outside counts (>= 2: masked off)
   if (hasH) {
     int hx, hy;
@@ -234,7 +235,7 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
     const int ax = it.x0 + hx, ay = it.y0 + hy;
     hs = (hy + 2) * W + hx + 2;
     if (ax < bx.nx + 2 && ay < bx.ny + 2) {
-      hg = bx.off + ax + (long long)ay * bx.py;
+      hg = off0 + ax + ay * py;
       const int o = out_of(ay, bx.ny);
       hx0 = out_of(ax, bx.nx) + o;
       hx1 = out_of(ax + 1, bx.nx) + o;
@@ -246,10 +247,10 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
   };
 
   // running element offsets (advance by one plane per iteration)
-  long long oc = colOff + (long long)(it.z0 + 2) * pz;  // next column load
-  long long oh = hg + (long long)it.z0 * pz;            // next halo load
-  long long op = colOff + (long long)it.z0 * pz;        // next pointwise stage
-  long long oi = op;                                    // current plane
+  int oc = colOff + (it.z0 + 2) * pz;  // next column load
+  int oh = hg + it.z0 * pz;            // next halo load
+  int op = colOff + it.z0 * pz;        // next pointwise stage
+  int oi = op;                         // current plane
   auto stage_pw = [&](int buf) {
     if (actA) {
 #pragma unroll

@@ -28,6 +28,7 @@ int upload_items(sc_level* L);
 struct SizeClass {
   std::array<int64_t, 3> ext;  // interior extent rounded up to a multiple of 8
   sc_tile tile;
+  bool fixed = false;          // tile set by sc_level_set_tuning / autotune
 };
 
 // Device-side state, created lazily on the first call that takes a stream.

@@ -216,6 +216,10 @@ int sc_level_create(const sc_box* boxes, int32_t nboxes, const sc_domain* doms, 
       base += st;
     }
     L->field_size = base + 2;
+    if (L->field_size >= (int64_t(1) << 31)) {
+      delete L;
+      return set_error(SC_EINVAL, "level too large: a field must hold fewer than 2^31 doubles");
+    }
     build_exchange(L);
     build_classes(L);
   } catch (const std::bad_alloc&) {

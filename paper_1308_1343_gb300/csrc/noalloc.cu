@@ -82,7 +82,7 @@ struct NoAllocEpi {
   double* wu_out;
   double* wp_out;
   double g, kap;
-  __device__ __forceinline__ void point(long long i, const double2* pw, double rA, double rB,
+  __device__ __forceinline__ void point(int i, const double2* pw, double rA, double rB,
                                         bool actB) {
     const double2 wp = pw[0], u0 = pw[1], p0 = pw[2], c = pw[3];
     double2 un, pn;

@@ -65,15 +65,29 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
 
 int upload_items(sc_level* L) {
   DeviceState* D = L->dev;
-  std::vector<DItem> items;
-  build_items(L, items, D->box_items);
-  int rc = upload(&D->items, items);
-  if (rc) return rc;
-  D->nitems = (int)items.size();
   int occ = 0;
   SC_CUDA(dev::stage_occupancy(L->arith, &occ));
   const int per_sm = L->ctas_per_sm > 0 ? L->ctas_per_sm : std::max(1, occ);
   D->grid_stage = D->sms * per_sm;
+  std::vector<DItem> items;
+  build_items(L, items, D->box_items);
+  // heuristic first choice (the paper's initial parameters, Sec. 3.2): while
+  // the level's items do not fill two waves of the persistent grid, halve the
+  // z-run of every class whose tile was not set explicitly
+  for (;;) {
+    if ((int)items.size() >= 2 * D->grid_stage) break;
+    bool any = false;
+    for (auto& c : L->classes)
+      if (!c.fixed && c.tile.tile_z > 4) {
+        c.tile.tile_z /= 2;
+        any = true;
+      }
+    if (!any) break;
+    build_items(L, items, D->box_items);
+  }
+  int rc = upload(&D->items, items);
+  if (rc) return rc;
+  D->nitems = (int)items.size();
   for (auto& kv : D->graphs) cudaGraphExecDestroy(kv.second.first);
   D->graphs.clear();
   L->version++;
@@ -810,6 +824,7 @@ int sc_level_set_tuning(sc_level* L, int32_t cls, const sc_tile* t, int32_t ctas
   if (ctas_per_sm < 0 || ctas_per_sm > 8) return set_error(SC_EINVAL, "ctas_per_sm in [0, 8]");
   L->classes[cls].tile = *t;
   L->classes[cls].tile.reserved = 0;
+  L->classes[cls].fixed = true;
   if (ctas_per_sm > 0) L->ctas_per_sm = ctas_per_sm;
   if (L->dev) return upload_items(L);
   return SC_OK;
