@@ -39,6 +39,8 @@ BYTES_PER_POINT_STAGE = BYTES_PER_POINT_STEP / 4
 # FP64 pipe instructions per point per stage (FP64 form): 10 adds + 2 FMAs
 # for the sum, 1 multiply by c2, 2 update FMAs
 FP64_OPS_PER_POINT_STAGE = {"fp64": 15, "fixed": 3}
+# run-time tuning results (tile per box-size class) are cached here between runs
+TUNE_CACHE = os.path.join(ROOT, "paper_1308_1343_gb300", "_build", "tune_cache.txt")
 
 
 def _args():
@@ -216,6 +218,8 @@ def _extras(torch, W, B, Level, arith, stream):
     inst = W.uneven_level()
     lev = Level.from_instances([inst])
     lev.set_arith(arith)
+    lev.autotune(seed=3, budget_ms=3000.0, abort_factor=2.0, cache_path=TUNE_CACHE,
+                 stream=stream)
     u, pi = lev.to_device([inst.u]), lev.to_device([inst.pi])
     c2 = lev.to_device([inst.c2], fill=1.0)
     n = inst.u.size
@@ -244,8 +248,8 @@ def _extras(torch, W, B, Level, arith, stream):
     c2 = lev.to_device([i.c2 for i in insts], fill=1.0)
     dts = [i.dt for i in insts]
     n = sum(i.u.size for i in insts)
-    lev.autotune(seed=5, budget_ms=3000.0, abort_factor=2.0,
-                 cache_path=os.path.join(ROOT, "paper_1308_1343_gb300", "_build", "tune_cache.txt"), stream=stream)
+    lev.autotune(seed=5, budget_ms=3000.0, abort_factor=2.0, cache_path=TUNE_CACHE,
+                 stream=stream)
     _time_steps(torch, lev, u, pi, c2, dts, 5, B.SC_MODE_GRAPH, 1, stream)
     t = _time_steps(torch, lev, u, pi, c2, dts, 100, B.SC_MODE_GRAPH, 1, stream)
     out["ensemble"] = {"workload": "256 periodic cubes, edges 24..96, own c2 and pulse, "
@@ -258,6 +262,8 @@ def _extras(torch, W, B, Level, arith, stream):
     inst = W.gradient_problem(128, 4)
     lev = Level.from_instances([inst])
     lev.set_arith(arith)
+    lev.autotune(seed=4, budget_ms=2000.0, abort_factor=2.0, cache_path=TUNE_CACHE,
+                 stream=stream)
     u0, pi0 = lev.to_device([inst.u]), lev.to_device([inst.pi])
     c2 = lev.to_device([inst.c2], fill=1.0)
     u = u0.clone()
@@ -280,10 +286,23 @@ def _extras(torch, W, B, Level, arith, stream):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
     lev.sync(stream)
+    # where the backward's device time goes (separate, event-timed pass)
+    lev.set_profiling(True)
+    lev.forward_tape(u0, pi0, c2, inst.dt, 200, 20, uT, None, stream=stream)
+    lev.backward_tape(c2, seed, None, g[0], g[1], g[2], stream=stream)
+    torch.cuda.synchronize()
+    names = {B.SC_KERNEL_STAGE_RECORD: "stage_record", B.SC_KERNEL_GATHER: "gather",
+             B.SC_KERNEL_ADJ_A: "adj_a", B.SC_KERNEL_ADJ_B: "adj_b", B.SC_KERNEL_ADJ_C: "adj_combine"}
+    kern = {}
+    for k, name in names.items():
+        ms, n = lev.kernel_time(k)
+        kern[name] = {"ms": ms, "launches": n}
+    lev.set_profiling(False)
     out["adjoint"] = {"workload": "128^3 periodic box, 200 RK4 steps, checkpoints every 20",
                       "t_forward_s": t_fwd, "t_forward_tape_s": t1 - t0,
                       "t_backward_s": t2 - t1, "ratio_backward_over_forward": (t2 - t1) / t_fwd,
-                      "ratio_total_over_forward": (t2 - t0) / t_fwd}
+                      "ratio_total_over_forward": (t2 - t0) / t_fwd,
+                      "backward_kernels": kern}
     return out
 
 
@@ -307,6 +326,8 @@ def run_ours(a, ws, rank, local):
     npts = inst.u.size
     lev = Level.from_instances([inst])
     lev.set_arith(arith)
+    lev.autotune(seed=2, budget_ms=2000.0, abort_factor=2.0, cache_path=TUNE_CACHE,
+                 stream=stream)
     u0 = lev.to_device([inst.u])
     pi0 = lev.to_device([inst.pi])
     c2 = lev.to_device([inst.c2], fill=1.0)

@@ -252,11 +252,27 @@ int sc_level_grad(sc_level* level, const double* u0, const double* pi0,
 /* Wait for the stream and report any device error word (SC_EDEVICE). */
 int sc_level_sync(sc_level* level, void* stream);
 
-/* Per-kernel device times of the last sc_level_rk4_step call made with
- * SC_MODE_TIMED: summed CUDA-event durations and launch counts of the stage
- * kernel and of the ghost gather.  Waits for those events. */
+/* Kernel kinds for per-kernel timing. */
+#define SC_KERNEL_STAGE 0        /* forward stage kernel                     */
+#define SC_KERNEL_GATHER 1       /* ghost gather                             */
+#define SC_KERNEL_STAGE_RECORD 2 /* forward stage kernel recording L w.u     */
+#define SC_KERNEL_ADJ_A 3        /* adjoint: L(c2 .) with c2 product output  */
+#define SC_KERNEL_ADJ_B 4        /* adjoint: L(c2 .)                          */
+#define SC_KERNEL_ADJ_C 5        /* adjoint: pointwise combination           */
+
+/* Per-kernel device times of the last timed call: sc_level_rk4_step with
+ * SC_MODE_TIMED, or sc_level_forward_tape / sc_level_backward_tape while
+ * profiling is on.  Each launch of those calls is bracketed by CUDA events
+ * on the stream; these return the summed durations and launch counts of one
+ * kernel kind (SC_KERNEL_*), or of the stage kernel and the gather.  Wait
+ * for those events. */
+int sc_level_kernel_time(sc_level* level, int32_t kind, double* ms, int64_t* launches);
 int sc_level_kernel_times(sc_level* level, double* stage_ms, int64_t* stage_launches,
                           double* gather_ms, int64_t* gather_launches);
+
+/* Time every launch of later sc_level_forward_tape / sc_level_backward_tape
+ * calls with CUDA events (on != 0) or not (0, the default). */
+int sc_level_set_profiling(sc_level* level, int32_t on);
 
 /* Number of kernel launches the library enqueued since creation (graph
  * launches count their kernel nodes).  For measurement bookkeeping. */

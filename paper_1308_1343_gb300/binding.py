@@ -16,6 +16,8 @@ SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_EDEVICE, SC_ENOTSUP = 0, -1, -2, -3, -
 SC_ARITH_FP64, SC_ARITH_FIXED = 0, 1
 SC_MODE_GRAPH, SC_MODE_PER_BOX, SC_MODE_BATCHED, SC_MODE_TIMED = 0, 1, 2, 3
 SC_SET_UNION, SC_SET_INTERSECTION, SC_SET_DIFFERENCE, SC_SET_XOR = 0, 1, 2, 3
+(SC_KERNEL_STAGE, SC_KERNEL_GATHER, SC_KERNEL_STAGE_RECORD, SC_KERNEL_ADJ_A, SC_KERNEL_ADJ_B,
+ SC_KERNEL_ADJ_C) = range(6)
 
 _i32, _i64, _u32, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
 _vp = ctypes.c_void_p
@@ -74,6 +76,8 @@ _SIGS = {
     "sc_level_launch_count": (_i32, [_vp, _p64]),
     "sc_level_kernel_times": (_i32, [_vp, ctypes.POINTER(_dbl), _p64, ctypes.POINTER(_dbl),
                                      _p64]),
+    "sc_level_kernel_time": (_i32, [_vp, _i32, ctypes.POINTER(_dbl), _p64]),
+    "sc_level_set_profiling": (_i32, [_vp, _i32]),
     "sc_box_rk4_step_noalloc": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _dbl, _dbl, _i32, _vp]),
     "sc_last_error": (ctypes.c_char_p, []),
     "sc_bboxset_op": (_i32, [_i32, _p64, _i64, _p64, _i64, _p64, _i64, _p64]),

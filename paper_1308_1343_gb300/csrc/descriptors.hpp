@@ -39,7 +39,8 @@ struct DChunk {
   int first;  // index of the first point within the rectangle (x fastest)
 };
 
-constexpr int kChunk = 1024;
+constexpr int kChunk = 1024;  // reductions and pointwise kernels
+constexpr int kGatherChunk = 256;  // ghost gather: one point per thread
 
 // Error bits of the device error word.
 constexpr unsigned kErrNonFinite = 1u;   // Inf/NaN reached the fixed-point path

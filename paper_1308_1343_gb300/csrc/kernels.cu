@@ -25,20 +25,20 @@ constexpr int NT = 256;
 // the exchange list, one launch.
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) gather_kernel(const DRect* __restrict__ rects,
-                                                     const DChunk* __restrict__ chunks,
-                                                     int nchunks, double* f) {
+__global__ void __launch_bounds__(kGatherChunk) gather_kernel(
+    const DRect* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks, double* f) {
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const DChunk ch = chunks[c];
     const DRect r = rects[ch.rect];
-    const int n = r.ex * r.ey * r.ez;
-    const int end = min(ch.first + kChunk, n);
-    for (int p = ch.first + threadIdx.x; p < end; p += blockDim.x) {
-      const int x = p % r.ex;
+    const int p = ch.first + (int)threadIdx.x;
+    if (p < r.ex * r.ey * r.ez) {
       const int t = p / r.ex;
-      const int y = t % r.ey;
+      const int x = p - t * r.ex;
       const int z = t / r.ey;
-      f[r.dst + x + y * r.dpy + z * r.dpz] = f[r.src + x + y * r.spy + z * r.spz];
+      const int y = t - z * r.ey;
+      // offsets fit 32 bits: a field holds fewer than 2^31 doubles
+      f[(int)r.dst + x + y * (int)r.dpy + z * (int)r.dpz] =
+          f[(int)r.src + x + y * (int)r.spy + z * (int)r.spz];
     }
   }
 }
@@ -211,7 +211,7 @@ struct FwdEpi {
   double* __restrict__ lapw;
   A arith;
   int qk;          // stage factor 2^qk applied to q (1/4, 1/2, 1; 1/3 lives in q)
-  double g, lw;    // g_s; L w scale for recording
+  double g, lw;    // g_s; scale of the recorded C_s L w (adjoint constant included)
   unsigned emax;
 
   __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
     const StageCoef cf = a.coef[bx.dom];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
     FwdEpi<A, RECORD> epi{{a.wp_in, a.yu, a.yp, a.q}, a.wu_out, a.wp_out, a.lapw, arith,
-                          a.qk, cf.gamma, cf.inv12h2 * exp2_int(-a.qk)};
+                          a.qk, cf.gamma, cf.rec};
     epi.emax = 0;
     run_item<NT>(it, bx, a.wu_in, arith, smem, err, epi);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
@@ -295,58 +295,78 @@ __global__ void __launch_bounds__(NT, 4) lap_kernel(LapArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint stages.  Reverse of w_s = y + g_s A w_{s-1} with
-// A^T(a, b) = (L(c2 b), a), given lam_s (adjoint of w_s):
-//   lam_{s-1}.u  = g_s L z_s,  z_s = c2 lam_s.pi
-//   lam_{s-1}.pi = g_s lam_s.u
-//   ybar        += lam_s            (and lam_0 at the end)
-//   c2bar       += g_s lam_s.pi (L w_{s-1}.u)
-// Stages s = 4, 3, 2 write lam_{s-1}.u and z_{s-1} = c2 g_s lam_s.u; the
-// last kernel (s = 1) also forms ybar and c2bar from the stored lam_s.u and
-// the recorded L w_{s-1}.u of the forward stages, and writes z_4 = c2 ybar.pi
-// for the next (earlier) step.
+// Adjoint of one nested-RK4 step.  With M = L(c2 .), the reverse of
+// w_s = y + g_s A w_{s-1} (A^T(a, b) = (L(c2 b), a), L symmetric) applied to
+// the adjoint (a, b) of the step's output needs four applications of M:
+//   P4 = M b,  P3 = M a,  P2 = M P4,  P1 = M P3,
+// and then, with G4 = g4, G34 = g3 g4, G234 = g2 g3 g4, G1234 = g1 g2 g3 g4:
+//   ybar.u  = a + G4 P4 + G34 P3 + G234 P2 + G1234 P1
+//   ybar.pi = b + G4 a + G34 P4 + G234 P3 + G1234 P2
+//   c2bar  += G4 b Lw3 + G34 a Lw2 + G234 P4 Lw1 + G1234 P3 Lw0
+// (Lw_{s-1} = L w_{s-1}.u of forward stage s).  The kernels work with the
+// unscaled sums Phat = 12 h^2 P; all constant factors (the G's, powers of
+// 1/(12 h^2)) are folded into per-domain coefficients, and the forward pass
+// records Q_s = C_s Lw_{s-1} already multiplied by its constant.
+//   adj_a   (x2): Phat = L^ z, and z' = c2 Phat   (z = c2 b or c2 a)
+//   adj_b   (x2): Phat2 = L^ (c2 Phat4), Phat1 = L^ (c2 Phat3)
+//   adj_combine : the combination above, pointwise; it also writes the next
+//                 (earlier) step's stencil inputs c2 ybar.pi and c2 ybar.u
 // ---------------------------------------------------------------------------
 
 template <class A>
-struct AdjEpi {
-  static constexpr int NF = 2;  // lam_s.u, c2
+struct AdjAEpi {
+  static constexpr int NF = 1;  // c2
   const double* f[NF];
-  double* __restrict__ lam_out;
+  double* __restrict__ p_out;
   double* __restrict__ z_out;
   A arith;
-  double g, kap;
   unsigned emax;
   __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
                                         typename A::T rB, bool actB) {
-    const double2 l = pw[0], c = pw[1];
-    const double2 lo = make_double2(kap * arith.scaled(rA, 0), kap * arith.scaled(rB, 0));
-    const double2 zo = make_double2(c.x * (g * l.x), c.y * (g * l.y));
+    const double2 c = pw[0];
+    const double2 p = make_double2(arith.scaled(rA, 0), arith.scaled(rB, 0));
+    const double2 z = make_double2(c.x * p.x, c.y * p.y);
     if (actB) {
-      st2(lam_out + i, lo);
-      st2(z_out + i, zo);
+      st2(p_out + i, p);
+      st2(z_out + i, z);
     } else {
-      lam_out[i] = lo.x;
-      z_out[i] = zo.x;
+      p_out[i] = p.x;
+      z_out[i] = z.x;
     }
     if (A::kFixed) {
-      emax = max(emax, biased_exp(zo.x));
-      if (actB) emax = max(emax, biased_exp(zo.y));
+      emax = max(emax, biased_exp(z.x));
+      if (actB) emax = max(emax, biased_exp(z.y));
     }
   }
 };
 
 template <class A>
-__global__ void __launch_bounds__(NT, 4) adj_stage_kernel(AdjArgs a) {
-  __shared__ Smem<NT, A, 2> smem;
+struct AdjBEpi {
+  static constexpr int NF = 0;
+  const double* f[1];
+  double* __restrict__ p_out;
+  A arith;
+  __device__ __forceinline__ void point(int i, const double2*, typename A::T rA,
+                                        typename A::T rB, bool actB) {
+    const double2 p = make_double2(arith.scaled(rA, 0), arith.scaled(rB, 0));
+    if (actB)
+      st2(p_out + i, p);
+    else
+      p_out[i] = p.x;
+  }
+};
+
+template <class A>
+__global__ void __launch_bounds__(NT, 4) adj_a_kernel(AdjArgs a) {
+  __shared__ Smem<NT, A, 1> smem;
   __shared__ unsigned red[NT / 32];
   if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
   unsigned err = 0;
   for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
     const DItem it = a.items[i];
     const DBox bx = a.boxes[it.box];
-    const StageCoef cf = a.coef[bx.dom];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    AdjEpi<A> epi{{a.lam_u, a.c2}, a.lam_out, a.z_out, arith, cf.gamma, cf.kappa};
+    AdjAEpi<A> epi{{a.c2}, a.p_out, a.z_out, arith};
     epi.emax = 0;
     run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
@@ -355,85 +375,75 @@ __global__ void __launch_bounds__(NT, 4) adj_stage_kernel(AdjArgs a) {
 }
 
 template <class A>
-struct AdjLastEpi {
-  static constexpr int NF = 4;  // lam_1.u, lam_2.u, lam_3.u, lam_4.u (streamed)
-  const double* f[NF];
-  double* yu;
-  double* yp;
-  const double* __restrict__ c2;
-  const double* __restrict__ w1;  // L w_0.u  (forward stage 1)
-  const double* __restrict__ w2;
-  const double* __restrict__ w3;
-  const double* __restrict__ w4;  // L w_3.u  (forward stage 4)
-  double* cb;
-  double* __restrict__ z_out;
-  A arith;
-  double g1, g2, g3, g4, kap1;
-  unsigned emax;
-  __device__ __forceinline__ double pi_one(double p, double u, double b3, double b2,
-                                           double b1) const {
-    return p + fma(g4, u, fma(g3, b3, fma(g2, b2, g1 * b1)));
-  }
-  __device__ __forceinline__ double c2_one(double p, double u, double b3, double b2, double q4,
-                                           double q3, double q2, double q1) const {
-    // g4 lam4.pi Lw3 + g3 (g4 lam4.u) Lw2 + g2 (g3 lam3.u) Lw1 + g1 (g2 lam2.u) Lw0
-    return fma(g4 * p, q4, fma(g3 * (g4 * u), q3, fma(g2 * (g3 * b3), q2, g1 * (g2 * b2) * q1)));
-  }
-  __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
-                                        typename A::T rB, bool actB) {
-    const double2 a1 = pw[0], a2 = pw[1], a3 = pw[2], u4 = pw[3];
-    const double2 p4 = ld2(yp + i);
-    const double2 l0 = make_double2(kap1 * arith.scaled(rA, 0), kap1 * arith.scaled(rB, 0));
-    const double2 un = make_double2(((u4.x + a3.x) + (a2.x + a1.x)) + l0.x,
-                                    ((u4.y + a3.y) + (a2.y + a1.y)) + l0.y);
-    const double2 pn = make_double2(pi_one(p4.x, u4.x, a3.x, a2.x, a1.x),
-                                    pi_one(p4.y, u4.y, a3.y, a2.y, a1.y));
-    const double2 q4 = ld2(w4 + i), q3 = ld2(w3 + i), q2 = ld2(w2 + i), q1 = ld2(w1 + i);
-    const double2 cbo = ld2(cb + i);
-    const double2 cn = make_double2(
-        cbo.x + c2_one(p4.x, u4.x, a3.x, a2.x, q4.x, q3.x, q2.x, q1.x),
-        cbo.y + c2_one(p4.y, u4.y, a3.y, a2.y, q4.y, q3.y, q2.y, q1.y));
-    const double2 cc = ld2(c2 + i);
-    const double2 zo = make_double2(cc.x * pn.x, cc.y * pn.y);
-    if (actB) {
-      st2(yu + i, un);
-      st2(yp + i, pn);
-      st2(cb + i, cn);
-      st2(z_out + i, zo);
-    } else {
-      yu[i] = un.x;
-      yp[i] = pn.x;
-      cb[i] = cn.x;
-      z_out[i] = zo.x;
-    }
-    if (A::kFixed) {
-      emax = max(emax, biased_exp(zo.x));
-      if (actB) emax = max(emax, biased_exp(zo.y));
-    }
-  }
-};
-
-template <class A>
-__global__ void __launch_bounds__(NT) adj_last_kernel(AdjLastArgs a) {
-  __shared__ Smem<NT, A, 4> smem;
-  __shared__ unsigned red[NT / 32];
+__global__ void __launch_bounds__(NT, 4) adj_b_kernel(AdjArgs a) {
+  __shared__ Smem<NT, A, 0> smem;
   if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
   unsigned err = 0;
   for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
     const DItem it = a.items[i];
     const DBox bx = a.boxes[it.box];
     const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    const int d = bx.dom, nd = a.ndom;
-    AdjLastEpi<A> epi{{a.l1, a.l2, a.l3, a.yu}, a.yu, a.yp, a.c2, a.lapw1, a.lapw2,
-                      a.lapw3, a.lapw4, a.c2bar, a.z_out, arith,
-                              a.coef[0 * nd + d].gamma, a.coef[1 * nd + d].gamma,
-                              a.coef[2 * nd + d].gamma, a.coef[3 * nd + d].gamma,
-                      a.coef[0 * nd + d].kappa};
-    epi.emax = 0;
+    AdjBEpi<A> epi{{nullptr}, a.p_out, arith};
     run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
-    if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
   }
   if (err) atomicOr(a.err, err);
+}
+
+// The combination of one adjoint step, pointwise over interior points: one
+// point per thread (chunks of kGatherChunk points), all fields distinct.
+template <bool FIXED>
+__global__ void __launch_bounds__(kGatherChunk) adj_combine_kernel(
+    const DRect* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
+    AdjCombineArgs a) {
+  __shared__ unsigned red[32];
+  double* __restrict__ yu = a.yu;
+  double* __restrict__ yp = a.yp;
+  double* __restrict__ cb = a.c2bar;
+  double* __restrict__ xo = a.x_out;
+  double* __restrict__ yo = a.y_out;
+  const double* __restrict__ p4 = a.p4;
+  const double* __restrict__ p3 = a.p3;
+  const double* __restrict__ p2 = a.p2;
+  const double* __restrict__ p1 = a.p1;
+  const double* __restrict__ q1 = a.q1;
+  const double* __restrict__ q2 = a.q2;
+  const double* __restrict__ q3 = a.q3;
+  const double* __restrict__ q4 = a.q4;
+  const double* __restrict__ c2 = a.c2;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const DChunk ch = chunks[c];
+    const DRect r = rects[ch.rect];
+    const AdjCoef k = a.coef[r.dom];
+    const int p = ch.first + (int)threadIdx.x;
+    unsigned mx = 0, my = 0;
+    if (p < r.ex * r.ey * r.ez) {
+      const int t = p / r.ex;
+      const int x = p - t * r.ex;
+      const int z = t / r.ey;
+      const int y = t - z * r.ey;
+      const int i = (int)r.src + x + y * (int)r.spy + z * (int)r.spz;
+      const double av = yu[i], bv = yp[i];
+      const double P4 = p4[i], P3 = p3[i], P2 = p2[i], P1 = p1[i];
+      const double Q1 = q1[i], Q2 = q2[i], Q3 = q3[i], Q4 = q4[i], cbv = cb[i], cc = c2[i];
+      const double ou = fma(k.cu[3], P1, fma(k.cu[2], P2, fma(k.cu[1], P3, fma(k.cu[0], P4, av))));
+      const double op = fma(k.cp[3], P2, fma(k.cp[2], P3, fma(k.cp[1], P4, fma(k.cp[0], av, bv))));
+      const double oc = fma(P3, Q1, fma(P4, Q2, fma(av, Q3, fma(bv, Q4, cbv))));
+      const double ox = cc * op, oy = cc * ou;
+      yu[i] = ou;
+      yp[i] = op;
+      cb[i] = oc;
+      xo[i] = ox;
+      yo[i] = oy;
+      if (FIXED) {
+        mx = biased_exp(ox);
+        my = biased_exp(oy);
+      }
+    }
+    if (FIXED) {
+      cta_max_to(mx, a.emax_x + r.dom, red);
+      cta_max_to(my, a.emax_y + r.dom, red);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +453,8 @@ __global__ void __launch_bounds__(NT) adj_last_kernel(AdjLastArgs a) {
 cudaError_t launch_gather(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
                           int grid, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
-  gather_kernel<<<min(grid, nchunks), 256, 0, s>>>(rects, chunks, nchunks, f);
+  (void)grid;
+  gather_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, f);
   return cudaGetLastError();
 }
 
@@ -500,10 +511,10 @@ static void set_carveouts() {
   prefer_shared(fwd_stage_kernel<Fixed, false>);
   prefer_shared(fwd_stage_kernel<Fp64, true>);
   prefer_shared(fwd_stage_kernel<Fp64, false>);
-  prefer_shared(adj_stage_kernel<Fixed>);
-  prefer_shared(adj_stage_kernel<Fp64>);
-  prefer_shared(adj_last_kernel<Fixed>);
-  prefer_shared(adj_last_kernel<Fp64>);
+  prefer_shared(adj_a_kernel<Fixed>);
+  prefer_shared(adj_a_kernel<Fp64>);
+  prefer_shared(adj_b_kernel<Fixed>);
+  prefer_shared(adj_b_kernel<Fp64>);
   prefer_shared(lap_kernel<Fixed>);
   prefer_shared(lap_kernel<Fp64>);
 }
@@ -538,24 +549,32 @@ cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_stage(int arith, const AdjArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_adj(int kind, int arith, const AdjArgs& a, int grid, cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
   set_carveouts();
   grid = min(grid, a.nitems);
-  if (arith == 1)
-    adj_stage_kernel<Fixed><<<grid, NT, 0, s>>>(a);
-  else
-    adj_stage_kernel<Fp64><<<grid, NT, 0, s>>>(a);
+  if (kind == 0) {
+    if (arith == 1)
+      adj_a_kernel<Fixed><<<grid, NT, 0, s>>>(a);
+    else
+      adj_a_kernel<Fp64><<<grid, NT, 0, s>>>(a);
+  } else {
+    if (arith == 1)
+      adj_b_kernel<Fixed><<<grid, NT, 0, s>>>(a);
+    else
+      adj_b_kernel<Fp64><<<grid, NT, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_last(int arith, const AdjLastArgs& a, int grid, cudaStream_t s) {
-  if (a.nitems <= 0) return cudaSuccess;
-  grid = min(grid, a.nitems);
+cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chunks,
+                               int nchunks, const AdjCombineArgs& a, int grid, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  (void)grid;
   if (arith == 1)
-    adj_last_kernel<Fixed><<<grid, NT, 0, s>>>(a);
+    adj_combine_kernel<true><<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, a);
   else
-    adj_last_kernel<Fp64><<<grid, NT, 0, s>>>(a);
+    adj_combine_kernel<false><<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, a);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,13 @@ struct StageCoef {
   double gamma;    // g_s = c_s * dt, c = (1/4, 1/3, 1/2, 1)
   double kappa;    // g_s / (12 h^2)
   double inv12h2;  // 1 / (12 h^2)
-  double pad;
+  double rec;      // recording scale: C_s 2^-qk_s / (12 h^2) (see kernels.cu)
+};
+
+// Per-domain constants of the adjoint combination (see kernels.cu).
+struct AdjCoef {
+  double cu[4];  // ybar.u coefficients of Phat4, Phat3, Phat2, Phat1
+  double cp[4];  // ybar.pi coefficients of a, Phat4, Phat3, Phat2
 };
 
 struct FwdArgs {
@@ -58,41 +64,34 @@ struct AdjArgs {
   int nitems;
   int ndom;
   const DBox* boxes;
-  const double* z_in;   // c2 * lam_s.pi (ghosts filled)
-  const double* lam_u;  // lam_s.u
+  const double* z_in;  // stencil input (ghosts filled)
   const double* c2;
-  double* lam_out;      // lam_{s-1}.u
-  double* z_out;        // z_{s-1}
-  const StageCoef* coef;  // [ndom] of stage s
+  double* p_out;       // Phat = 12 h^2 L z_in
+  double* z_out;       // c2 Phat (adj_a only)
   const unsigned* emax_in;
   unsigned* emax_out;
   unsigned* emax_clear;
   unsigned* err;
 };
 
-struct AdjLastArgs {
-  const DItem* items;
-  int nitems;
-  int ndom;
-  const DBox* boxes;
-  const double* z_in;  // z_1
-  const double* l1;    // lam_1.u
-  const double* l2;    // lam_2.u
-  const double* l3;    // lam_3.u
-  double* yu;          // in: lam_4 = adjoint of the step output; out: of its input
-  double* yp;
+struct AdjCombineArgs {
+  double* yu;          // in: a (adjoint of the step output); out: of its input
+  double* yp;          // in: b; out
+  const double* p4;    // Phat4 .. Phat1
+  const double* p3;
+  const double* p2;
+  const double* p1;
+  const double* q1;    // recorded C_1 Lw0 ... C_4 Lw3 of the forward step
+  const double* q2;
+  const double* q3;
+  const double* q4;
   const double* c2;
-  const double* lapw1;  // recorded L w_0.u .. L w_3.u of the forward step
-  const double* lapw2;
-  const double* lapw3;
-  const double* lapw4;
   double* c2bar;
-  double* z_out;  // c2 * ybar.pi, first stencil input of the previous step
-  const StageCoef* coef;  // [4 * ndom]
-  const unsigned* emax_in;
-  unsigned* emax_out;
-  unsigned* emax_clear;
-  unsigned* err;
+  double* x_out;       // c2 ybar.pi: next adjoint step's first stencil input
+  double* y_out;       // c2 ybar.u
+  const AdjCoef* coef; // [ndom]
+  unsigned* emax_x;
+  unsigned* emax_y;
 };
 
 cudaError_t launch_gather(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
@@ -112,8 +111,10 @@ cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
 cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
                              cudaStream_t s);
 cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_adj_stage(int arith, const AdjArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_adj_last(int arith, const AdjLastArgs& a, int grid, cudaStream_t s);
+// kind 0: adj_a (Phat and c2 Phat), kind 1: adj_b (Phat only)
+cudaError_t launch_adj(int kind, int arith, const AdjArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chunks,
+                               int nchunks, const AdjCombineArgs& a, int grid, cudaStream_t s);
 int stage_threads();
 cudaError_t stage_occupancy(int arith, int* blocks_per_sm);
 

@@ -52,18 +52,21 @@ struct DeviceState {
   dev::DRect* irects = nullptr;
   dev::DChunk* ichunks = nullptr;
   int nichunks = 0;
+  dev::DChunk* pchunks = nullptr;  // interior, kGatherChunk points per chunk
+  int npchunks = 0;
   // interior + the six ghost slabs of every box (all points the stencil reads)
   dev::DRect* srects = nullptr;
   dev::DChunk* schunks = nullptr;
   int nschunks = 0;
 
   dev::StageCoef* coef = nullptr;  // [4][ndom]
+  dev::AdjCoef* acoef = nullptr;   // [ndom]
   std::vector<double> coef_dt;     // dt per domain the coefficients were built for
   double* inv12h2 = nullptr;       // [ndom]
   double* qfac = nullptr;          // [ndom][2]: dt/(12 h^2), (dt/3)/(12 h^2)
   double* h3 = nullptr;            // [ndom]
   unsigned* emax = nullptr;        // forward ring [4][ndom]
-  unsigned* emax_adj = nullptr;    // adjoint ring [4][ndom]
+  unsigned* emax_adj = nullptr;    // adjoint slots [8][ndom]
   unsigned* err = nullptr;
   double* partial = nullptr;       // [nichunks]
   double* pinned = nullptr;        // host staging for small uploads
@@ -80,7 +83,7 @@ struct DeviceState {
   // per-kernel CUDA-event timing (mode SC_MODE_TIMED): kind -> event pairs
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
-  std::vector<int> ev_kind;  // 0 = stage kernel, 1 = ghost gather, 2 = other
+  std::vector<int> ev_kind;  // SC_KERNEL_* of each timed launch
   int grid_stage = 0;  // persistent grid of the stage kernels
   int grid_small = 0;  // grid of the gather / reduction kernels
 };
@@ -99,6 +102,7 @@ struct sc_level {
   int ctas_per_sm = 0;
   int version = 0;  // bumps when items change (invalidates graphs)
   int64_t launches = 0;
+  int profile = 0;  // time every launch of the taped forward/backward
   bool all_periodic = true;
   // tape of the last sc_level_forward_tape
   bool tape_valid = false;

@@ -2,6 +2,7 @@
 // step (per-box launches, batched launches, or a CUDA graph per step), the
 // end-to-end host entry point, the misfit, and the checkpointed adjoint.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -38,8 +39,8 @@ int upload(T** dst, const std::vector<T>& v) {
   return SC_OK;
 }
 
-void add_chunks(int rect, int64_t n, std::vector<DChunk>& out) {
-  for (int64_t f = 0; f < n; f += dev::kChunk) out.push_back(DChunk{rect, (int)f});
+void add_chunks(int rect, int64_t n, std::vector<DChunk>& out, int chunk = dev::kChunk) {
+  for (int64_t f = 0; f < n; f += chunk) out.push_back(DChunk{rect, (int)f});
 }
 
 // Work items: every box cut into (tile_x, tile_y, tile_z) items of its class,
@@ -108,7 +109,7 @@ void release_device(sc_level* L) {
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
   void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->irects, D->ichunks,
-                  D->srects, D->schunks, D->coef, D->inv12h2, D->qfac, D->h3, D->emax,
+                  D->srects, D->schunks, D->pchunks, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -174,7 +175,8 @@ int ensure_device(sc_level* L) {
         r.ez = (int)C.ext[2];
         r.dom = L->boxes[b].domain;
         grects.push_back(r);
-        add_chunks((int)grects.size() - 1, C.ext[0] * C.ext[1] * C.ext[2], gchunks);
+        add_chunks((int)grects.size() - 1, C.ext[0] * C.ext[1] * C.ext[2], gchunks,
+                   dev::kGatherChunk);
       }
     }
     D->box_gchunks[nb] = (int)gchunks.size();
@@ -186,7 +188,7 @@ int ensure_device(sc_level* L) {
 
   // interior rectangles, and interior + six ghost slabs
   std::vector<DRect> irects, srects;
-  std::vector<DChunk> ichunks, schunks;
+  std::vector<DChunk> ichunks, schunks, pchunks;
   for (int b = 0; b < nb; ++b) {
     const sc_box& B = L->boxes[b];
     int64_t n[3];
@@ -201,6 +203,7 @@ int ensure_device(sc_level* L) {
     r.dom = B.domain;
     irects.push_back(r);
     add_chunks((int)irects.size() - 1, n[0] * n[1] * n[2], ichunks);
+    add_chunks((int)irects.size() - 1, n[0] * n[1] * n[2], pchunks, dev::kGatherChunk);
     srects.push_back(r);
     add_chunks((int)srects.size() - 1, n[0] * n[1] * n[2], schunks);
     for (int d = 0; d < 3; ++d)
@@ -222,7 +225,9 @@ int ensure_device(sc_level* L) {
   if (!rc) rc = upload(&D->ichunks, ichunks);
   if (!rc) rc = upload(&D->srects, srects);
   if (!rc) rc = upload(&D->schunks, schunks);
+  if (!rc) rc = upload(&D->pchunks, pchunks);
   if (rc) return rc;
+  D->npchunks = (int)pchunks.size();
   D->nichunks = (int)ichunks.size();
   D->nschunks = (int)schunks.size();
 
@@ -238,13 +243,15 @@ int ensure_device(sc_level* L) {
   SC_CUDA(cudaMalloc(&D->coef, sizeof(StageCoef) * 4 * nd));
   SC_CUDA(cudaMalloc(&D->qfac, sizeof(double) * 2 * nd));
   SC_CUDA(cudaMalloc(&D->emax, sizeof(unsigned) * 4 * nd));
-  SC_CUDA(cudaMalloc(&D->emax_adj, sizeof(unsigned) * 4 * nd));
+  SC_CUDA(cudaMalloc(&D->emax_adj, sizeof(unsigned) * 8 * nd));
+  SC_CUDA(cudaMalloc(&D->acoef, sizeof(dev::AdjCoef) * nd));
   SC_CUDA(cudaMemset(D->emax, 0, sizeof(unsigned) * 4 * nd));
-  SC_CUDA(cudaMemset(D->emax_adj, 0, sizeof(unsigned) * 4 * nd));
+  SC_CUDA(cudaMemset(D->emax_adj, 0, sizeof(unsigned) * 8 * nd));
   SC_CUDA(cudaMalloc(&D->err, sizeof(unsigned)));
   SC_CUDA(cudaMemset(D->err, 0, sizeof(unsigned)));
   SC_CUDA(cudaMalloc(&D->partial, sizeof(double) * std::max(1, D->nichunks)));
-  D->pinned_size = sizeof(StageCoef) * 4 * nd + sizeof(double) * 2 * nd + 64;
+  D->pinned_size =
+      sizeof(StageCoef) * 4 * nd + sizeof(double) * 2 * nd + sizeof(dev::AdjCoef) * nd + 64;
   SC_CUDA(cudaMallocHost(&D->pinned, D->pinned_size));
   return upload_items(L);
 }
@@ -281,23 +288,30 @@ int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s) {
   }
   if (want == D->coef_dt) return SC_OK;
   static const double c[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  static const int qk[4] = {-2, 0, -1, 0};  // stage factors folded into the stencil sum
   // wait for earlier work that reads the pinned staging buffer
   SC_CUDA(cudaStreamSynchronize(s));
   StageCoef* h = reinterpret_cast<StageCoef*>(D->pinned);
-  for (int st = 0; st < 4; ++st)
-    for (int d = 0; d < nd; ++d) {
-      const double hh = L->doms[d].h;
-      const double g = c[st] * want[d];
-      h[st * nd + d] = StageCoef{g, g / (12.0 * hh * hh), 1.0 / (12.0 * hh * hh), 0.0};
-    }
-  SC_CUDA(cudaMemcpyAsync(D->coef, h, sizeof(StageCoef) * 4 * nd, cudaMemcpyHostToDevice, s));
   double* qf = reinterpret_cast<double*>(h + 4 * nd);
+  dev::AdjCoef* ac = reinterpret_cast<dev::AdjCoef*>(qf + 2 * nd);
   for (int d = 0; d < nd; ++d) {
     const double hh = L->doms[d].h;
-    qf[2 * d] = want[d] / (12.0 * hh * hh);
-    qf[2 * d + 1] = (want[d] / 3.0) / (12.0 * hh * hh);
+    const double inv = 1.0 / (12.0 * hh * hh);
+    double g[4];
+    for (int st = 0; st < 4; ++st) g[st] = c[st] * want[d];
+    // adjoint constants: G4, G34, G234, G1234 (products of the stage steps)
+    const double G4 = g[3], G34 = g[2] * g[3], G234 = g[1] * G34, G1234 = g[0] * G234;
+    const double C[4] = {G1234 * inv, G234 * inv, G34, G4};  // of Lw0 .. Lw3
+    for (int st = 0; st < 4; ++st)
+      h[st * nd + d] = StageCoef{g[st], g[st] * inv, inv, C[st] * std::ldexp(1.0, -qk[st]) * inv};
+    qf[2 * d] = want[d] * inv;
+    qf[2 * d + 1] = (want[d] / 3.0) * inv;
+    ac[d] = dev::AdjCoef{{G4 * inv, G34 * inv, G234 * inv * inv, G1234 * inv * inv},
+                         {G4, G34 * inv, G234 * inv, G1234 * inv * inv}};
   }
+  SC_CUDA(cudaMemcpyAsync(D->coef, h, sizeof(StageCoef) * 4 * nd, cudaMemcpyHostToDevice, s));
   SC_CUDA(cudaMemcpyAsync(D->qfac, qf, sizeof(double) * 2 * nd, cudaMemcpyHostToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(D->acoef, ac, sizeof(dev::AdjCoef) * nd, cudaMemcpyHostToDevice, s));
   D->coef_dt = want;
   return SC_OK;
 }
@@ -341,14 +355,14 @@ static cudaError_t enq_fill(const Enq& q, double* f) {
   DeviceState* D = q.L->dev;
   if (!q.per_box) {
     (*q.count)++;
-    TimedLaunch t(q, 1);
+    TimedLaunch t(q, SC_KERNEL_GATHER);
     return dev::launch_gather(D->grects, D->gchunks, D->ngchunks, f, D->grid_small, q.s);
   }
   for (size_t b = 0; b + 1 < D->box_gchunks.size(); ++b) {
     const int n = D->box_gchunks[b + 1] - D->box_gchunks[b];
     if (n <= 0) continue;
     (*q.count)++;
-    TimedLaunch t(q, 1);
+    TimedLaunch t(q, SC_KERNEL_GATHER);
     cudaError_t e = dev::launch_gather(D->grects, D->gchunks + D->box_gchunks[b], n, f,
                                        D->grid_small, q.s);
     if (e != cudaSuccess) return e;
@@ -372,14 +386,14 @@ static cudaError_t enq_fwd(const Enq& q, dev::FwdArgs a, bool record) {
     a.items = D->items;
     a.nitems = D->nitems;
     (*q.count)++;
-    TimedLaunch t(q, 0);
+    TimedLaunch t(q, record ? SC_KERNEL_STAGE_RECORD : SC_KERNEL_STAGE);
     return dev::launch_fwd_stage(q.L->arith, record, a, D->grid_stage, q.s);
   }
   for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
     a.items = D->items + D->box_items[b];
     a.nitems = D->box_items[b + 1] - D->box_items[b];
     (*q.count)++;
-    TimedLaunch t(q, 0);
+    TimedLaunch t(q, record ? SC_KERNEL_STAGE_RECORD : SC_KERNEL_STAGE);
     cudaError_t e = dev::launch_fwd_stage(q.L->arith, record, a, D->grid_stage, q.s);
     if (e != cudaSuccess) return e;
   }
@@ -643,6 +657,11 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
       return rc;
   L->tape_valid = false;
   Enq q{L, s, &L->launches, false};
+  if (L->profile) {
+    q.timed = true;
+    D->ev_used = 0;
+    D->ev_kind.clear();
+  }
   SC_CUDA(cudaMemcpyAsync(Su, u0, bytes, cudaMemcpyDeviceToDevice, s));
   SC_CUDA(cudaMemcpyAsync(Sp, pi0, bytes, cudaMemcpyDeviceToDevice, s));
   for (int c = 0; c < nck; ++c) {
@@ -698,8 +717,20 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     if ((rc = get_field(L, "lapw." + std::to_string(j), &lapw[j]))) return rc;
 
   Enq q{L, s, &L->launches, false};
+  if (L->profile) {
+    q.timed = true;
+    D->ev_used = 0;
+    D->ev_kind.clear();
+  }
   const bool fixed = L->arith == SC_ARITH_FIXED;
-  // adjoint seeds, z_4 = c2 * ybar.pi
+  double *P4, *P3, *P2, *P1;
+  if ((rc = get_field(L, "P4", &P4)) || (rc = get_field(L, "P3", &P3)) ||
+      (rc = get_field(L, "P2", &P2)) || (rc = get_field(L, "P1", &P1)))
+    return rc;
+  // stencil inputs: X = c2 ybar.pi, Y = c2 ybar.u, X' = c2 P4hat, Y' = c2 P3hat
+  double *X = Za, *Y = Zb, *Xp = L1, *Yq = L2;
+  (void)L3;
+  // adjoint seeds
   if (gu_T)
     SC_CUDA(cudaMemcpyAsync(Yu, gu_T, bytes, cudaMemcpyDeviceToDevice, s));
   else
@@ -709,69 +740,107 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
   else
     SC_CUDA(cudaMemsetAsync(Yp, 0, bytes, s));
   SC_CUDA(cudaMemsetAsync(g_c2, 0, bytes, s));
-  SC_CUDA(cudaMemsetAsync(D->emax_adj, 0, sizeof(unsigned) * 4 * nd, s));
-  L->launches++;
-  SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yp, Za,
-                          fixed ? D->emax_adj : nullptr, D->grid_small, s));
+  SC_CUDA(cudaMemsetAsync(D->emax_adj, 0, sizeof(unsigned) * 8 * nd, s));
+  // exponent slots per adjoint step n (p = n & 1): X in 2p, Y in 2p+1,
+  // X' in 4+2p, Y' in 5+2p; each slot is cleared one step ahead
+  auto slot = [&](int k) { return D->emax_adj + k * nd; };
+  L->launches += 2;
+  SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yp, X,
+                          fixed ? slot(0) : nullptr, D->grid_small, s));
+  SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yu, Y,
+                          fixed ? slot(1) : nullptr, D->grid_small, s));
 
-  auto slot = [&](int t) { return D->emax_adj + (t % 4) * nd; };
+  long long n_adj = 0;
   for (int c = nck - 1; c >= 0; --c) {
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(enq_prologue(q, Su, c2, W));
     for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, lapw.data() + 4 * n));
-    for (int n = len - 1; n >= 0; --n) {
-      double* zin[3] = {Za, Zb, Za};
-      double* zout[3] = {Zb, Za, Zb};
-      const double* lin[3] = {Yu, L3, L2};
-      double* lout[3] = {L3, L2, L1};
-      for (int t = 0; t < 3; ++t) {
-        SC_CUDA(enq_fill(q, zin[t]));
-        dev::AdjArgs a{};
-        a.items = D->items;
-        a.nitems = D->nitems;
-        a.ndom = nd;
-        a.boxes = D->boxes;
-        a.z_in = zin[t];
-        a.lam_u = lin[t];
-        a.c2 = c2;
-        a.lam_out = lout[t];
-        a.z_out = zout[t];
-        a.coef = D->coef + (3 - t) * nd;
-        a.emax_in = slot(t);
-        a.emax_out = slot(t + 1);
-        a.emax_clear = slot(t + 2);
-        a.err = D->err;
-        L->launches++;
-        SC_CUDA(dev::launch_adj_stage(L->arith, a, D->grid_stage, s));
+    for (int n = len - 1; n >= 0; --n, ++n_adj) {
+      const int p = (int)(n_adj & 1), pn = 1 - p;
+      dev::AdjArgs a{};
+      a.items = D->items;
+      a.nitems = D->nitems;
+      a.ndom = nd;
+      a.boxes = D->boxes;
+      a.c2 = c2;
+      a.err = D->err;
+      // P4hat = L^(c2 b), X' = c2 P4hat
+      SC_CUDA(enq_fill(q, X));
+      a.z_in = X;
+      a.p_out = P4;
+      a.z_out = Xp;
+      a.emax_in = slot(2 * p);
+      a.emax_out = slot(4 + 2 * p);
+      a.emax_clear = slot(2 * pn);
+      L->launches++;
+      {
+        TimedLaunch t(q, SC_KERNEL_ADJ_A);
+        SC_CUDA(dev::launch_adj(0, L->arith, a, D->grid_stage, s));
       }
-      SC_CUDA(enq_fill(q, Zb));
-      dev::AdjLastArgs b{};
-      b.items = D->items;
-      b.nitems = D->nitems;
-      b.ndom = nd;
-      b.boxes = D->boxes;
-      b.z_in = Zb;
-      b.l1 = L1;
-      b.l2 = L2;
-      b.l3 = L3;
+      // P3hat = L^(c2 a), Y' = c2 P3hat
+      SC_CUDA(enq_fill(q, Y));
+      a.z_in = Y;
+      a.p_out = P3;
+      a.z_out = Yq;
+      a.emax_in = slot(2 * p + 1);
+      a.emax_out = slot(5 + 2 * p);
+      a.emax_clear = slot(2 * pn + 1);
+      L->launches++;
+      {
+        TimedLaunch t(q, SC_KERNEL_ADJ_A);
+        SC_CUDA(dev::launch_adj(0, L->arith, a, D->grid_stage, s));
+      }
+      // P2hat = L^ X'
+      SC_CUDA(enq_fill(q, Xp));
+      a.z_in = Xp;
+      a.p_out = P2;
+      a.z_out = nullptr;
+      a.emax_in = slot(4 + 2 * p);
+      a.emax_out = nullptr;
+      a.emax_clear = slot(4 + 2 * pn);
+      L->launches++;
+      {
+        TimedLaunch t(q, SC_KERNEL_ADJ_B);
+        SC_CUDA(dev::launch_adj(1, L->arith, a, D->grid_stage, s));
+      }
+      // P1hat = L^ Y'
+      SC_CUDA(enq_fill(q, Yq));
+      a.z_in = Yq;
+      a.p_out = P1;
+      a.emax_in = slot(5 + 2 * p);
+      a.emax_clear = slot(5 + 2 * pn);
+      L->launches++;
+      {
+        TimedLaunch t(q, SC_KERNEL_ADJ_B);
+        SC_CUDA(dev::launch_adj(1, L->arith, a, D->grid_stage, s));
+      }
+      // the combination, pointwise
+      dev::AdjCombineArgs b{};
       b.yu = Yu;
       b.yp = Yp;
+      b.p4 = P4;
+      b.p3 = P3;
+      b.p2 = P2;
+      b.p1 = P1;
+      b.q1 = lapw[4 * n + 0];
+      b.q2 = lapw[4 * n + 1];
+      b.q3 = lapw[4 * n + 2];
+      b.q4 = lapw[4 * n + 3];
       b.c2 = c2;
-      b.lapw1 = lapw[4 * n + 0];
-      b.lapw2 = lapw[4 * n + 1];
-      b.lapw3 = lapw[4 * n + 2];
-      b.lapw4 = lapw[4 * n + 3];
       b.c2bar = g_c2;
-      b.z_out = Za;
-      b.coef = D->coef;
-      b.emax_in = slot(3);
-      b.emax_out = slot(4);
-      b.emax_clear = slot(5);
-      b.err = D->err;
+      b.x_out = X;
+      b.y_out = Y;
+      b.coef = D->acoef;
+      b.emax_x = slot(2 * pn);
+      b.emax_y = slot(2 * pn + 1);
       L->launches++;
-      SC_CUDA(dev::launch_adj_last(L->arith, b, D->grid_stage, s));
+      {
+        TimedLaunch t(q, SC_KERNEL_ADJ_C);
+        SC_CUDA(dev::launch_adj_combine(L->arith, D->irects, D->pchunks, D->npchunks, b,
+                                        D->grid_small, s));
+      }
     }
   }
   SC_CUDA(cudaMemcpyAsync(g_u0, Yu, bytes, cudaMemcpyDeviceToDevice, s));
@@ -789,26 +858,33 @@ int sc_level_grad(sc_level* L, const double* u0, const double* pi0, const double
   return sc_level_backward_tape(L, c2, gu_T, gpi_T, g_u0, g_pi0, g_c2, stream);
 }
 
-int sc_level_kernel_times(sc_level* L, double* stage_ms, int64_t* stage_launches,
-                          double* gather_ms, int64_t* gather_launches) {
-  if (!L || !stage_ms || !stage_launches || !gather_ms || !gather_launches)
-    return set_error(SC_EINVAL, "NULL argument");
-  *stage_ms = *gather_ms = 0.0;
-  *stage_launches = *gather_launches = 0;
+int sc_level_kernel_time(sc_level* L, int32_t kind, double* ms, int64_t* launches) {
+  if (!L || !ms || !launches) return set_error(SC_EINVAL, "NULL argument");
+  *ms = 0.0;
+  *launches = 0;
   DeviceState* D = L->dev;
   if (!D) return SC_OK;
   for (size_t i = 0; i < D->ev_used; ++i) {
+    if (D->ev_kind[i] != kind) continue;
     SC_CUDA(cudaEventSynchronize(D->ev_pool[i].second));
-    float ms = 0.f;
-    SC_CUDA(cudaEventElapsedTime(&ms, D->ev_pool[i].first, D->ev_pool[i].second));
-    if (D->ev_kind[i] == 0) {
-      *stage_ms += ms;
-      ++*stage_launches;
-    } else if (D->ev_kind[i] == 1) {
-      *gather_ms += ms;
-      ++*gather_launches;
-    }
+    float t = 0.f;
+    SC_CUDA(cudaEventElapsedTime(&t, D->ev_pool[i].first, D->ev_pool[i].second));
+    *ms += t;
+    ++*launches;
   }
+  return SC_OK;
+}
+
+int sc_level_kernel_times(sc_level* L, double* stage_ms, int64_t* stage_launches,
+                          double* gather_ms, int64_t* gather_launches) {
+  int rc = sc_level_kernel_time(L, SC_KERNEL_STAGE, stage_ms, stage_launches);
+  if (rc) return rc;
+  return sc_level_kernel_time(L, SC_KERNEL_GATHER, gather_ms, gather_launches);
+}
+
+int sc_level_set_profiling(sc_level* L, int32_t on) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  L->profile = on ? 1 : 0;
   return SC_OK;
 }
 

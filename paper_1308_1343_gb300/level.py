@@ -264,6 +264,17 @@ class Level:
                                               ctypes.byref(gm), ctypes.byref(gl)))
         return sm.value, sl.value, gm.value, gl.value
 
+    def kernel_time(self, kind: int):
+        """(ms, launches) of one kernel kind (binding.SC_KERNEL_*) in the
+        last timed call."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        B.check(B.lib().sc_level_kernel_time(self._h, int(kind), ctypes.byref(ms),
+                                             ctypes.byref(n)))
+        return ms.value, n.value
+
+    def set_profiling(self, on: bool):
+        B.check(B.lib().sc_level_set_profiling(self._h, 1 if on else 0))
+
     def sync(self, stream=None):
         B.check(B.lib().sc_level_sync(self._h, _stream(stream)))
 
