@@ -194,9 +194,10 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
 
 /* Advance (u, pi) by nsteps classic RK4 steps of dt, in place.  dt points to
  * ndt host doubles: ndt == 1 (one step size) or ndt == number of domains
- * (step size of each domain).  c2 is read on interior points only.  Ghosts
- * of u are refreshed internally before every stage; on return the ghosts of
- * u hold the values of the last stage's input, not of the result.  All
+ * (step size of each domain).  c2 is read on interior points only.  The
+ * ghosts of every stage input are gathered before the stage (one batched
+ * launch, inside the step's CUDA graph in SC_MODE_GRAPH), so on return the
+ * ghosts of u hold the input of the last stage, not the result.  All
  * domains must be periodic on every axis (SC_EINVAL otherwise).  mode is one
  * of SC_MODE_*.  Scratch stage arrays are allocated on the first call. */
 int sc_level_rk4_step(sc_level* level, double* u, double* pi, const double* c2,
@@ -218,7 +219,9 @@ int sc_level_misfit(sc_level* level, const double* u, const double* u_obs,
                     double* loss, double* seed, void* stream);
 
 /* Forward pass for differentiation: runs nsteps RK4 steps from (u0, pi0)
- * (batched launches), keeping the state every ckpt_every steps in
+ * (batched launches; the ghosts of each stage output are written by the
+ * stage kernel itself, from the level's exchange list grouped by source
+ * box and face slab), keeping the state every ckpt_every steps in
  * library-owned checkpoint fields (the level's tape, replacing any earlier
  * tape), and writes the final state to u_T, pi_T (either may be NULL).
  * Inputs are not modified.  Requires periodic domains.  Device memory:

@@ -126,6 +126,8 @@ struct Timer {
     a.c2 = c2;
     a.q = c2;
     a.qk = 0;
+    a.push = D->push;
+    a.push_gofs = D->push_gofs;
     a.wu_out = W[2];
     a.wp_out = W[3];
     a.coef = D->coef;

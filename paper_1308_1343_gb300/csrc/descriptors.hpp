@@ -31,6 +31,18 @@ struct DRect {
   long long dpy, dpz;        // destination pitches
   int ex, ey, ez;            // extent
   int dom;                   // domain of the points
+  int box;                   // box of the points (interior rectangles)
+  int x0, y0, z0;            // interior coordinates of the first point
+};
+
+// One ghost copy seen from its source: the source rectangle in the source
+// box's interior coordinates [lo, hi) and where its first point goes.  A
+// producer that writes point (x, y, z) of the source box inside the
+// rectangle also writes it to dbase + (x-lo0) + (y-lo1)*dpy + (z-lo2)*dpz.
+struct DPush {
+  int lo0, lo1, lo2, hi0, hi1, hi2;
+  int dbase, dpy, dpz;
+  int pad[3];
 };
 
 // A chunk of up to CHUNK consecutive points of one rectangle.

@@ -215,7 +215,7 @@ struct FwdEpi {
   unsigned emax;
 
   __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
-                                        typename A::T rB, bool actB) {
+                                        typename A::T rB, bool actB, int, int, int) {
     const double2 wp = pw[0], u0 = pw[1], p0 = pw[2], q = pw[3];
     const double dA = arith.scaled(rA, qk), dB = arith.scaled(rB, qk);
     double2 un, pn;
@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
                           a.qk, cf.gamma, cf.rec};
     epi.emax = 0;
     run_item<NT>(it, bx, a.wu_in, arith, smem, err, epi);
+    // ghost copies of the new w.u, the next stage's stencil input
+    push_item<NT>(PushTab{a.push, a.push_gofs}, it, bx, a.wu_out);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
   }
   if (err) atomicOr(a.err, err);
@@ -271,7 +273,7 @@ struct LapEpi {
   A arith;
   double lw;
   __device__ __forceinline__ void point(int i, const double2*, typename A::T rA,
-                                        typename A::T rB, bool actB) {
+                                        typename A::T rB, bool actB, int, int, int) {
     const double dA = arith.scaled(rA, 0) * lw, dB = arith.scaled(rB, 0) * lw;
     if (actB)
       st2(out + i, make_double2(dA, dB));
@@ -322,7 +324,7 @@ struct AdjAEpi {
   A arith;
   unsigned emax;
   __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
-                                        typename A::T rB, bool actB) {
+                                        typename A::T rB, bool actB, int, int, int) {
     const double2 c = pw[0];
     const double2 p = make_double2(arith.scaled(rA, 0), arith.scaled(rB, 0));
     const double2 z = make_double2(c.x * p.x, c.y * p.y);
@@ -347,7 +349,7 @@ struct AdjBEpi {
   double* __restrict__ p_out;
   A arith;
   __device__ __forceinline__ void point(int i, const double2*, typename A::T rA,
-                                        typename A::T rB, bool actB) {
+                                        typename A::T rB, bool actB, int, int, int) {
     const double2 p = make_double2(arith.scaled(rA, 0), arith.scaled(rB, 0));
     if (actB)
       st2(p_out + i, p);
@@ -369,6 +371,7 @@ __global__ void __launch_bounds__(NT, 4) adj_a_kernel(AdjArgs a) {
     AdjAEpi<A> epi{{a.c2}, a.p_out, a.z_out, arith};
     epi.emax = 0;
     run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
+    push_item<NT>(PushTab{a.push, a.push_gofs}, it, bx, a.z_out);  // next stencil input
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
   }
   if (err) atomicOr(a.err, err);
@@ -434,6 +437,14 @@ __global__ void __launch_bounds__(kGatherChunk) adj_combine_kernel(
       cb[i] = oc;
       xo[i] = ox;
       yo[i] = oy;
+      const int gx = r.x0 + x, gy = r.y0 + y, gz = r.z0 + z;
+      const DBox bx = a.boxes[r.box];
+      if (a.push_gofs &&
+          (gx < 2 || gx >= bx.nx - 2 || gy < 2 || gy >= bx.ny - 2 || gz < 2 || gz >= bx.nz - 2)) {
+        const PushTab pt{a.push, a.push_gofs};
+        push_point(pt, r.box, gx, gy, gz, bx.nx, bx.ny, bx.nz, ox, xo);
+        push_point(pt, r.box, gx, gy, gz, bx.nx, bx.ny, bx.nz, oy, yo);
+      }
       if (FIXED) {
         mx = biased_exp(ox);
         my = biased_exp(oy);

@@ -94,6 +94,75 @@ __device__ __forceinline__ long long to_fix(double x, int E, bool use, unsigned&
   return (hi >> 31) ? -v : v;
 }
 
+// ---------------------------------------------------------------------------
+// Ghost exchange fused into producers ("push")
+// ---------------------------------------------------------------------------
+
+// Push table of a level: per box, six groups of DPush entries -- axis d, and
+// whether the sources lie in the low (side 0) or high (side 1) two-deep slab
+// of the box; group g of box b spans entries [gofs[6b+g], gofs[6b+g+1]).
+struct PushTab {
+  const DPush* e;
+  const int* gofs;
+};
+
+__device__ __forceinline__ void push_group(const PushTab& t, int g, int x, int y, int z, double v,
+                                           double* f) {
+  const int j1 = t.gofs[g + 1];
+  for (int j = t.gofs[g]; j < j1; ++j) {
+    const DPush p = t.e[j];
+    if (x >= p.lo0 && x < p.hi0 && y >= p.lo1 && y < p.hi1 && z >= p.lo2 && z < p.hi2)
+      f[p.dbase + (x - p.lo0) + (y - p.lo1) * p.dpy + (z - p.lo2) * p.dpz] = v;
+  }
+}
+
+// Write v, the new value of interior point (x, y, z) of box b (extent n), to
+// every ghost point that copies it.  Each ghost point has exactly one owner,
+// so these writes never collide.
+__device__ __forceinline__ void push_point(const PushTab& t, int b, int x, int y, int z, int nx,
+                                           int ny, int nz, double v, double* f) {
+  const int g = 6 * b;
+  if (x < 2) push_group(t, g + 0, x, y, z, v, f);
+  if (x >= nx - 2) push_group(t, g + 1, x, y, z, v, f);
+  if (y < 2) push_group(t, g + 2, x, y, z, v, f);
+  if (y >= ny - 2) push_group(t, g + 3, x, y, z, v, f);
+  if (z < 2) push_group(t, g + 4, x, y, z, v, f);
+  if (z >= nz - 2) push_group(t, g + 5, x, y, z, v, f);
+}
+
+// After a CTA has written work item `it` of field f (and passed a barrier),
+// copy the item's points that other boxes read as ghosts: every push entry
+// of the item's box is intersected with the item's region, and the CTA's
+// threads copy the intersection.  Items away from all faces return at once.
+template <int NT>
+__device__ __forceinline__ void push_item(const PushTab& t, const DItem& it, const DBox& bx,
+                                          double* f) {
+  if (!t.gofs) return;  // no push table: the caller gathers instead
+  const int xa = it.x0, xb = min(it.x0 + 2 * it.txh, bx.nx);
+  const int ya = it.y0, yb = min(it.y0 + NT / it.txh, bx.ny);
+  const int za = it.z0, zb = it.z0 + it.nzr;
+  if (xa >= 2 && xb <= bx.nx - 2 && ya >= 2 && yb <= bx.ny - 2 && za >= 2 && zb <= bx.nz - 2)
+    return;
+  const int off0 = (int)bx.off, py = (int)bx.py, pz = (int)bx.pz;
+  const int j0 = t.gofs[6 * it.box], j1 = t.gofs[6 * it.box + 6];
+  for (int j = j0; j < j1; ++j) {
+    const DPush p = t.e[j];
+    const int lx = max(p.lo0, xa), hx = min(p.hi0, xb);
+    const int ly = max(p.lo1, ya), hy = min(p.hi1, yb);
+    const int lz = max(p.lo2, za), hz = min(p.hi2, zb);
+    if (lx >= hx || ly >= hy || lz >= hz) continue;
+    const int ex = hx - lx, ey = hy - ly, n = ex * ey * (hz - lz);
+    for (int q = threadIdx.x; q < n; q += NT) {
+      const int tq = q / ex;
+      const int x = lx + (q - tq * ex);
+      const int z = lz + tq / ey;
+      const int y = ly + (tq - (z - lz) * ey);
+      f[p.dbase + (x - p.lo0) + (y - p.lo1) * p.dpy + (z - p.lo2) * p.dpz] =
+          f[off0 + x + y * py + z * pz];
+    }
+  }
+}
+
 // 2^k as a double for -1022 <= k <= 1023
 __device__ __forceinline__ double exp2_int(int k) {
   return __longlong_as_double((long long)(1023 + k) << 52);
@@ -182,10 +251,11 @@ __device__ __forceinline__ int out_of(int c, int n) {
 // Walk one work item.  `F` is the stencil field (its ghosts filled).  The
 // epilogue names Epi::NF pointwise fields (epi.f[0..NF)) that the traversal
 // streams into shared memory; for every plane k it calls
-//   epi.point(idx, pw, rA, rB, actB)
+//   epi.point(idx, pw, rA, rB, actB, x, y, k)
 // on the threads owning interior points, with idx the element index of the
-// thread's first point, pw[f] its pair of field f, and rA, rB the unscaled
-// sums r = 12 h^2 (L F) at both points in the policy's integer or FP64 form.
+// thread's first point (x, y, k), pw[f] its pair of field f, and rA, rB the
+// unscaled sums r = 12 h^2 (L F) at both points in the policy's integer or
+// FP64 form.
 template <int NT, class A, class Epi>
 __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
                                          const double* __restrict__ F, A arith,
@@ -310,7 +380,7 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
       double2 pw[NF > 0 ? NF : 1];
 #pragma unroll
       for (int f = 0; f < NF; ++f) pw[f] = sm.pw[kk & 1][f][tid];
-      epi.point(oi, pw, rA, rB, actB);
+      epi.point(oi, pw, rA, rB, actB, gx, gy, k);
     }
     oi += pz;
   };

@@ -10,6 +10,7 @@ struct DBox;
 struct DItem;
 struct DRect;
 struct DChunk;
+struct DPush;
 
 // Per (stage, domain) coefficients of the nested RK4 form.
 struct StageCoef {
@@ -40,6 +41,8 @@ struct FwdArgs {
   double* lapw;  // recorded L w_in.u (adjoint checkpoints) or nullptr
   const double* q;  // c2 dt/(12 h^2) or c2 (dt/3)/(12 h^2), pre-scaled per run
   int qk;           // stage factor 2^qk on q
+  const DPush* push;     // ghost copies grouped by source box and face slab
+  const int* push_gofs;
   const StageCoef* coef;  // [ndom] of this stage
   const unsigned* emax_in;
   unsigned* emax_out;
@@ -67,7 +70,9 @@ struct AdjArgs {
   const double* z_in;  // stencil input (ghosts filled)
   const double* c2;
   double* p_out;       // Phat = 12 h^2 L z_in
-  double* z_out;       // c2 Phat (adj_a only)
+  double* z_out;       // c2 Phat (adj_a only), ghosts pushed
+  const DPush* push;
+  const int* push_gofs;
   const unsigned* emax_in;
   unsigned* emax_out;
   unsigned* emax_clear;
@@ -88,8 +93,11 @@ struct AdjCombineArgs {
   const double* c2;
   double* c2bar;
   double* x_out;       // c2 ybar.pi: next adjoint step's first stencil input
-  double* y_out;       // c2 ybar.u
+  double* y_out;       // c2 ybar.u (both with ghosts pushed)
   const AdjCoef* coef; // [ndom]
+  const DBox* boxes;
+  const DPush* push;
+  const int* push_gofs;
   unsigned* emax_x;
   unsigned* emax_y;
 };

@@ -54,6 +54,8 @@ struct DeviceState {
   int nichunks = 0;
   dev::DChunk* pchunks = nullptr;  // interior, kGatherChunk points per chunk
   int npchunks = 0;
+  dev::DPush* push = nullptr;      // ghost copies grouped by source box and face slab
+  int* push_gofs = nullptr;        // [6 nboxes + 1]
   // interior + the six ghost slabs of every box (all points the stencil reads)
   dev::DRect* srects = nullptr;
   dev::DChunk* schunks = nullptr;

@@ -83,7 +83,7 @@ struct NoAllocEpi {
   double* wp_out;
   double g, kap;
   __device__ __forceinline__ void point(int i, const double2* pw, double rA, double rB,
-                                        bool actB) {
+                                        bool actB, int, int, int) {
     const double2 wp = pw[0], u0 = pw[1], p0 = pw[2], c = pw[3];
     double2 un, pn;
     un.x = fma(g, wp.x, u0.x);

@@ -14,6 +14,7 @@ namespace sc {
 using dev::DBox;
 using dev::DChunk;
 using dev::DItem;
+using dev::DPush;
 using dev::DRect;
 using dev::StageCoef;
 
@@ -109,7 +110,7 @@ void release_device(sc_level* L) {
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
   void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->irects, D->ichunks,
-                  D->srects, D->schunks, D->pchunks, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
+                  D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -163,7 +164,7 @@ int ensure_device(sc_level* L) {
       D->box_gchunks[b] = (int)gchunks.size();
       for (; c < L->copies.size() && L->copies[c].dst_box == b; ++c) {
         const sc_copy& C = L->copies[c];
-        DRect r;
+        DRect r{};
         r.src = index_of(C.src_box, C.src_lo);
         r.dst = index_of(C.dst_box, C.dst_lo);
         r.spy = L->py[C.src_box];
@@ -186,6 +187,43 @@ int ensure_device(sc_level* L) {
   if (rc) return rc;
   D->ngchunks = (int)gchunks.size();
 
+  // the same copies seen from their sources: a ghost on the low (high) side
+  // of its box along axis d is owned by a point in the high (low) two-deep
+  // slab of the source box, so group the copies by (source box, d, slab)
+  {
+    std::vector<std::vector<DPush>> groups((size_t)nb * 6);
+    for (const sc_copy& C : L->copies) {
+      const sc_box& Bd = L->boxes[C.dst_box];
+      const sc_box& Bs = L->boxes[C.src_box];
+      int d = -1, side = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (C.dst_lo[a] < Bd.lo[a]) { d = a; side = 1; }
+        else if (C.dst_lo[a] >= Bd.hi[a]) { d = a; side = 0; }
+      }
+      if (d < 0) return set_error(SC_EINVAL, "exchange copy does not target a ghost region");
+      DPush e{};
+      e.lo0 = (int)(C.src_lo[0] - Bs.lo[0]);
+      e.lo1 = (int)(C.src_lo[1] - Bs.lo[1]);
+      e.lo2 = (int)(C.src_lo[2] - Bs.lo[2]);
+      e.hi0 = e.lo0 + (int)C.ext[0];
+      e.hi1 = e.lo1 + (int)C.ext[1];
+      e.hi2 = e.lo2 + (int)C.ext[2];
+      e.dbase = (int)index_of(C.dst_box, C.dst_lo);
+      e.dpy = (int)L->py[C.dst_box];
+      e.dpz = (int)L->pz[C.dst_box];
+      groups[(size_t)C.src_box * 6 + 2 * d + side].push_back(e);
+    }
+    std::vector<DPush> entries;
+    std::vector<int> gofs(1, 0);
+    for (const auto& g : groups) {
+      entries.insert(entries.end(), g.begin(), g.end());
+      gofs.push_back((int)entries.size());
+    }
+    rc = upload(&D->push, entries);
+    if (!rc) rc = upload(&D->push_gofs, gofs);
+    if (rc) return rc;
+  }
+
   // interior rectangles, and interior + six ghost slabs
   std::vector<DRect> irects, srects;
   std::vector<DChunk> ichunks, schunks, pchunks;
@@ -201,6 +239,7 @@ int ensure_device(sc_level* L) {
     r.ey = (int)n[1];
     r.ez = (int)n[2];
     r.dom = B.domain;
+    r.box = b;
     irects.push_back(r);
     add_chunks((int)irects.size() - 1, n[0] * n[1] * n[2], ichunks);
     add_chunks((int)irects.size() - 1, n[0] * n[1] * n[2], pchunks, dev::kGatherChunk);
@@ -326,6 +365,10 @@ struct Enq {
   int64_t* count;
   bool per_box;
   bool timed = false;
+  // ghost exchange of the stage outputs: false = a gather launch before each
+  // stage (best when a CUDA graph hides the launches), true = every stage
+  // kernel writes the ghost copies of what it produces (fewer launches)
+  bool push = false;
 };
 
 // Event pair around one launch when timing is on.
@@ -414,9 +457,15 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
   double* in_p[4] = {pi, W[1], W[3], W[1]};
   double* out_u[4] = {W[0], W[2], W[0], u};
   double* out_p[4] = {W[1], W[3], W[1], pi};
+  // with push, each stage writes the ghosts of its stencil output, so the
+  // next stage (and the next step) find theirs filled and only the first
+  // input of a run is gathered (enq_prologue); otherwise each stage gathers
   for (int s = 0; s < 4; ++s) {
-    cudaError_t e = enq_fill(q, in_u[s]);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (!q.push) {
+      e = enq_fill(q, in_u[s]);
+      if (e != cudaSuccess) return e;
+    }
     dev::FwdArgs a{};
     a.ndom = nd;
     a.boxes = D->boxes;
@@ -430,6 +479,8 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
     a.lapw = lapw ? lapw[s] : nullptr;
     a.q = qarr[s];
     a.qk = qk[s];
+    a.push = q.push ? D->push : nullptr;
+    a.push_gofs = q.push ? D->push_gofs : nullptr;
     a.coef = D->coef + s * nd;
     a.emax_in = D->emax + (s % 4) * nd;
     a.emax_out = D->emax + ((s + 1) % 4) * nd;
@@ -441,12 +492,17 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
   return cudaSuccess;
 }
 
-// Prologue of a run of steps: the pre-scaled wave speed q = c2 * dt/(12 h^2)
-// (and the 1/3 variant) in W[4], W[5]; for the fixed form, the exponent ring
-// cleared and slot 0 = max exponent of u.
-static cudaError_t enq_prologue(const Enq& q, const double* u, const double* c2,
+// Prologue of a run of steps: the ghosts of u gathered (push exchange); the
+// pre-scaled wave speed q = c2 * dt/(12 h^2) (and the 1/3 variant) in W[4],
+// W[5]; for the fixed form, the exponent ring cleared and slot 0 = max
+// exponent of u.
+static cudaError_t enq_prologue(const Enq& q, double* u, const double* c2,
                                 double* const* W) {
   DeviceState* D = q.L->dev;
+  if (q.push) {
+    cudaError_t e0 = enq_fill(q, u);  // ghosts of the run's first stencil input
+    if (e0 != cudaSuccess) return e0;
+  }
   (*q.count)++;
   cudaError_t e = dev::launch_qprep(D->irects, D->ichunks, D->nichunks, c2, W[4], W[5],
                                     D->qfac, D->grid_small, q.s);
@@ -657,6 +713,7 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
       return rc;
   L->tape_valid = false;
   Enq q{L, s, &L->launches, false};
+  q.push = true;
   if (L->profile) {
     q.timed = true;
     D->ev_used = 0;
@@ -717,6 +774,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     if ((rc = get_field(L, "lapw." + std::to_string(j), &lapw[j]))) return rc;
 
   Enq q{L, s, &L->launches, false};
+  q.push = true;
   if (L->profile) {
     q.timed = true;
     D->ev_used = 0;
@@ -749,6 +807,10 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
                           fixed ? slot(0) : nullptr, D->grid_small, s));
   SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yu, Y,
                           fixed ? slot(1) : nullptr, D->grid_small, s));
+  // the only gathers of the sweep: later stencil inputs have their ghosts
+  // pushed by the kernels that write them
+  SC_CUDA(enq_fill(q, X));
+  SC_CUDA(enq_fill(q, Y));
 
   long long n_adj = 0;
   for (int c = nck - 1; c >= 0; --c) {
@@ -766,8 +828,9 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
       a.boxes = D->boxes;
       a.c2 = c2;
       a.err = D->err;
+      a.push = D->push;
+      a.push_gofs = D->push_gofs;
       // P4hat = L^(c2 b), X' = c2 P4hat
-      SC_CUDA(enq_fill(q, X));
       a.z_in = X;
       a.p_out = P4;
       a.z_out = Xp;
@@ -780,7 +843,6 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
         SC_CUDA(dev::launch_adj(0, L->arith, a, D->grid_stage, s));
       }
       // P3hat = L^(c2 a), Y' = c2 P3hat
-      SC_CUDA(enq_fill(q, Y));
       a.z_in = Y;
       a.p_out = P3;
       a.z_out = Yq;
@@ -793,7 +855,6 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
         SC_CUDA(dev::launch_adj(0, L->arith, a, D->grid_stage, s));
       }
       // P2hat = L^ X'
-      SC_CUDA(enq_fill(q, Xp));
       a.z_in = Xp;
       a.p_out = P2;
       a.z_out = nullptr;
@@ -806,7 +867,6 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
         SC_CUDA(dev::launch_adj(1, L->arith, a, D->grid_stage, s));
       }
       // P1hat = L^ Y'
-      SC_CUDA(enq_fill(q, Yq));
       a.z_in = Yq;
       a.p_out = P1;
       a.emax_in = slot(5 + 2 * p);
@@ -833,6 +893,9 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
       b.x_out = X;
       b.y_out = Y;
       b.coef = D->acoef;
+      b.boxes = D->boxes;
+      b.push = D->push;
+      b.push_gofs = D->push_gofs;
       b.emax_x = slot(2 * pn);
       b.emax_y = slot(2 * pn + 1);
       L->launches++;

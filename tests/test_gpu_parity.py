@@ -218,7 +218,8 @@ def test_nonfinite_input_is_reported(B):
 def test_launch_count_grows():
     inst = W.plane_wave(16)
     lev, _, _ = run_gpu([inst], 2, 1, 0)
-    assert lev.launch_count() >= 2 * 8
+    # a gather and a stage kernel per stage, plus the run prologue
+    assert lev.launch_count() >= 2 * 8 + 2
 
 
 # ----------------------------------------------------------------------------
@@ -260,3 +261,31 @@ def test_full_uneven_level_vs_oracle(orc):
     _, u, pi = run_gpu([inst], 1, 1, 0)
     assert rel_err(u[0], ou) <= TOL
     assert rel_err(pi[0], op) <= TOL
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_ghosts_written_by_stage_kernels(orc, arith):
+    """In the taped forward the stage kernels write the ghost copies of every
+    value they produce; the final state's ghosts must equal a fresh exchange
+    of its interior, bit for bit, on a 64-box level and on a single box."""
+    import torch
+    for inst in (W.uneven_level(n=(96, 80, 64), h=1.0 / 64, levels=6, seed=3, box_seed=30),
+                 W.bumpy_instance(W.Domain((36, 28, 20), 1.0 / 28), 5)):
+        lev = make_level([inst])
+        lev.set_arith(arith)
+        u = upload(lev, [inst.u], fill=np.nan)
+        pi = upload(lev, [inst.pi])
+        c2 = upload(lev, [inst.c2], fill=1.0)
+        uT = torch.full_like(u, float("nan"))
+        piT = torch.empty_like(pi)
+        lev.forward_tape(u, pi, c2, inst.dt, 3, 2, uT, piT)
+        lev.sync()
+        got = lev.padded_boxes(uT)
+        want = lev.padded_boxes(lev.scatter([lev.gather(uT)[0]], fill=np.nan))
+        n = inst.dom.n
+        orc.fill_ghosts([lo + hi for lo, hi in inst.boxes], (0, 0, 0) + tuple(n), 7, want)
+        for a, b in zip(got, want):
+            m = ~np.isnan(b)
+            assert np.array_equal(a[m], b[m])
+        _, ug, _ = run_gpu([inst], 3, arith, 0)
+        assert np.array_equal(lev.gather(uT)[0], ug[0])
