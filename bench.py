@@ -63,6 +63,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(t: float, dist=None, device=None) -> float:
+    """The largest of every rank's value (the job's time); t itself when
+    running alone."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank: float, t_max: float, world: int) -> float:
+    """Whole-job throughput: every rank processes units_per_rank units (an
+    independent replica) and the job takes the slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -359,11 +376,8 @@ def run_ours(a, ws, rank, local):
     clk = clocks.stop()
     lev.sync(stream)
     launches = lev.launch_count() - launches0
-    if dist:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = tt.item()
-    value = npts * nsub * a.steps * ws / t
+    t = max_over_ranks(t, dist, "cuda")
+    value = job_rate(npts * nsub * a.steps, t, ws)
 
     # dominant kernel: the stage kernel, timed per launch with CUDA events
     lev.rk4_step(u, pi, c2, inst.dt, nsub, B.SC_MODE_TIMED, stream=stream)
@@ -391,12 +405,9 @@ def run_ours(a, ws, rank, local):
     for _ in range(a.steps):
         lev.rk4_step_host(hun, hpn, hcn, inst.dt, nsub, oun, opn, stream=stream)
     te2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([te2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te2e = tt.item()
+    te2e = max_over_ranks(te2e, dist, "cuda")
     fbytes = lev.field_size * 8
-    e2e = {"value": npts * nsub * a.steps * ws / te2e, "unit": UNIT,
+    e2e = {"value": job_rate(npts * nsub * a.steps, te2e, ws), "unit": UNIT,
            "h2d_bytes_per_step": 3 * fbytes, "d2h_bytes_per_step": 2 * fbytes}
 
     extras = {}

@@ -1,0 +1,44 @@
+"""The multi-rank bookkeeping of bench.py on CPU: two gloo ranks, each timing
+an independent replica, agree on the job time (the slower rank's) and on the
+whole-job throughput (both replicas' units over that time)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t_local = 1.0 + rank  # rank 1 is the slow one
+    t = bench.max_over_ranks(t_local, dist, "cpu")
+    out[rank] = (t, bench.job_rate(100.0, t, world))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_time_and_rate():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0] == res[1] == (2.0, 100.0)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.job_rate(10.0, 2.0, 1) == 5.0
