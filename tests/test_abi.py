@@ -291,3 +291,10 @@ def test_exchange_full_uneven_level_counts(B):
         lo, hi = np.array(inst.boxes[sb][0]), np.array(inst.boxes[sb][1])
         assert (slo >= lo).all() and (slo + e <= hi).all()
         assert ((dlo - slo) % N == 0).all()
+
+
+def test_level_too_large_is_rejected(B):
+    from paper_1308_1343_gb300.level import Level
+    n = (2048, 2048, 520)  # (2048+16) * (2048+4) * (520+4) > 2^31 doubles
+    with pytest.raises(B.ScError, match="too large"):
+        Level([((0, 0, 0), n, 0)], [dict(hi=n, h=0.1)])

@@ -289,3 +289,59 @@ def test_ghosts_written_by_stage_kernels(orc, arith):
             assert np.array_equal(a[m], b[m])
         _, ug, _ = run_gpu([inst], 3, arith, 0)
         assert np.array_equal(lev.gather(uT)[0], ug[0])
+
+
+# ----------------------------------------------------------------------------
+# degenerate cases
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_thin_and_odd_boxes(orc, arith):
+    """Boxes of edge 2 and 3 and odd sizes on one periodic level."""
+    n = (13, 11, 9)
+    boxes = [((0, 0, 0), (2, 11, 9)), ((2, 0, 0), (5, 11, 9)), ((5, 0, 0), (13, 4, 9)),
+             ((5, 4, 0), (13, 11, 2)), ((5, 4, 2), (13, 11, 9))]
+    inst = W.bumpy_instance(W.Domain(n, 1.0 / 11), 7)
+    inst.boxes = boxes
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 4)
+    for mode in (0, 1):
+        _, u, pi = run_gpu([inst], 4, arith, mode)
+        assert rel_err(u[0], ou) <= TOL
+        assert rel_err(pi[0], op) <= TOL
+
+
+def test_zero_steps_and_zero_field():
+    inst = W.bumpy_instance(W.Domain((20, 16, 12), 1.0 / 16), 3)
+    lev, u, pi = run_gpu([inst], 0, 1, 0)
+    assert np.array_equal(u[0], inst.u) and np.array_equal(pi[0], inst.pi)
+    z = W.Instance(inst.dom, np.zeros_like(inst.u), np.zeros_like(inst.u), inst.c2, inst.dt)
+    _, u, pi = run_gpu([z], 3, 1, 0)
+    assert not np.any(u[0]) and not np.any(pi[0])
+
+
+@pytest.mark.parametrize("scale", [1e250, 1e-250])
+def test_extreme_amplitudes(orc, scale):
+    """The fixed-point scale follows the field's exponent: amplitudes near
+    the ends of the FP64 range keep the 1e-12 bar."""
+    inst = W.bumpy_instance(W.Domain((24, 20, 16), 1.0 / 20), 9)
+    big = W.Instance(inst.dom, inst.u * scale, inst.pi, inst.c2, inst.dt)
+    ou, op = orc.rk4_periodic(big.u, big.pi, big.c2, big.dom.h, big.dt, 3)
+    for arith in (0, 1):
+        _, u, pi = run_gpu([big], 3, arith, 0)
+        assert rel_err(u[0], ou) <= TOL
+        assert rel_err(pi[0], op) <= TOL
+
+
+def test_amplitude_below_fixed_point_floor(orc):
+    """Below 2^-959 the fixed form keeps an absolute resolution of 2^-1013
+    (the exponent bound is clamped at 64): results stay finite and within
+    that absolute bound of the oracle."""
+    inst = W.bumpy_instance(W.Domain((24, 20, 16), 1.0 / 20), 9)
+    tiny = W.Instance(inst.dom, inst.u * 1e-295, inst.pi, inst.c2, inst.dt)
+    ou, op = orc.rk4_periodic(tiny.u, tiny.pi, tiny.c2, tiny.dom.h, tiny.dt, 2)
+    _, u, pi = run_gpu([tiny], 2, 1, 0)
+    assert np.all(np.isfinite(u[0])) and np.all(np.isfinite(pi[0]))
+    h = tiny.dom.h
+    # per stage the Laplacian is off by at most 192 2^-1013 / (12 h^2)
+    bound = 8 * 192 * 2.0 ** -1013 / (12 * h * h) * (tiny.dt + 1)
+    assert np.abs(pi[0] - op).max() <= bound
