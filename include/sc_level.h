@@ -162,6 +162,28 @@ int sc_level_set_arith(sc_level* level, int32_t arith);
 int sc_level_set_tuning(sc_level* level, int32_t size_class, const sc_tile* tile,
                         int32_t ctas_per_sm);
 
+/* The tile of one size class as the kernels use it: set by
+ * sc_level_set_tuning or sc_level_autotune, else the heuristic default
+ * (whose tile_z is final only once the level has device state). */
+int sc_level_get_tuning(const sc_level* level, int32_t size_class, sc_tile* tile);
+
+/* RK4 stages per stencil pass in sc_level_rk4_step (default 1).
+ * 1: one launch per stage, w_s = y + g_s A w_{s-1} as in the paper's
+ *    method-of-lines stage loop.
+ * 2: two launches per step.  Only the u-component goes through L and
+ *    w_s.u is pointwise in (y.u, w_{s-1}.pi), so by linearity
+ *    L w_1.u = L y.u + g_1 L y.pi and L w_3.u = L y.u + g_3 L w_2.pi: pass A
+ *    applies L to y.u and y.pi and gives w_2 (and L y.u), pass B applies L to
+ *    w_2.u and w_2.pi and gives the new y, every stencil still of radius 2
+ *    and every exchange still two points deep (two fields per exchange).
+ *    This is loop fusion chosen per run (arXiv 1308.1343, Sec. 3.3, fusing
+ *    loops as a tuning option).  Results equal the one-stage form up to
+ *    rounding.  The taped forward (sc_level_forward_tape) and
+ *    sc_box_rk4_step_noalloc always run one stage per pass.
+ * Errors: SC_EINVAL for other values. */
+int sc_level_set_fusion(sc_level* level, int32_t stages_per_pass);
+int sc_level_get_fusion(const sc_level* level, int32_t* stages_per_pass);
+
 /* Number of box-size classes and the class of each box (boxes are grouped
  * by interior extent rounded up to a multiple of 8 per axis). */
 int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
@@ -262,6 +284,8 @@ int sc_level_sync(sc_level* level, void* stream);
 #define SC_KERNEL_ADJ_A 3        /* adjoint: L(c2 .) with c2 product output  */
 #define SC_KERNEL_ADJ_B 4        /* adjoint: L(c2 .)                          */
 #define SC_KERNEL_ADJ_C 5        /* adjoint: pointwise combination           */
+#define SC_KERNEL_PAIR_A 6       /* two-stage pass A (stages 1, 2)           */
+#define SC_KERNEL_PAIR_B 7       /* two-stage pass B (stages 3, 4)           */
 
 /* Per-kernel device times of the last timed call: sc_level_rk4_step with
  * SC_MODE_TIMED, or sc_level_forward_tape / sc_level_backward_tape while

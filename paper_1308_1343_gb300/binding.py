@@ -17,7 +17,7 @@ SC_ARITH_FP64, SC_ARITH_FIXED = 0, 1
 SC_MODE_GRAPH, SC_MODE_PER_BOX, SC_MODE_BATCHED, SC_MODE_TIMED = 0, 1, 2, 3
 SC_SET_UNION, SC_SET_INTERSECTION, SC_SET_DIFFERENCE, SC_SET_XOR = 0, 1, 2, 3
 (SC_KERNEL_STAGE, SC_KERNEL_GATHER, SC_KERNEL_STAGE_RECORD, SC_KERNEL_ADJ_A, SC_KERNEL_ADJ_B,
- SC_KERNEL_ADJ_C) = range(6)
+ SC_KERNEL_ADJ_C, SC_KERNEL_PAIR_A, SC_KERNEL_PAIR_B) = range(8)
 
 _i32, _i64, _u32, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
 _vp = ctypes.c_void_p
@@ -59,6 +59,9 @@ _SIGS = {
     "sc_level_set_arith": (_i32, [_vp, _i32]),
     "sc_level_set_tuning": (_i32, [_vp, _i32, ctypes.POINTER(ScTile), _i32]),
     "sc_level_size_classes": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "sc_level_get_tuning": (_i32, [_vp, _i32, ctypes.POINTER(ScTile)]),
+    "sc_level_set_fusion": (_i32, [_vp, _i32]),
+    "sc_level_get_fusion": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "sc_level_autotune": (_i32, [_vp, _i32, _dbl, _dbl, ctypes.c_char_p, _vp]),
     "sc_level_fill_ghosts": (_i32, [_vp, _vp, _vp]),
     "sc_level_apply_laplacian": (_i32, [_vp, _vp, _vp, _vp]),

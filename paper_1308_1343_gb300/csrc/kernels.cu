@@ -25,8 +25,13 @@ constexpr int NT = 256;
 // the exchange list, one launch.
 // ---------------------------------------------------------------------------
 
+template <bool TWO>
 __global__ void __launch_bounds__(kGatherChunk) gather_kernel(
-    const DRect* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks, double* f) {
+    const DRect* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks, double* f,
+    double* g, unsigned* clear, int nclear) {
+  // exponent slots that the next kernel accumulates into start at zero
+  if (clear && blockIdx.x == 0)
+    for (int d = threadIdx.x; d < nclear; d += blockDim.x) clear[d] = 0u;
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const DChunk ch = chunks[c];
     const DRect r = rects[ch.rect];
@@ -37,8 +42,10 @@ __global__ void __launch_bounds__(kGatherChunk) gather_kernel(
       const int z = t / r.ey;
       const int y = t - z * r.ey;
       // offsets fit 32 bits: a field holds fewer than 2^31 doubles
-      f[(int)r.dst + x + y * (int)r.dpy + z * (int)r.dpz] =
-          f[(int)r.src + x + y * (int)r.spy + z * (int)r.spz];
+      const int dst = (int)r.dst + x + y * (int)r.dpy + z * (int)r.dpz;
+      const int src = (int)r.src + x + y * (int)r.spy + z * (int)r.spz;
+      f[dst] = f[src];
+      if (TWO) g[dst] = g[src];
     }
   }
 }
@@ -262,6 +269,104 @@ __global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Two RK4 stages per pass
+// ---------------------------------------------------------------------------
+//
+// Only the u-component passes through the stencil, and w_s.u is pointwise in
+// (y.u, w_{s-1}.pi).  So by linearity of L
+//     L w_1.u = L y.u + g_1 L y.pi,     L w_3.u = L y.u + g_3 L w_2.pi,
+// and a step splits into two passes whose stencils all have radius 2:
+//   pass A (stages 1, 2), stencils of y.u and y.pi:
+//     w_1.pi = y.pi + g_1 c2 L y.u        w_2.u  = y.u + g_2 w_1.pi
+//     w_2.pi = y.pi + g_2 c2 (L y.u + g_1 L y.pi),   and it stores L y.u;
+//   pass B (stages 3, 4), stencils of w_2.u and w_2.pi:
+//     w_3.pi = y.pi + g_3 c2 L w_2.u      y.u   <- y.u + g_4 w_3.pi
+//     y.pi  <- y.pi + g_4 c2 (L y.u + g_3 L w_2.pi)   (in place).
+// Per point and step: 2 FP64 FMAs and one int->FP64 conversion per stage as
+// in the one-stage kernels, but 15 instead of 26 doubles moved (A: read y.u,
+// y.pi, q, q/3; write w_2, L y.u.  B: read w_2, y, q, L y.u; write y).
+// Results differ from the one-stage form by rounding only.
+
+template <class A, bool SECOND>
+struct PairEpi {
+  static constexpr int NF = 4;  // y.u, y.pi, q = c2 dt/(12 h^2), then A: q/3, B: L y.u
+  const double* f[NF];
+  double* out_u;
+  double* out_p;
+  double* __restrict__ ly;  // pass A: 12 h^2 L y.u
+  A a0, a1;                 // arithmetic of the two stencil fields
+  double ga, gb;            // A: g_1, g_2.  B: g_3, g_4
+  unsigned eu, ep;
+
+  // one point: s0, s1 the two stencil sums, x the pointwise fields
+  __device__ __forceinline__ void one(typename A::T s0, typename A::T s1, double u0, double p0,
+                                      double q, double x, double& un, double& pn,
+                                      double& lyv) const {
+    if (!SECOND) {
+      const double dU = a0.scaled(s0, 0);  // 12 h^2 L y.u
+      const double dP = a1.scaled(s1, 0);  // 12 h^2 L y.pi
+      const double w1p = fma(q, a0.rescale(dU, -2), p0);
+      un = fma(gb, w1p, u0);
+      pn = fma(x, fma(ga, dP, dU), p0);
+      lyv = dU;
+    } else {
+      const double w3p = fma(q, a0.scaled(s0, -1), p0);  // 12 h^2 L w_2.u * 1/2
+      un = fma(gb, w3p, u0);
+      pn = fma(q, fma(ga, a1.scaled(s1, 0), x), p0);
+    }
+  }
+
+  __device__ __forceinline__ void point(int i, const double2* pw,
+                                        const typename A::T (&rA)[2],
+                                        const typename A::T (&rB)[2], bool actB, int, int,
+                                        int) {
+    const double2 u0 = pw[0], p0 = pw[1], q = pw[2], x = pw[3];
+    double2 un, pn, lv;
+    one(rA[0], rA[1], u0.x, p0.x, q.x, x.x, un.x, pn.x, lv.x);
+    one(rB[0], rB[1], u0.y, p0.y, q.y, x.y, un.y, pn.y, lv.y);
+    if (actB) {
+      st2(out_u + i, un);
+      st2(out_p + i, pn);
+      if (!SECOND) st2(ly + i, lv);
+    } else {
+      out_u[i] = un.x;
+      out_p[i] = pn.x;
+      if (!SECOND) ly[i] = lv.x;
+    }
+    if (A::kFixed) {
+      eu = max(eu, biased_exp(un.x));
+      ep = max(ep, biased_exp(pn.x));
+      if (actB) {
+        eu = max(eu, biased_exp(un.y));
+        ep = max(ep, biased_exp(pn.y));
+      }
+    }
+  }
+};
+
+template <class A, bool SECOND>
+__global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
+  __shared__ Smem<NT, A, 4, 2> smem;
+  __shared__ unsigned red[2 * NT / 32];
+  unsigned err = 0;
+  const double* const F[2] = {a.s0, a.s1};
+  for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
+    const DItem it = a.items[i];
+    const DBox bx = a.boxes[it.box];
+    const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
+                     make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
+    const int s0 = SECOND ? 2 : 0;  // stage coefficients g_{s0+1}, g_{s0+2}
+    PairEpi<A, SECOND> epi{{a.yu, a.yp, a.q, a.x}, a.out_u, a.out_p, a.ly, ar[0], ar[1],
+                           a.coef[s0 * a.ndom + bx.dom].gamma,
+                           a.coef[(s0 + 1) * a.ndom + bx.dom].gamma, 0u, 0u};
+    run_items<NT, 2>(it, bx, F, ar, smem, err, epi);
+    if (A::kFixed)
+      cta_max2_to(epi.eu, epi.ep, a.emax_out + bx.dom, a.emax_out + a.ndom + bx.dom, red);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+// ---------------------------------------------------------------------------
 // out = L u
 // ---------------------------------------------------------------------------
 
@@ -465,7 +570,16 @@ cudaError_t launch_gather(const DRect* rects, const DChunk* chunks, int nchunks,
                           int grid, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   (void)grid;
-  gather_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, f);
+  gather_kernel<false><<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, f, nullptr,
+                                                         nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
+                           double* g, unsigned* clear, int nclear, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  gather_kernel<true><<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, f, g, clear,
+                                                        nclear);
   return cudaGetLastError();
 }
 
@@ -528,6 +642,10 @@ static void set_carveouts() {
   prefer_shared(adj_b_kernel<Fp64>);
   prefer_shared(lap_kernel<Fixed>);
   prefer_shared(lap_kernel<Fp64>);
+  prefer_shared(pair_kernel<Fixed, false>);
+  prefer_shared(pair_kernel<Fixed, true>);
+  prefer_shared(pair_kernel<Fp64, false>);
+  prefer_shared(pair_kernel<Fp64, true>);
 }
 
 cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
@@ -587,6 +705,33 @@ cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chun
   else
     adj_combine_kernel<false><<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s) {
+  if (a.nitems <= 0) return cudaSuccess;
+  set_carveouts();
+  grid = min(grid, a.nitems);
+  if (arith == 1) {
+    if (second)
+      pair_kernel<Fixed, true><<<grid, NT, 0, s>>>(a);
+    else
+      pair_kernel<Fixed, false><<<grid, NT, 0, s>>>(a);
+  } else {
+    if (second)
+      pair_kernel<Fp64, true><<<grid, NT, 0, s>>>(a);
+    else
+      pair_kernel<Fp64, false><<<grid, NT, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {
+  set_carveouts();
+  if (arith == 1)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                         pair_kernel<Fixed, true>, NT, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pair_kernel<Fp64, true>,
+                                                       NT, 0);
 }
 
 int stage_threads() { return NT; }

@@ -191,6 +191,8 @@ struct Fp64 {
   __device__ __forceinline__ static double to_double(T r) { return r; }
   // r * 2^(k - S) with S = 0: an exact power-of-two multiply
   __device__ __forceinline__ double scaled(T r, int k) const { return r * exp2_int(k); }
+  // d * 2^k for a result d of scaled()
+  __device__ __forceinline__ double rescale(double d, int k) const { return d * exp2_int(k); }
 };
 
 struct Fixed {
@@ -219,6 +221,12 @@ struct Fixed {
                            ((long long)(k - (1077 - E)) << 52);
     return r == 0 ? 0.0 : __longlong_as_double(bits);
   }
+  // d * 2^k for a result d of scaled() and -8 <= k <= 0: every nonzero d has
+  // |d| >= 2^(E - 1077) >= 2^-1013, so the product stays normal and the
+  // exponent field can be adjusted on the integer pipe
+  __device__ __forceinline__ double rescale(double d, int k) const {
+    return d == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) + ((long long)k << 52));
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -235,9 +243,11 @@ struct TileSmem {
   static constexpr int kMaxElems = kA > kB ? kA : kB;
 };
 
-template <int NT, class A, int NF>
+// NS stencil fields share the traversal (one pipeline, one barrier per
+// plane); field f uses tile buffers 2f and 2f+1.
+template <int NT, class A, int NF, int NS = 1>
 struct Smem {
-  typename A::T tile[2 * TileSmem<NT>::kMaxElems];
+  typename A::T tile[2 * NS * TileSmem<NT>::kMaxElems];
   double2 pw[2][NF > 0 ? NF : 1][NT];
 };
 
@@ -248,18 +258,20 @@ __device__ __forceinline__ int out_of(int c, int n) {
   return (unsigned)c < (unsigned)n ? 0 : ((c >= -2 && c < n + 2) ? 1 : 2);
 }
 
-// Walk one work item.  `F` is the stencil field (its ghosts filled).  The
-// epilogue names Epi::NF pointwise fields (epi.f[0..NF)) that the traversal
-// streams into shared memory; for every plane k it calls
+// Walk one work item over NS stencil fields F[0..NS) (ghosts filled), field
+// f in the arithmetic arith[f].  The epilogue names Epi::NF pointwise fields
+// (epi.f[0..NF)) that the traversal streams into shared memory; for every
+// plane k it calls
 //   epi.point(idx, pw, rA, rB, actB, x, y, k)
 // on the threads owning interior points, with idx the element index of the
-// thread's first point (x, y, k), pw[f] its pair of field f, and rA, rB the
-// unscaled sums r = 12 h^2 (L F) at both points in the policy's integer or
-// FP64 form.
-template <int NT, class A, class Epi>
-__device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
-                                         const double* __restrict__ F, A arith,
-                                         Smem<NT, A, Epi::NF>& sm, unsigned& err, Epi& epi) {
+// thread's first point (x, y, k), pw[j] its pair of pointwise field j, and
+// rA[f], rB[f] the unscaled sums r = 12 h^2 (L F[f]) at both points in the
+// policy's integer or FP64 form.
+template <int NT, int NS, class A, class Epi>
+__device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
+                                          const double* const (&F)[NS], const A (&arith)[NS],
+                                          Smem<NT, A, Epi::NF, NS>& sm, unsigned& err,
+                                          Epi& epi) {
   using T = typename A::T;
   using T2 = typename A::T2;
   constexpr int NF = Epi::NF;
@@ -311,9 +323,9 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
       hx1 = out_of(ax + 1, bx.nx) + o;
     }
   }
-  auto conv_at = [&](double2 raw, int k) -> T2 {
+  auto conv_at = [&](int f, double2 raw, int k) -> T2 {
     const int oz = out_of(k, bx.nz);
-    return arith.conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
+    return arith[f].conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
   };
 
   // running element offsets (advance by one plane per iteration)
@@ -330,33 +342,44 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
     op += pz;
   };
 
-  T2 qa = conv_at(ld2(F + oc - 4 * pz), it.z0 - 2);
-  T2 qb = conv_at(ld2(F + oc - 3 * pz), it.z0 - 1);
-  T2 qc = conv_at(ld2(F + oc - 2 * pz), it.z0);
-  T2 qd = conv_at(ld2(F + oc - pz), it.z0 + 1);
-  T2 qe;
-  double2 rc = ld2(F + oc);  // raw column of plane k+2
+  T2 qa[NS], qb[NS], qc[NS], qd[NS], qe[NS];
+  double2 rc[NS], rh[NS];  // raw column of plane k+2, raw halo pair of plane k
+#pragma unroll
+  for (int f = 0; f < NS; ++f) {
+    qa[f] = conv_at(f, ld2(F[f] + oc - 4 * pz), it.z0 - 2);
+    qb[f] = conv_at(f, ld2(F[f] + oc - 3 * pz), it.z0 - 1);
+    qc[f] = conv_at(f, ld2(F[f] + oc - 2 * pz), it.z0);
+    qd[f] = conv_at(f, ld2(F[f] + oc - pz), it.z0 + 1);
+    rc[f] = ld2(F[f] + oc);
+    rh[f] = ld2(F[f] + oh);
+  }
   oc += pz;
-  double2 rh = ld2(F + oh);  // raw halo pair of plane k
   oh += pz;
   stage_pw(0);
 
   const int rowSelf = (ly + 2) * W + 2 * lx + 2;
   // one plane: m2..p1 hold planes k-2..k+1; p2 receives plane k+2
-  auto plane = [&](int kk, const T2& m2, const T2& m1, const T2& c0, const T2& p1, T2& p2) {
+  auto plane = [&](int kk, const T2 (&m2)[NS], const T2 (&m1)[NS], const T2 (&c0)[NS],
+                   const T2 (&p1)[NS], T2 (&p2)[NS]) {
     const int k = it.z0 + kk;
-    p2 = conv_at(rc, k + 2);
-    T* buf = sm.tile + (kk & 1) * bufElems;
-    *reinterpret_cast<T2*>(buf + rowSelf) = c0;
-    if (hasH) {
-      const int oz = out_of(k, bx.nz);
-      *reinterpret_cast<T2*>(buf + hs) = arith.conv(rh, hx0 + oz <= 1, hx1 + oz <= 1, err);
+    const int oz = out_of(k, bx.nz);
+#pragma unroll
+    for (int f = 0; f < NS; ++f) {
+      p2[f] = conv_at(f, rc[f], k + 2);
+      T* buf = sm.tile + (2 * f + (kk & 1)) * bufElems;
+      *reinterpret_cast<T2*>(buf + rowSelf) = c0[f];
+      if (hasH)
+        *reinterpret_cast<T2*>(buf + hs) =
+            arith[f].conv(rh[f], hx0 + oz <= 1, hx1 + oz <= 1, err);
     }
     // issue the next plane's loads before waiting on this one
     if (kk + 1 < it.nzr) {
-      rc = ld2(F + oc);
+#pragma unroll
+      for (int f = 0; f < NS; ++f) {
+        rc[f] = ld2(F[f] + oc);
+        rh[f] = ld2(F[f] + oh);
+      }
       oc += pz;
-      rh = ld2(F + oh);
       oh += pz;
       stage_pw((kk + 1) & 1);
     } else {
@@ -365,18 +388,22 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
     cp_async_wait_one();
     __syncthreads();
     if (actA) {
-      const T* row = buf + rowSelf;
-      const T2 xm = *reinterpret_cast<const T2*>(row - 2);
-      const T2 xp = *reinterpret_cast<const T2*>(row + 2);
-      const T2 ym1 = *reinterpret_cast<const T2*>(row - W);
-      const T2 ym2 = *reinterpret_cast<const T2*>(row - 2 * W);
-      const T2 yp1 = *reinterpret_cast<const T2*>(row + W);
-      const T2 yp2 = *reinterpret_cast<const T2*>(row + 2 * W);
-      // point A at x, point B at x+1
-      const T rA = A::lap(c0.x, xm.y, c0.y, ym1.x, yp1.x, m1.x, p1.x,
-                          xm.x, xp.x, ym2.x, yp2.x, m2.x, p2.x);
-      const T rB = A::lap(c0.y, c0.x, xp.x, ym1.y, yp1.y, m1.y, p1.y,
-                          xm.y, xp.y, ym2.y, yp2.y, m2.y, p2.y);
+      T rA[NS], rB[NS];
+#pragma unroll
+      for (int f = 0; f < NS; ++f) {
+        const T* row = sm.tile + (2 * f + (kk & 1)) * bufElems + rowSelf;
+        const T2 xm = *reinterpret_cast<const T2*>(row - 2);
+        const T2 xp = *reinterpret_cast<const T2*>(row + 2);
+        const T2 ym1 = *reinterpret_cast<const T2*>(row - W);
+        const T2 ym2 = *reinterpret_cast<const T2*>(row - 2 * W);
+        const T2 yp1 = *reinterpret_cast<const T2*>(row + W);
+        const T2 yp2 = *reinterpret_cast<const T2*>(row + 2 * W);
+        // point A at x, point B at x+1
+        rA[f] = A::lap(c0[f].x, xm.y, c0[f].y, ym1.x, yp1.x, m1[f].x, p1[f].x,
+                       xm.x, xp.x, ym2.x, yp2.x, m2[f].x, p2[f].x);
+        rB[f] = A::lap(c0[f].y, c0[f].x, xp.x, ym1.y, yp1.y, m1[f].y, p1[f].y,
+                       xm.y, xp.y, ym2.y, yp2.y, m2[f].y, p2[f].y);
+      }
       double2 pw[NF > 0 ? NF : 1];
 #pragma unroll
       for (int f = 0; f < NF; ++f) pw[f] = sm.pw[kk & 1][f][tid];
@@ -399,6 +426,54 @@ __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
   }
   cp_async_wait_all();
   __syncthreads();  // the next item reuses the buffers
+}
+
+// One stencil field: epi.point receives the two sums as scalars.
+template <class Epi>
+struct OneField {
+  static constexpr int NF = Epi::NF;
+  Epi& e;
+  const double* const* f;
+  template <class T>
+  __device__ __forceinline__ void point(int i, const double2* pw, const T (&rA)[1],
+                                        const T (&rB)[1], bool actB, int x, int y, int k) {
+    e.point(i, pw, rA[0], rB[0], actB, x, y, k);
+  }
+};
+
+template <int NT, class A, class Epi>
+__device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
+                                         const double* __restrict__ F, A arith,
+                                         Smem<NT, A, Epi::NF>& sm, unsigned& err, Epi& epi) {
+  const double* const Fs[1] = {F};
+  const A as[1] = {arith};
+  OneField<Epi> one{epi, epi.f};
+  run_items<NT, 1>(it, bx, Fs, as, sm, err, one);
+}
+
+// Largest biased exponents of two fields over the CTA, one atomicMax per CTA
+// and field (red holds 2 * warps entries).
+__device__ __forceinline__ void cta_max2_to(unsigned a, unsigned b, unsigned* da, unsigned* db,
+                                            unsigned* red) {
+  a = __reduce_max_sync(0xffffffffu, a);
+  b = __reduce_max_sync(0xffffffffu, b);
+  const int nw = (int)(blockDim.x >> 5);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[w] = a;
+    red[nw + w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    unsigned x = l < nw ? red[l] : 0u, y = l < nw ? red[nw + l] : 0u;
+    x = __reduce_max_sync(0xffffffffu, x);
+    y = __reduce_max_sync(0xffffffffu, y);
+    if (l == 0) {
+      if (x) atomicMax(da, x);
+      if (y) atomicMax(db, y);
+    }
+  }
+  __syncthreads();
 }
 
 // Largest biased exponent over the CTA, one atomicMax per CTA.

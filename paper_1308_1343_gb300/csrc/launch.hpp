@@ -50,6 +50,27 @@ struct FwdArgs {
   unsigned* err;
 };
 
+// Two RK4 stages per pass (pass A: stages 1-2, pass B: stages 3-4).
+struct PairArgs {
+  const DItem* items;
+  int nitems;
+  int ndom;
+  const DBox* boxes;
+  const double* s0;  // stencil fields, ghosts filled: A: y.u, y.pi.  B: w_2.u, w_2.pi
+  const double* s1;
+  const double* yu;  // pointwise: the step input y
+  const double* yp;
+  const double* q;   // c2 dt/(12 h^2), pre-scaled per run
+  const double* x;   // A: c2 (dt/3)/(12 h^2).  B: 12 h^2 L y.u written by A
+  double* out_u;     // A: w_2.u, w_2.pi.  B: y.u, y.pi (in place)
+  double* out_p;
+  double* ly;        // A: 12 h^2 L y.u
+  const StageCoef* coef;    // [4 ndom], stage s at s * ndom
+  const unsigned* emax_in;  // [2 ndom]: exponent bounds of s0, s1
+  unsigned* emax_out;       // [2 ndom]: of out_u, out_p (zero on entry)
+  unsigned* err;
+};
+
 struct LapArgs {
   const DItem* items;
   int nitems;
@@ -119,6 +140,11 @@ cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
 cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
                              cudaStream_t s);
 cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s);
+cudaError_t pair_occupancy(int arith, int* blocks_per_sm);
+// two fields over one exchange list; block 0 zeroes clear[0..nclear)
+cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
+                           double* g, unsigned* clear, int nclear, cudaStream_t s);
 // kind 0: adj_a (Phat and c2 Phat), kind 1: adj_b (Phat only)
 cudaError_t launch_adj(int kind, int arith, const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chunks,

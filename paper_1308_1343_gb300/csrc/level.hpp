@@ -87,6 +87,7 @@ struct DeviceState {
   size_t ev_used = 0;
   std::vector<int> ev_kind;  // SC_KERNEL_* of each timed launch
   int grid_stage = 0;  // persistent grid of the stage kernels
+  int grid_pair = 0;   // persistent grid of the two-stage kernels
   int grid_small = 0;  // grid of the gather / reduction kernels
 };
 
@@ -101,6 +102,7 @@ struct sc_level {
   std::vector<int> box_class;
   std::vector<sc::SizeClass> classes;
   int arith = SC_ARITH_FIXED;
+  int fuse = 1;  // RK4 stages per stencil pass of sc_level_rk4_step: 1 or 2
   int ctas_per_sm = 0;
   int version = 0;  // bumps when items change (invalidates graphs)
   int64_t launches = 0;

@@ -287,6 +287,28 @@ int sc_level_set_arith(sc_level* L, int32_t arith) {
   return SC_OK;
 }
 
+int sc_level_set_fusion(sc_level* L, int32_t stages_per_pass) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (stages_per_pass != 1 && stages_per_pass != 2)
+    return set_error(SC_EINVAL, "stages_per_pass must be 1 or 2");
+  L->fuse = stages_per_pass;  // the step graphs are keyed by it
+  return SC_OK;
+}
+
+int sc_level_get_fusion(const sc_level* L, int32_t* stages_per_pass) {
+  if (!L || !stages_per_pass) return set_error(SC_EINVAL, "NULL argument");
+  *stages_per_pass = L->fuse;
+  return SC_OK;
+}
+
+int sc_level_get_tuning(const sc_level* L, int32_t size_class, sc_tile* tile) {
+  if (!L || !tile) return set_error(SC_EINVAL, "NULL argument");
+  if (size_class < 0 || size_class >= (int32_t)L->classes.size())
+    return set_error(SC_EINVAL, "bad class");
+  *tile = L->classes[size_class].tile;
+  return SC_OK;
+}
+
 int sc_level_launch_count(const sc_level* L, int64_t* n) {
   if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
   *n = L->launches;

@@ -71,6 +71,9 @@ int upload_items(sc_level* L) {
   SC_CUDA(dev::stage_occupancy(L->arith, &occ));
   const int per_sm = L->ctas_per_sm > 0 ? L->ctas_per_sm : std::max(1, occ);
   D->grid_stage = D->sms * per_sm;
+  int occ2 = 0;
+  SC_CUDA(dev::pair_occupancy(L->arith, &occ2));
+  D->grid_pair = D->sms * std::max(1, occ2);
   std::vector<DItem> items;
   build_items(L, items, D->box_items);
   // heuristic first choice (the paper's initial parameters, Sec. 3.2): while
@@ -492,11 +495,104 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
   return cudaSuccess;
 }
 
+// Ghost gather of two fields; the exponent slots `clear` (2 ndom, may be
+// NULL) are zeroed for the kernel that follows.
+static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear) {
+  DeviceState* D = q.L->dev;
+  const int nclear = clear ? 2 * (int)q.L->doms.size() : 0;
+  bool cleared = clear == nullptr;
+  if (!q.per_box) {
+    if (D->ngchunks > 0) {
+      (*q.count)++;
+      TimedLaunch t(q, SC_KERNEL_GATHER);
+      cudaError_t e = dev::launch_gather2(D->grects, D->gchunks, D->ngchunks, f, g, clear,
+                                          nclear, q.s);
+      if (e != cudaSuccess) return e;
+      cleared = true;
+    }
+  } else {
+    for (size_t b = 0; b + 1 < D->box_gchunks.size(); ++b) {
+      const int n = D->box_gchunks[b + 1] - D->box_gchunks[b];
+      if (n <= 0) continue;
+      (*q.count)++;
+      TimedLaunch t(q, SC_KERNEL_GATHER);
+      cudaError_t e = dev::launch_gather2(D->grects, D->gchunks + D->box_gchunks[b], n, f, g,
+                                          cleared ? nullptr : clear, nclear, q.s);
+      if (e != cudaSuccess) return e;
+      cleared = true;
+    }
+  }
+  if (!cleared) return cudaMemsetAsync(clear, 0, sizeof(unsigned) * nclear, q.s);
+  return cudaSuccess;
+}
+
+static cudaError_t enq_pair(const Enq& q, dev::PairArgs a, bool second) {
+  DeviceState* D = q.L->dev;
+  const int kind = second ? SC_KERNEL_PAIR_B : SC_KERNEL_PAIR_A;
+  if (!q.per_box) {
+    a.items = D->items;
+    a.nitems = D->nitems;
+    (*q.count)++;
+    TimedLaunch t(q, kind);
+    return dev::launch_pair(q.L->arith, second, a, D->grid_pair, q.s);
+  }
+  for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
+    a.items = D->items + D->box_items[b];
+    a.nitems = D->box_items[b + 1] - D->box_items[b];
+    (*q.count)++;
+    TimedLaunch t(q, kind);
+    cudaError_t e = dev::launch_pair(q.L->arith, second, a, D->grid_pair, q.s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One RK4 step in two passes of two stages each (see kernels.cu): W[0], W[1]
+// receive w_2, W[2] receives 12 h^2 L y.u.  Exponent slots: X = emax[0, 2
+// ndom) holds the bounds of (u, pi), Y = emax[2 ndom, 4 ndom) those of w_2;
+// each gather zeroes the slots that the pass after it accumulates into.
+static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* const* W) {
+  DeviceState* D = q.L->dev;
+  const int nd = (int)q.L->doms.size();
+  const bool fixed = q.L->arith == SC_ARITH_FIXED;
+  unsigned* X = D->emax;
+  unsigned* Y = D->emax + 2 * nd;
+  cudaError_t e = enq_fill2(q, u, pi, fixed ? Y : nullptr);
+  if (e != cudaSuccess) return e;
+  dev::PairArgs a{};
+  a.ndom = nd;
+  a.boxes = D->boxes;
+  a.s0 = u;
+  a.s1 = pi;
+  a.yu = u;
+  a.yp = pi;
+  a.q = W[4];
+  a.x = W[5];
+  a.out_u = W[0];
+  a.out_p = W[1];
+  a.ly = W[2];
+  a.coef = D->coef;
+  a.emax_in = X;
+  a.emax_out = Y;
+  a.err = D->err;
+  if ((e = enq_pair(q, a, false)) != cudaSuccess) return e;
+  if ((e = enq_fill2(q, W[0], W[1], fixed ? X : nullptr)) != cudaSuccess) return e;
+  a.s0 = W[0];
+  a.s1 = W[1];
+  a.x = W[2];
+  a.out_u = u;
+  a.out_p = pi;
+  a.ly = nullptr;
+  a.emax_in = Y;
+  a.emax_out = X;
+  return enq_pair(q, a, true);
+}
+
 // Prologue of a run of steps: the ghosts of u gathered (push exchange); the
 // pre-scaled wave speed q = c2 * dt/(12 h^2) (and the 1/3 variant) in W[4],
 // W[5]; for the fixed form, the exponent ring cleared and slot 0 = max
-// exponent of u.
-static cudaError_t enq_prologue(const Enq& q, double* u, const double* c2,
+// exponent of u (and, if pi is not NULL, slot ndom = that of pi).
+static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const double* c2,
                                 double* const* W) {
   DeviceState* D = q.L->dev;
   if (q.push) {
@@ -510,7 +606,9 @@ static cudaError_t enq_prologue(const Enq& q, double* u, const double* c2,
   if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
   e = cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
   if (e != cudaSuccess) return e;
-  return enq_maxexp(q, u, D->emax, false);
+  e = enq_maxexp(q, u, D->emax, false);
+  if (e != cudaSuccess || !pi) return e;
+  return enq_maxexp(q, pi, D->emax + q.L->doms.size(), false);  // slot X.pi of the pair form
 }
 
 // Stage scratch: Wa.u, Wa.pi, Wb.u, Wb.pi and the two pre-scaled wave speeds.
@@ -535,13 +633,17 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     D->ev_used = 0;
     D->ev_kind.clear();
   }
-  SC_CUDA(enq_prologue(q, u, c2, W));
+  const bool pairs = L->fuse == 2;
+  SC_CUDA(enq_prologue(q, u, pairs ? pi : nullptr, c2, W));
+  auto step = [&](const Enq& e) {
+    return pairs ? enq_step_pairs(e, u, pi, W) : enq_step(e, u, pi, c2, W, nullptr);
+  };
   if (mode != SC_MODE_GRAPH) {
-    for (int n = 0; n < nsteps; ++n) SC_CUDA(enq_step(q, u, pi, c2, W, nullptr));
+    for (int n = 0; n < nsteps; ++n) SC_CUDA(step(q));
     return SC_OK;
   }
-  auto key = std::make_tuple((const void*)u, (const void*)pi, (const void*)c2, L->arith,
-                             L->version);
+  auto key = std::make_tuple((const void*)u, (const void*)pi, (const void*)c2,
+                             L->arith + 2 * L->fuse, L->version);
   auto it = D->graphs.find(key);
   if (it == D->graphs.end()) {
     if (D->graphs.size() >= 16) {  // bounded cache: drop the oldest-keyed graphs
@@ -552,7 +654,7 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     int64_t nodes = 0;
     Enq cq{L, D->capture, &nodes, false};
     SC_CUDA(cudaStreamBeginCapture(D->capture, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enq_step(cq, u, pi, c2, W, nullptr);
+    cudaError_t e = step(cq);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(D->capture, &g);
     if (e != cudaSuccess) return cuda_fail(e, "capture of the RK4 step");
@@ -725,7 +827,7 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(cku[c], Su, bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(ckp[c], Sp, bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su, c2, W));
+    SC_CUDA(enq_prologue(q, Su, nullptr, c2, W));
     for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, nullptr));
   }
   if (u_T) SC_CUDA(cudaMemcpyAsync(u_T, Su, bytes, cudaMemcpyDeviceToDevice, s));
@@ -817,7 +919,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su, c2, W));
+    SC_CUDA(enq_prologue(q, Su, nullptr, c2, W));
     for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, lapw.data() + 4 * n));
     for (int n = len - 1; n >= 0; --n, ++n_adj) {
       const int p = (int)(n_adj & 1), pn = 1 - p;

@@ -189,6 +189,21 @@ class Level:
         t = B.ScTile(int(tile_x), 512 // int(tile_x), int(tile_z), 0)
         B.check(B.lib().sc_level_set_tuning(self._h, int(cls), ctypes.byref(t), int(ctas_per_sm)))
 
+    def get_tuning(self, cls: int):
+        """(tile_x, tile_y, tile_z) of size class `cls`."""
+        t = B.ScTile()
+        B.check(B.lib().sc_level_get_tuning(self._h, int(cls), ctypes.byref(t)))
+        return t.tile_x, t.tile_y, t.tile_z
+
+    def set_fusion(self, stages_per_pass: int):
+        """RK4 stages per stencil pass of rk4_step (1 or 2)."""
+        B.check(B.lib().sc_level_set_fusion(self._h, int(stages_per_pass)))
+
+    def get_fusion(self) -> int:
+        n = ctypes.c_int32()
+        B.check(B.lib().sc_level_get_fusion(self._h, ctypes.byref(n)))
+        return n.value
+
     def autotune(self, seed: int = 0, budget_ms: float = 2000.0, abort_factor: float = 2.0,
                  cache_path: Optional[str] = None, stream=None):
         cp = cache_path.encode() if cache_path else None

@@ -298,3 +298,22 @@ def test_level_too_large_is_rejected(B):
     n = (2048, 2048, 520)  # (2048+16) * (2048+4) * (520+4) > 2^31 doubles
     with pytest.raises(B.ScError, match="too large"):
         Level([((0, 0, 0), n, 0)], [dict(hi=n, h=0.1)])
+
+
+def test_fusion_setting_and_tile_query(B):
+    from paper_1308_1343_gb300.level import Level
+    n = (32, 24, 16)
+    lev = Level([((0, 0, 0), n, 0)], [dict(hi=n, h=0.1)])
+    assert lev.get_fusion() == 1
+    lev.set_fusion(2)
+    assert lev.get_fusion() == 2
+    for bad in (0, 3, -1):
+        with pytest.raises(B.ScError, match="stages_per_pass"):
+            lev.set_fusion(bad)
+    assert lev.get_fusion() == 2
+    tx, ty, tz = lev.get_tuning(0)
+    assert tx in (16, 32, 64) and tx * ty == 512 and tz >= 1
+    lev.set_tuning(0, 32, 12)
+    assert lev.get_tuning(0) == (32, 16, 12)
+    with pytest.raises(B.ScError, match="bad class"):
+        lev.get_tuning(1)
