@@ -36,9 +36,20 @@ N_EDGE = 256
 # stages 2-4 read w.u (stencil), w.pi, y.u, y.pi, c2 and write 2 (7 doubles)
 BYTES_PER_POINT_STEP = 8 * (5 + 7 + 7 + 7)
 BYTES_PER_POINT_STAGE = BYTES_PER_POINT_STEP / 4
+# two stages per pass: pass A reads y.u, y.pi (stencils), q, q/3 and writes
+# w_2.u, w_2.pi, L y.u (7 doubles); pass B reads w_2.u, w_2.pi (stencils),
+# y.u, y.pi, q, L y.u and writes y.u, y.pi (8 doubles)
+BYTES_PER_POINT_PASS = {"A": 8 * 7, "B": 8 * 8}
 # FP64 pipe instructions per point per stage (FP64 form): 10 adds + 2 FMAs
-# for the sum, 1 multiply by c2, 2 update FMAs
+# for the sum, 1 multiply by c2, 2 update FMAs; fixed form: the conversion
+# of the sum and 2 update FMAs (the pass kernels convert on the integer pipes
+# and need 4 FMAs per pass, i.e. 2 per stage)
 FP64_OPS_PER_POINT_STAGE = {"fp64": 15, "fixed": 3}
+FP64_OPS_PER_POINT_PASS = {"fp64": 28, "fixed": 4}
+# seconds of CPU work the oracle's cpu_baseline sample aims at
+CPU_SAMPLE_S = 12.0
+# RK4 steps of the oracle per step of the reference arm
+REF_RK4_STEPS = 10
 # run-time tuning results (tile per box-size class) are cached here between runs
 TUNE_CACHE = os.path.join(ROOT, "paper_1308_1343_gb300", "_build", "tune_cache.txt")
 
@@ -151,8 +162,27 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def _stencil_roofline(lev, B, npts):
+    """Algorithmic GB/s of the level's stencil kernels in its current form,
+    from the per-launch CUDA events of the last SC_MODE_TIMED call:
+    (achieved GB/s, mean launch ms, mean bytes per launch, launches, name)."""
+    if lev.get_fusion() == 2:
+        ta, na = lev.kernel_time(B.SC_KERNEL_PAIR_A)
+        tb, nb = lev.kernel_time(B.SC_KERNEL_PAIR_B)
+        if not (na and nb):
+            return None, None, None, 0, "pair_kernel"
+        nbytes = (BYTES_PER_POINT_PASS["A"] * na + BYTES_PER_POINT_PASS["B"] * nb) * npts
+        return (nbytes / ((ta + tb) * 1e-3) / 1e9, (ta + tb) / (na + nb), nbytes / (na + nb),
+                na + nb, "pair_kernel (passes A and B)")
+    sm, sl, _, _ = lev.kernel_times()
+    if not sl:
+        return None, None, None, 0, "fwd_stage_kernel"
+    return (BYTES_PER_POINT_STAGE * npts * sl / (sm * 1e-3) / 1e9, sm / sl,
+            BYTES_PER_POINT_STAGE * npts, sl, "fwd_stage_kernel")
+
+
 def _traffic(kernel_hash, workload):
-    """DRAM bytes per launch of the stage kernel from the committed ncu
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None if it was taken on another version of the kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
@@ -191,12 +221,12 @@ def run_reference(a, ws, rank):
     rates, times = [], []
     used = 1
     for _ in range(a.steps):
-        r, used, dt = _oracle_rate(inst, 1)
+        r, used, dt = _oracle_rate(inst, REF_RK4_STEPS)
         rates.append(r)
         times.append(dt)
     total_t = sum(times)
-    value = inst.u.size * len(times) / total_t
-    sample = "1 RK4 step of the 256^3 workload per benchmark step"
+    value = inst.u.size * REF_RK4_STEPS * len(times) / total_t
+    sample = "%d RK4 steps of the 256^3 workload per benchmark step" % REF_RK4_STEPS
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
@@ -246,12 +276,12 @@ def _extras(torch, W, B, Level, arith, stream):
         t = _time_steps(torch, lev, u, pi, c2, inst.dt, 50, mode, 1, stream)
         res[name] = n * 50 / t
     lev.rk4_step(u, pi, c2, inst.dt, 10, B.SC_MODE_TIMED, stream=stream)
-    sm, sl, gm, gl = lev.kernel_times()
+    gbs, _, _, _, kname = _stencil_roofline(lev, B, n)
     out["uneven_level"] = {
         "workload": "512x512x256 periodic domain, 64 bisected boxes, 50 RK4 steps",
-        "boxes": len(inst.boxes), "points": n,
+        "boxes": len(inst.boxes), "points": n, "stages_per_pass": lev.get_fusion(),
         "graph_updates_per_s": res["graph"], "per_box_updates_per_s": res["per_box"],
-        "stage_kernel_gbs": BYTES_PER_POINT_STAGE * n * sl / (sm * 1e-3) / 1e9 if sm else None,
+        "stencil_kernel": kname, "stencil_kernel_gbs": gbs,
     }
     del lev, u, pi, c2
     torch.cuda.empty_cache()
@@ -271,7 +301,8 @@ def _extras(torch, W, B, Level, arith, stream):
     t = _time_steps(torch, lev, u, pi, c2, dts, 100, B.SC_MODE_GRAPH, 1, stream)
     out["ensemble"] = {"workload": "256 periodic cubes, edges 24..96, own c2 and pulse, "
                                    "100 RK4 steps, autotuned tiles",
-                       "points": n, "graph_updates_per_s": n * 100 / t}
+                       "points": n, "stages_per_pass": lev.get_fusion(),
+                       "graph_updates_per_s": n * 100 / t}
     del lev, u, pi, c2
     torch.cuda.empty_cache()
 
@@ -308,7 +339,8 @@ def _extras(torch, W, B, Level, arith, stream):
     lev.forward_tape(u0, pi0, c2, inst.dt, 200, 20, uT, None, stream=stream)
     lev.backward_tape(c2, seed, None, g[0], g[1], g[2], stream=stream)
     torch.cuda.synchronize()
-    names = {B.SC_KERNEL_STAGE_RECORD: "stage_record", B.SC_KERNEL_GATHER: "gather",
+    names = {B.SC_KERNEL_STAGE_RECORD: "stage_record", B.SC_KERNEL_PAIR_A: "pass_a",
+             B.SC_KERNEL_PAIR_B: "pass_b", B.SC_KERNEL_GATHER: "gather",
              B.SC_KERNEL_ADJ_A: "adj_a", B.SC_KERNEL_ADJ_B: "adj_b", B.SC_KERNEL_ADJ_C: "adj_combine"}
     kern = {}
     for k, name in names.items():
@@ -316,7 +348,7 @@ def _extras(torch, W, B, Level, arith, stream):
         kern[name] = {"ms": ms, "launches": n}
     lev.set_profiling(False)
     out["adjoint"] = {"workload": "128^3 periodic box, 200 RK4 steps, checkpoints every 20",
-                      "t_forward_s": t_fwd, "t_forward_tape_s": t1 - t0,
+                      "stages_per_pass": lev.get_fusion(), "t_forward_s": t_fwd, "t_forward_tape_s": t1 - t0,
                       "t_backward_s": t2 - t1, "ratio_backward_over_forward": (t2 - t1) / t_fwd,
                       "ratio_total_over_forward": (t2 - t0) / t_fwd,
                       "backward_kernels": kern}
@@ -379,19 +411,19 @@ def run_ours(a, ws, rank, local):
     t = max_over_ranks(t, dist, "cuda")
     value = job_rate(npts * nsub * a.steps, t, ws)
 
-    # dominant kernel: the stage kernel, timed per launch with CUDA events
+    # dominant kernels: the stencil kernels of the form the tuner chose,
+    # timed per launch with CUDA events on the launching stream
+    form = lev.get_fusion()
     lev.rk4_step(u, pi, c2, inst.dt, nsub, B.SC_MODE_TIMED, stream=stream)
-    stage_ms, stage_n, gather_ms, gather_n = lev.kernel_times()
+    achieved, avg_ms, bytes_launch, nlaunch, kname = _stencil_roofline(lev, B, npts)
+    gather_ms, gather_n = lev.kernel_time(B.SC_KERNEL_GATHER)
     lev.sync(stream)
-    avg_s = stage_ms / stage_n * 1e-3
-    achieved = BYTES_PER_POINT_STAGE * npts / avg_s / 1e9
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     khash = _kernel_source_hash()
-    traffic = _traffic(khash, "single256")
-    fp64_peak_tflops = None
-    ops = FP64_OPS_PER_POINT_STAGE[a.arith]
-    fp64_achieved = 2 * ops * npts / avg_s / 1e12  # FMA = 2 flops upper estimate
+    traffic = _traffic(khash, "single256_f%d" % form)
+    ops = (FP64_OPS_PER_POINT_PASS if form == 2 else FP64_OPS_PER_POINT_STAGE)[a.arith]
+    fp64_achieved = 2 * ops * npts / (avg_ms * 1e-3) / 1e12  # FMA = 2 flops upper estimate
 
     # end to end through the C ABI with pinned host buffers
     hu = torch.from_numpy(lev.scatter([inst.u])).pin_memory()
@@ -417,9 +449,15 @@ def run_ours(a, ws, rank, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu:
-        r, used, dt = _oracle_rate(inst, 3)
+        # a bounded sample of about 12 s of oracle work: the step count is
+        # calibrated by a 2-step run (counted in the sample)
+        r0, used, dt0 = _oracle_rate(inst, 2)
+        nmore = max(1, int(round((CPU_SAMPLE_S - dt0) * r0 / npts)))
+        r1, used, dt1 = _oracle_rate(inst, nmore)
+        nall = 2 + nmore
+        r = npts * nall / (dt0 + dt1)
         cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
-               "sample": "3 RK4 steps of the same 256^3 workload (%.1f s)" % dt}
+               "sample": "%d RK4 steps of the same 256^3 workload (%.1f s)" % (nall, dt0 + dt1)}
 
     if rank == 0:
         line = {
@@ -431,18 +469,24 @@ def run_ours(a, ws, rank, local):
                        "points": npts, "rk4_steps_per_step": nsub,
                        "arith": a.arith, "mode": "batched persistent launch, CUDA graph per "
                                                   "RK4 step",
+                       "stages_per_pass": form,
+                       "tiles": [list(lev.get_tuning(c)) for c in range(lev.size_classes()[0])],
                        "l2": "inputs larger than L2 (fields 7 x %d MB)" % (fbytes >> 20),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "fwd_stage_kernel",
+            "roofline": {"bound": "hbm", "kernel": kname,
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm if hbm else None, "traffic": traffic,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                         "bytes_per_launch": BYTES_PER_POINT_STAGE * npts,
-                         "launches": stage_n, "avg_launch_ms": avg_s * 1e3,
+                         "bytes_per_launch": bytes_launch,
+                         "launches": nlaunch, "avg_launch_ms": avg_ms,
                          "gather_avg_launch_ms": gather_ms / max(gather_n, 1),
                          "fp64_tflops_est": fp64_achieved,
                          "hbm_fraction_of_nominal_7900": achieved / 7900.0,
-                         "kernel_hash": khash},
+                         "kernel_hash": khash,
+                         "note": ("two RK4 stages per pass halve the DRAM bytes of a step; "
+                                  "these kernels are then limited by SM instruction issue "
+                                  "(fixed-point integer work and FP64 FMAs), not by HBM")
+                         if form == 2 else "one stage per pass, HBM-bound"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

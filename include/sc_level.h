@@ -167,7 +167,8 @@ int sc_level_set_tuning(sc_level* level, int32_t size_class, const sc_tile* tile
  * (whose tile_z is final only once the level has device state). */
 int sc_level_get_tuning(const sc_level* level, int32_t size_class, sc_tile* tile);
 
-/* RK4 stages per stencil pass in sc_level_rk4_step (default 1).
+/* RK4 stages per stencil pass of sc_level_rk4_step, sc_level_forward_tape
+ * and the forward recomputation of sc_level_backward_tape (default 2).
  * 1: one launch per stage, w_s = y + g_s A w_{s-1} as in the paper's
  *    method-of-lines stage loop.
  * 2: two launches per step.  Only the u-component goes through L and
@@ -178,9 +179,9 @@ int sc_level_get_tuning(const sc_level* level, int32_t size_class, sc_tile* tile
  *    and every exchange still two points deep (two fields per exchange).
  *    This is loop fusion chosen per run (arXiv 1308.1343, Sec. 3.3, fusing
  *    loops as a tuning option).  Results equal the one-stage form up to
- *    rounding.  The taped forward (sc_level_forward_tape) and
- *    sc_box_rk4_step_noalloc always run one stage per pass.
- * Errors: SC_EINVAL for other values. */
+ *    rounding.  sc_box_rk4_step_noalloc always runs one stage per pass.
+ * Setting the form fixes it; until then sc_level_autotune tunes both forms
+ * and keeps the faster.  Errors: SC_EINVAL for other values. */
 int sc_level_set_fusion(sc_level* level, int32_t stages_per_pass);
 int sc_level_get_fusion(const sc_level* level, int32_t* stages_per_pass);
 
@@ -189,15 +190,18 @@ int sc_level_get_fusion(const sc_level* level, int32_t* stages_per_pass);
 int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
                           int32_t* class_of_box /* nboxes entries or NULL */);
 
-/* Run-time tuning of the batched stage kernel (GPU counterpart of the
+/* Run-time tuning of the batched stencil kernels (GPU counterpart of the
  * paper's random-restart hill climbing, Sec. 3.2): for every size class,
- * times candidate tiles on scratch fields of this level, moves to better
- * neighbours, restarts at random with small probability, aborts candidates
- * that run longer than `abort_factor` x the best time, and keeps the best.
- * budget_ms bounds the total tuning time.  Results are applied to the level
- * and, if cache_path is not NULL, merged into that on-disk cache (keyed by
- * GPU name, SM count, arithmetic and class extent) and reused from it.
- * Synchronises the stream. */
+ * times candidate tiles on scratch fields of this level (in the launch of
+ * the whole level), moves to better neighbours, restarts at random with
+ * small probability, aborts candidates that run longer than `abort_factor`
+ * x the best time, and keeps the best.  Unless sc_level_set_fusion fixed
+ * the form, it does so for one and for two RK4 stages per pass and keeps
+ * the form whose step is faster (selecting between sets of loop kernels,
+ * Sec. 3.3).  budget_ms bounds the total tuning time.  Results are applied
+ * to the level and, if cache_path is not NULL, merged into that on-disk
+ * cache (keyed by GPU name, SM count, arithmetic, form and class extent)
+ * and reused from it.  Synchronises the stream. */
 int sc_level_autotune(sc_level* level, int32_t seed, double budget_ms,
                       double abort_factor, const char* cache_path, void* stream);
 
@@ -241,9 +245,11 @@ int sc_level_misfit(sc_level* level, const double* u, const double* u_obs,
                     double* loss, double* seed, void* stream);
 
 /* Forward pass for differentiation: runs nsteps RK4 steps from (u0, pi0)
- * (batched launches; the ghosts of each stage output are written by the
- * stage kernel itself, from the level's exchange list grouped by source
- * box and face slab), keeping the state every ckpt_every steps in
+ * (batched launches; with one stage per pass the ghosts of each stage
+ * output are written by the stage kernel itself, from the level's exchange
+ * list grouped by source box and face slab, so u_T's ghosts are filled;
+ * with two stages per pass they are gathered before each pass and u_T's
+ * ghosts are not refreshed), keeping the state every ckpt_every steps in
  * library-owned checkpoint fields (the level's tape, replacing any earlier
  * tape), and writes the final state to u_T, pi_T (either may be NULL).
  * Inputs are not modified.  Requires periodic domains.  Device memory:
@@ -281,8 +287,8 @@ int sc_level_sync(sc_level* level, void* stream);
 #define SC_KERNEL_STAGE 0        /* forward stage kernel                     */
 #define SC_KERNEL_GATHER 1       /* ghost gather                             */
 #define SC_KERNEL_STAGE_RECORD 2 /* forward stage kernel recording L w.u     */
-#define SC_KERNEL_ADJ_A 3        /* adjoint: L(c2 .) with c2 product output  */
-#define SC_KERNEL_ADJ_B 4        /* adjoint: L(c2 .)                          */
+#define SC_KERNEL_ADJ_A 3        /* adjoint pass 1: L(c2 .) twice, c2 products */
+#define SC_KERNEL_ADJ_B 4        /* adjoint pass 2: L(c2 .) twice              */
 #define SC_KERNEL_ADJ_C 5        /* adjoint: pointwise combination           */
 #define SC_KERNEL_PAIR_A 6       /* two-stage pass A (stages 1, 2)           */
 #define SC_KERNEL_PAIR_B 7       /* two-stage pass B (stages 3, 4)           */
@@ -310,8 +316,9 @@ int sc_level_launch_count(const sc_level* level, int64_t* n);
  * cannot allocate device memory (for example while their own allocator owns
  * the whole device, or where cudaMalloc/cudaFree are forbidden after
  * start-up): it advances ONE periodic box by nsteps RK4 steps (FP64 form of
- * the stage kernel, same results as sc_level_rk4_step with SC_ARITH_FP64 on a
- * one-box periodic level) and calls no cudaMalloc, cudaFree or other
+ * the stage kernel, same results as sc_level_rk4_step with SC_ARITH_FP64
+ * and one stage per pass on a one-box periodic level) and calls no
+ * cudaMalloc, cudaFree or other
  * allocating routine.  Its four stage arrays live in a file-scope static
  * device array of 16 MiB (4 arrays of 2^19 doubles) that every GPU loading
  * the library holds until the process exits.

@@ -35,8 +35,8 @@ const int kTx[] = {16, 32, 64};
 
 std::string cache_key(const sc_level* L, const SizeClass& c) {
   std::ostringstream k;
-  k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|" << c.ext[0] << ","
-    << c.ext[1] << "," << c.ext[2];
+  k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|f" << L->fuse << "|"
+    << c.ext[0] << "," << c.ext[1] << "," << c.ext[2];
   return k.str();
 }
 
@@ -107,8 +107,41 @@ struct Timer {
   }
   static int dev_threads() { return dev::stage_threads(); }
 
-  // Median time (microseconds) of one stage launch over the level's items;
-  // gives up after the second run if it exceeds `limit`.
+  // The two passes of one step (two stages per pass), on the scratch fields.
+  void launch_pairs(int n) {
+    DeviceState* D = L->dev;
+    const int nd = (int)L->doms.size();
+    dev::PairArgs p{};
+    p.items = ditems;
+    p.nitems = n;
+    p.ndom = nd;
+    p.boxes = D->boxes;
+    p.s0 = p.yu = W[0];
+    p.s1 = p.yp = W[1];
+    p.q = W[4];
+    p.x = W[5];
+    p.out_u = W[2];
+    p.out_p = W[3];
+    p.ly = c2;
+    p.coef = D->coef;
+    p.emax_in = D->emax;
+    p.emax_out = D->emax + 2 * nd;
+    p.err = D->err;
+    dev::launch_pair(L->arith, false, p, D->grid_pair, s);
+    p.s0 = W[2];
+    p.s1 = W[3];
+    p.x = c2;
+    p.out_u = W[0];
+    p.out_p = W[1];
+    p.ly = nullptr;
+    p.emax_in = D->emax + 2 * nd;
+    p.emax_out = D->emax;
+    dev::launch_pair(L->arith, true, p, D->grid_pair, s);
+  }
+
+  // Median time (microseconds) of what one stencil pass of the level's
+  // items costs in the configured form (one stage launch, or the two passes
+  // of a step); gives up after the second run if it exceeds `limit`.
   double time(int cls, const Cand& c, double limit) {
     const int n = stage(cls, c);
     if (n <= 0) return 1e30;
@@ -138,7 +171,10 @@ struct Timer {
     std::vector<double> ts;
     for (int r = 0; r < 5; ++r) {
       cudaEventRecord(e0, s);
-      dev::launch_fwd_stage(L->arith, false, a, D->grid_stage, s);
+      if (L->fuse == 2)
+        launch_pairs(n);
+      else
+        dev::launch_fwd_stage(L->arith, false, a, D->grid_stage, s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
       float ms = 0;
@@ -164,29 +200,15 @@ std::vector<Cand> neighbours(const Cand& c, int64_t nz) {
   return v;
 }
 
-}  // namespace
-}  // namespace sc
-
-using namespace sc;
-
-extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
-                                 double abort_factor, const char* cache_path, void* stream) {
-  if (!L) return set_error(SC_EINVAL, "NULL level");
-  if (!(abort_factor > 1.0)) return set_error(SC_EINVAL, "abort_factor must be > 1");
-  int rc = ensure_device(L);
-  if (rc) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  Timer T{L, s};
-  if ((rc = scratch4(L, T.W)) || (rc = get_field(L, "tune.c2", &T.c2))) return rc;
-  const double dt0 = 0.0;
-  if ((rc = set_coef(L, &dt0, 1, s))) return rc;
-  cudaEventCreate(&T.e0);
-  cudaEventCreate(&T.e1);
-  auto cache = read_cache(cache_path);
-  std::mt19937_64 rng((uint64_t)seed);
+// Tune the tile of every size class for the level's current form (stages
+// per pass): per class, hill climbing with random restarts from the class's
+// current tile, or the cached result.  Returns the time (microseconds) of
+// one step's stencil launches with the tuned tiles, or a negative value if
+// a launch failed.
+double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, double>>& cache,
+                 std::mt19937_64& rng, double per_class, double abort_factor) {
+  cudaStream_t s = T.s;
   std::uniform_real_distribution<double> U(0.0, 1.0);
-  const double per_class = budget_ms / std::max<size_t>(1, L->classes.size());
-  bool changed = false;
   for (size_t ci = 0; ci < L->classes.size(); ++ci) {
     SizeClass& C = L->classes[ci];
     const std::string key = cache_key(L, C);
@@ -196,7 +218,6 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
       C.tile.tile_y = 2 * dev::stage_threads() / hit->second.first.tx;
       C.tile.tile_z = hit->second.first.tz;
       C.fixed = true;
-      changed = true;
       continue;
     }
     std::map<Cand, double> seen;
@@ -263,7 +284,56 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
     C.tile.tile_z = best.tz;
     C.fixed = true;
     cache[key] = {best, tbest};
-    changed = true;
+  }
+  // the whole level with every class at its tuned tile
+  const double t = T.time(-1, Cand{0, 0}, 1e30);
+  if (t >= 1e30) return -1.0;
+  return L->fuse == 2 ? t : 4.0 * t;
+}
+
+}  // namespace
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
+                                 double abort_factor, const char* cache_path, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!(abort_factor > 1.0)) return set_error(SC_EINVAL, "abort_factor must be > 1");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  Timer T{L, s};
+  if ((rc = scratch4(L, T.W)) || (rc = get_field(L, "tune.c2", &T.c2))) return rc;
+  const double dt0 = 0.0;
+  if ((rc = set_coef(L, &dt0, 1, s))) return rc;
+  cudaEventCreate(&T.e0);
+  cudaEventCreate(&T.e1);
+  auto cache = read_cache(cache_path);
+  std::mt19937_64 rng((uint64_t)seed);
+  // Unless the caller fixed the form, both are tuned and the faster kept:
+  // choosing between sets of loop kernels (one or two RK4 stages per pass)
+  // with the same optimiser, as the paper proposes for fission and fusion.
+  const int nforms = L->fuse_fixed ? 1 : 2;
+  const double per_class = budget_ms / (nforms * std::max<size_t>(1, L->classes.size()));
+  bool ok = true;
+  if (L->fuse_fixed) {
+    ok = tune_form(L, T, cache, rng, per_class, abort_factor) >= 0;
+  } else {
+    std::vector<sc_tile> start;
+    for (const auto& c : L->classes) start.push_back(c.tile);
+    L->fuse = 1;
+    const double t1 = tune_form(L, T, cache, rng, per_class, abort_factor);
+    std::vector<sc_tile> tiles1;
+    for (const auto& c : L->classes) tiles1.push_back(c.tile);
+    for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = start[i];
+    L->fuse = 2;
+    const double t2 = tune_form(L, T, cache, rng, per_class, abort_factor);
+    ok = t1 >= 0 && t2 >= 0;
+    if (ok && t1 < t2) {
+      L->fuse = 1;
+      for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = tiles1[i];
+    }
   }
   if (T.ditems) cudaFree(T.ditems);
   cudaEventDestroy(T.e0);
@@ -271,6 +341,6 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
   write_cache(cache_path, cache);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(SC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
-  if (changed) return upload_items(L);
-  return SC_OK;
+  if (!ok) return set_error(SC_ECUDA, "autotune: a timed launch failed");
+  return upload_items(L);
 }

@@ -287,32 +287,48 @@ __global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
 // y.pi, q, q/3; write w_2, L y.u.  B: read w_2, y, q, L y.u; write y).
 // Results differ from the one-stage form by rounding only.
 
-template <class A, bool SECOND>
+template <class A, bool SECOND, bool RECORD>
 struct PairEpi {
   static constexpr int NF = 4;  // y.u, y.pi, q = c2 dt/(12 h^2), then A: q/3, B: L y.u
   const double* f[NF];
   double* out_u;
   double* out_p;
   double* __restrict__ ly;  // pass A: 12 h^2 L y.u
+  double* __restrict__ r0;  // RECORD: C_s L w_{s-1}.u of the pass's two stages
+  double* __restrict__ r1;
   A a0, a1;                 // arithmetic of the two stencil fields
   double ga, gb;            // A: g_1, g_2.  B: g_3, g_4
+  double c0, c1;            // recording scales of the two stages
   unsigned eu, ep;
 
-  // one point: s0, s1 the two stencil sums, x the pointwise fields
+  // one point: s0, s1 the two stencil sums, x the pointwise fields; q0, q1
+  // the recorded values (the stage kernel's C_s L w_{s-1}.u, same scaling)
   __device__ __forceinline__ void one(typename A::T s0, typename A::T s1, double u0, double p0,
-                                      double q, double x, double& un, double& pn,
-                                      double& lyv) const {
+                                      double q, double x, double& un, double& pn, double& lyv,
+                                      double& q0, double& q1) const {
     if (!SECOND) {
-      const double dU = a0.scaled(s0, 0);  // 12 h^2 L y.u
+      double dU, dU4;                      // 12 h^2 L y.u, and / 4
+      a0.scaled2(s0, 0, -2, dU, dU4);
       const double dP = a1.scaled(s1, 0);  // 12 h^2 L y.pi
-      const double w1p = fma(q, a0.rescale(dU, -2), p0);
+      const double w1p = fma(q, dU4, p0);
+      const double lw1 = fma(ga, dP, dU);  // 12 h^2 L w_1.u
       un = fma(gb, w1p, u0);
-      pn = fma(x, fma(ga, dP, dU), p0);
+      pn = fma(x, lw1, p0);
       lyv = dU;
+      if (RECORD) {
+        q0 = dU4 * c0;
+        q1 = lw1 * c1;
+      }
     } else {
-      const double w3p = fma(q, a0.scaled(s0, -1), p0);  // 12 h^2 L w_2.u * 1/2
+      const double dA = a0.scaled(s0, -1);  // 12 h^2 L w_2.u * 1/2
+      const double w3p = fma(q, dA, p0);
+      const double lw3 = fma(ga, a1.scaled(s1, 0), x);  // 12 h^2 L w_3.u
       un = fma(gb, w3p, u0);
-      pn = fma(q, fma(ga, a1.scaled(s1, 0), x), p0);
+      pn = fma(q, lw3, p0);
+      if (RECORD) {
+        q0 = dA * c0;
+        q1 = lw3 * c1;
+      }
     }
   }
 
@@ -321,17 +337,25 @@ struct PairEpi {
                                         const typename A::T (&rB)[2], bool actB, int, int,
                                         int) {
     const double2 u0 = pw[0], p0 = pw[1], q = pw[2], x = pw[3];
-    double2 un, pn, lv;
-    one(rA[0], rA[1], u0.x, p0.x, q.x, x.x, un.x, pn.x, lv.x);
-    one(rB[0], rB[1], u0.y, p0.y, q.y, x.y, un.y, pn.y, lv.y);
+    double2 un, pn, lv, q0, q1;
+    one(rA[0], rA[1], u0.x, p0.x, q.x, x.x, un.x, pn.x, lv.x, q0.x, q1.x);
+    one(rB[0], rB[1], u0.y, p0.y, q.y, x.y, un.y, pn.y, lv.y, q0.y, q1.y);
     if (actB) {
       st2(out_u + i, un);
       st2(out_p + i, pn);
       if (!SECOND) st2(ly + i, lv);
+      if (RECORD) {
+        st2(r0 + i, q0);
+        st2(r1 + i, q1);
+      }
     } else {
       out_u[i] = un.x;
       out_p[i] = pn.x;
       if (!SECOND) ly[i] = lv.x;
+      if (RECORD) {
+        r0[i] = q0.x;
+        r1[i] = q1.x;
+      }
     }
     if (A::kFixed) {
       eu = max(eu, biased_exp(un.x));
@@ -344,7 +368,7 @@ struct PairEpi {
   }
 };
 
-template <class A, bool SECOND>
+template <class A, bool SECOND, bool RECORD>
 __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
   __shared__ Smem<NT, A, 4, 2> smem;
   __shared__ unsigned red[2 * NT / 32];
@@ -356,9 +380,11 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
     const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
                      make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
     const int s0 = SECOND ? 2 : 0;  // stage coefficients g_{s0+1}, g_{s0+2}
-    PairEpi<A, SECOND> epi{{a.yu, a.yp, a.q, a.x}, a.out_u, a.out_p, a.ly, ar[0], ar[1],
-                           a.coef[s0 * a.ndom + bx.dom].gamma,
-                           a.coef[(s0 + 1) * a.ndom + bx.dom].gamma, 0u, 0u};
+    const StageCoef* ca = a.coef + s0 * a.ndom + bx.dom;
+    const StageCoef* cb = ca + a.ndom;
+    PairEpi<A, SECOND, RECORD> epi{{a.yu, a.yp, a.q, a.x}, a.out_u, a.out_p, a.ly, a.rec0,
+                                   a.rec1, ar[0], ar[1], ca->gamma, cb->gamma,
+                                   RECORD ? ca->rec : 0.0, RECORD ? cb->rec : 0.0, 0u, 0u};
     run_items<NT, 2>(it, bx, F, ar, smem, err, epi);
     if (A::kFixed)
       cta_max2_to(epi.eu, epi.ep, a.emax_out + bx.dom, a.emax_out + a.ndom + bx.dom, red);
@@ -414,85 +440,86 @@ __global__ void __launch_bounds__(NT, 4) lap_kernel(LapArgs a) {
 // unscaled sums Phat = 12 h^2 P; all constant factors (the G's, powers of
 // 1/(12 h^2)) are folded into per-domain coefficients, and the forward pass
 // records Q_s = C_s Lw_{s-1} already multiplied by its constant.
-//   adj_a   (x2): Phat = L^ z, and z' = c2 Phat   (z = c2 b or c2 a)
-//   adj_b   (x2): Phat2 = L^ (c2 Phat4), Phat1 = L^ (c2 Phat3)
+//   adj2 first  : Phat4, Phat3 = L^ z for z = c2 b, c2 a, and z' = c2 Phat
+//   adj2 second : Phat2 = L^ (c2 Phat4), Phat1 = L^ (c2 Phat3)
 //   adj_combine : the combination above, pointwise; it also writes the next
 //                 (earlier) step's stencil inputs c2 ybar.pi and c2 ybar.u
 // ---------------------------------------------------------------------------
 
-template <class A>
-struct AdjAEpi {
-  static constexpr int NF = 1;  // c2
-  const double* f[NF];
-  double* __restrict__ p_out;
-  double* __restrict__ z_out;
-  A arith;
-  unsigned emax;
-  __device__ __forceinline__ void point(int i, const double2* pw, typename A::T rA,
-                                        typename A::T rB, bool actB, int, int, int) {
-    const double2 c = pw[0];
-    const double2 p = make_double2(arith.scaled(rA, 0), arith.scaled(rB, 0));
-    const double2 z = make_double2(c.x * p.x, c.y * p.y);
-    if (actB) {
-      st2(p_out + i, p);
-      st2(z_out + i, z);
-    } else {
-      p_out[i] = p.x;
-      z_out[i] = z.x;
-    }
-    if (A::kFixed) {
-      emax = max(emax, biased_exp(z.x));
-      if (actB) emax = max(emax, biased_exp(z.y));
-    }
-  }
-};
-
-template <class A>
-struct AdjBEpi {
-  static constexpr int NF = 0;
+// The four applications of M as two passes over two stencil fields each:
+//   adj2 first  : (Phat4, Phat3) = L^ (c2 b, c2 a), and (c2 Phat4, c2 Phat3)
+//                 with their ghosts pushed (the second pass's inputs);
+//   adj2 second : (Phat2, Phat1) = L^ (c2 Phat4, c2 Phat3).
+template <class A, bool SECOND>
+struct Adj2Epi {
+  static constexpr int NF = SECOND ? 0 : 1;  // c2
   const double* f[1];
-  double* __restrict__ p_out;
-  A arith;
-  __device__ __forceinline__ void point(int i, const double2*, typename A::T rA,
-                                        typename A::T rB, bool actB, int, int, int) {
-    const double2 p = make_double2(arith.scaled(rA, 0), arith.scaled(rB, 0));
-    if (actB)
-      st2(p_out + i, p);
-    else
-      p_out[i] = p.x;
+  double* __restrict__ p0;
+  double* __restrict__ p1;
+  double* __restrict__ z0;
+  double* __restrict__ z1;
+  A a0, a1;
+  unsigned e0, e1;
+  __device__ __forceinline__ void point(int i, const double2* pw,
+                                        const typename A::T (&rA)[2],
+                                        const typename A::T (&rB)[2], bool actB, int, int,
+                                        int) {
+    const double2 q0 = make_double2(a0.scaled(rA[0], 0), a0.scaled(rB[0], 0));
+    const double2 q1 = make_double2(a1.scaled(rA[1], 0), a1.scaled(rB[1], 0));
+    double2 y0, y1;
+    if (!SECOND) {
+      const double2 c = pw[0];
+      y0 = make_double2(c.x * q0.x, c.y * q0.y);
+      y1 = make_double2(c.x * q1.x, c.y * q1.y);
+    }
+    if (actB) {
+      st2(p0 + i, q0);
+      st2(p1 + i, q1);
+      if (!SECOND) {
+        st2(z0 + i, y0);
+        st2(z1 + i, y1);
+      }
+    } else {
+      p0[i] = q0.x;
+      p1[i] = q1.x;
+      if (!SECOND) {
+        z0[i] = y0.x;
+        z1[i] = y1.x;
+      }
+    }
+    if (A::kFixed && !SECOND) {
+      e0 = max(e0, biased_exp(y0.x));
+      e1 = max(e1, biased_exp(y1.x));
+      if (actB) {
+        e0 = max(e0, biased_exp(y0.y));
+        e1 = max(e1, biased_exp(y1.y));
+      }
+    }
   }
 };
 
-template <class A>
-__global__ void __launch_bounds__(NT, 4) adj_a_kernel(AdjArgs a) {
-  __shared__ Smem<NT, A, 1> smem;
-  __shared__ unsigned red[NT / 32];
-  if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
+template <class A, bool SECOND>
+__global__ void __launch_bounds__(NT, 2) adj2_kernel(Adj2Args a) {
+  __shared__ Smem<NT, A, SECOND ? 0 : 1, 2> smem;
+  __shared__ unsigned red[2 * NT / 32];
+  if (A::kFixed) clear_slot(a.emax_clear, 2 * a.ndom);
   unsigned err = 0;
+  const double* const F[2] = {a.z0_in, a.z1_in};
   for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
     const DItem it = a.items[i];
     const DBox bx = a.boxes[it.box];
-    const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    AdjAEpi<A> epi{{a.c2}, a.p_out, a.z_out, arith};
-    epi.emax = 0;
-    run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
-    push_item<NT>(PushTab{a.push, a.push_gofs}, it, bx, a.z_out);  // next stencil input
-    if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
-  }
-  if (err) atomicOr(a.err, err);
-}
-
-template <class A>
-__global__ void __launch_bounds__(NT, 4) adj_b_kernel(AdjArgs a) {
-  __shared__ Smem<NT, A, 0> smem;
-  if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
-  unsigned err = 0;
-  for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
-    const DItem it = a.items[i];
-    const DBox bx = a.boxes[it.box];
-    const A arith = make_arith<A>(a.emax_in, bx.dom, err);
-    AdjBEpi<A> epi{{nullptr}, a.p_out, arith};
-    run_item<NT>(it, bx, a.z_in, arith, smem, err, epi);
+    const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
+                     make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
+    Adj2Epi<A, SECOND> epi{{a.c2}, a.p0_out, a.p1_out, a.z0_out, a.z1_out, ar[0], ar[1],
+                           0u, 0u};
+    run_items<NT, 2>(it, bx, F, ar, smem, err, epi);
+    if (!SECOND) {
+      const PushTab pt{a.push, a.push_gofs};
+      push_item<NT>(pt, it, bx, a.z0_out);  // the second pass's stencil inputs
+      push_item<NT>(pt, it, bx, a.z1_out);
+      if (A::kFixed)
+        cta_max2_to(epi.e0, epi.e1, a.emax_out + bx.dom, a.emax_out + a.ndom + bx.dom, red);
+    }
   }
   if (err) atomicOr(a.err, err);
 }
@@ -636,16 +663,20 @@ static void set_carveouts() {
   prefer_shared(fwd_stage_kernel<Fixed, false>);
   prefer_shared(fwd_stage_kernel<Fp64, true>);
   prefer_shared(fwd_stage_kernel<Fp64, false>);
-  prefer_shared(adj_a_kernel<Fixed>);
-  prefer_shared(adj_a_kernel<Fp64>);
-  prefer_shared(adj_b_kernel<Fixed>);
-  prefer_shared(adj_b_kernel<Fp64>);
   prefer_shared(lap_kernel<Fixed>);
   prefer_shared(lap_kernel<Fp64>);
-  prefer_shared(pair_kernel<Fixed, false>);
-  prefer_shared(pair_kernel<Fixed, true>);
-  prefer_shared(pair_kernel<Fp64, false>);
-  prefer_shared(pair_kernel<Fp64, true>);
+  prefer_shared(pair_kernel<FixedI, false, false>);
+  prefer_shared(pair_kernel<FixedI, true, false>);
+  prefer_shared(pair_kernel<Fp64, false, false>);
+  prefer_shared(pair_kernel<Fp64, true, false>);
+  prefer_shared(pair_kernel<FixedI, false, true>);
+  prefer_shared(pair_kernel<FixedI, true, true>);
+  prefer_shared(pair_kernel<Fp64, false, true>);
+  prefer_shared(pair_kernel<Fp64, true, true>);
+  prefer_shared(adj2_kernel<FixedI, false>);
+  prefer_shared(adj2_kernel<FixedI, true>);
+  prefer_shared(adj2_kernel<Fp64, false>);
+  prefer_shared(adj2_kernel<Fp64, true>);
 }
 
 cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
@@ -678,20 +709,20 @@ cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj(int kind, int arith, const AdjArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_adj2(bool second, int arith, const Adj2Args& a, int grid, cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
   set_carveouts();
   grid = min(grid, a.nitems);
-  if (kind == 0) {
-    if (arith == 1)
-      adj_a_kernel<Fixed><<<grid, NT, 0, s>>>(a);
+  if (arith == 1) {
+    if (second)
+      adj2_kernel<FixedI, true><<<grid, NT, 0, s>>>(a);
     else
-      adj_a_kernel<Fp64><<<grid, NT, 0, s>>>(a);
+      adj2_kernel<FixedI, false><<<grid, NT, 0, s>>>(a);
   } else {
-    if (arith == 1)
-      adj_b_kernel<Fixed><<<grid, NT, 0, s>>>(a);
+    if (second)
+      adj2_kernel<Fp64, true><<<grid, NT, 0, s>>>(a);
     else
-      adj_b_kernel<Fp64><<<grid, NT, 0, s>>>(a);
+      adj2_kernel<Fp64, false><<<grid, NT, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -711,16 +742,21 @@ cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cud
   if (a.nitems <= 0) return cudaSuccess;
   set_carveouts();
   grid = min(grid, a.nitems);
+  const bool rec = a.rec0 != nullptr;
   if (arith == 1) {
     if (second)
-      pair_kernel<Fixed, true><<<grid, NT, 0, s>>>(a);
+      rec ? pair_kernel<FixedI, true, true><<<grid, NT, 0, s>>>(a)
+          : pair_kernel<FixedI, true, false><<<grid, NT, 0, s>>>(a);
     else
-      pair_kernel<Fixed, false><<<grid, NT, 0, s>>>(a);
+      rec ? pair_kernel<FixedI, false, true><<<grid, NT, 0, s>>>(a)
+          : pair_kernel<FixedI, false, false><<<grid, NT, 0, s>>>(a);
   } else {
     if (second)
-      pair_kernel<Fp64, true><<<grid, NT, 0, s>>>(a);
+      rec ? pair_kernel<Fp64, true, true><<<grid, NT, 0, s>>>(a)
+          : pair_kernel<Fp64, true, false><<<grid, NT, 0, s>>>(a);
     else
-      pair_kernel<Fp64, false><<<grid, NT, 0, s>>>(a);
+      rec ? pair_kernel<Fp64, false, true><<<grid, NT, 0, s>>>(a)
+          : pair_kernel<Fp64, false, false><<<grid, NT, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -729,9 +765,9 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {
   set_carveouts();
   if (arith == 1)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                         pair_kernel<Fixed, true>, NT, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pair_kernel<Fp64, true>,
-                                                       NT, 0);
+                                                         pair_kernel<FixedI, true, true>, NT, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                       pair_kernel<Fp64, true, true>, NT, 0);
 }
 
 int stage_threads() { return NT; }

@@ -191,8 +191,11 @@ struct Fp64 {
   __device__ __forceinline__ static double to_double(T r) { return r; }
   // r * 2^(k - S) with S = 0: an exact power-of-two multiply
   __device__ __forceinline__ double scaled(T r, int k) const { return r * exp2_int(k); }
-  // d * 2^k for a result d of scaled()
-  __device__ __forceinline__ double rescale(double d, int k) const { return d * exp2_int(k); }
+  // (r * 2^k0, r * 2^k1)
+  __device__ __forceinline__ void scaled2(T r, int k0, int k1, double& d0, double& d1) const {
+    d0 = r * exp2_int(k0);
+    d1 = r * exp2_int(k1);
+  }
 };
 
 struct Fixed {
@@ -221,11 +224,44 @@ struct Fixed {
                            ((long long)(k - (1077 - E)) << 52);
     return r == 0 ? 0.0 : __longlong_as_double(bits);
   }
-  // d * 2^k for a result d of scaled() and -8 <= k <= 0: every nonzero d has
-  // |d| >= 2^(E - 1077) >= 2^-1013, so the product stays normal and the
-  // exponent field can be adjusted on the integer pipe
-  __device__ __forceinline__ double rescale(double d, int k) const {
-    return d == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) + ((long long)k << 52));
+  // scaled(r, k0) and scaled(r, k1) from one conversion (k0, k1 >= -8: a
+  // nonzero result has |r| >= 1 and stays normal)
+  __device__ __forceinline__ void scaled2(T r, int k0, int k1, double& d0, double& d1) const {
+    const long long b = __double_as_longlong(__ll2double_rn(r)) - ((long long)(1077 - E) << 52);
+    d0 = r == 0 ? 0.0 : __longlong_as_double(b + ((long long)k0 << 52));
+    d1 = r == 0 ? 0.0 : __longlong_as_double(b + ((long long)k1 << 52));
+  }
+};
+
+// The Fixed form with the int64 -> FP64 conversion on the integer pipes:
+// the leading one is found with a count of leading zeros, the next 52 bits
+// become the significand, rounded half away from zero on the 53rd (|error|
+// <= 1/2 ulp; exact ties, which need the 53rd bit set and every lower bit
+// clear, round away from zero instead of to even).  Used where FP64 issue
+// slots, not integer ones, are the scarce resource: GB300 runs FP64 at two
+// lanes per clock per SM, and the hardware conversion takes an FP64 slot.
+struct FixedI : Fixed {
+  // bits of r * 2^(k - S) less the k term, and whether r != 0
+  __device__ __forceinline__ unsigned long long base_bits(T r, bool& nz) const {
+    const unsigned long long a = r < 0 ? 0ull - (unsigned long long)r : (unsigned long long)r;
+    const int lz = __clzll((long long)a);
+    const unsigned long long m = a << (lz & 63);  // leading one at bit 63
+    nz = a != 0;
+    // (m >> 11) carries the leading one into the exponent field, hence 1085
+    return (m >> 11) + ((m >> 10) & 1ull) +
+           ((unsigned long long)(1085 - (1077 - E) - lz) << 52) +
+           ((unsigned long long)r & 0x8000000000000000ull);
+  }
+  __device__ __forceinline__ double scaled(T r, int k) const {
+    bool nz;
+    const unsigned long long b = base_bits(r, nz) + ((unsigned long long)(long long)k << 52);
+    return nz ? __longlong_as_double((long long)b) : 0.0;
+  }
+  __device__ __forceinline__ void scaled2(T r, int k0, int k1, double& d0, double& d1) const {
+    bool nz;
+    const unsigned long long b = base_bits(r, nz);
+    d0 = nz ? __longlong_as_double((long long)(b + ((unsigned long long)(long long)k0 << 52))) : 0.0;
+    d1 = nz ? __longlong_as_double((long long)(b + ((unsigned long long)(long long)k1 << 52))) : 0.0;
   }
 };
 
@@ -249,6 +285,10 @@ template <int NT, class A, int NF, int NS = 1>
 struct Smem {
   typename A::T tile[2 * NS * TileSmem<NT>::kMaxElems];
   double2 pw[2][NF > 0 ? NF : 1][NT];
+  // raw halo pairs and raw column pairs staged by cp.async (several stencil
+  // fields only)
+  double2 hraw[2][NS][NS > 1 ? NT : 1];
+  double2 craw[2][NS][NS > 1 ? NT : 1];
 };
 
 // a point is read by some stencil iff it lies outside the interior along at
@@ -328,6 +368,12 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
     return arith[f].conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
   };
 
+  // With several stencil fields the raw halo pairs of plane k and column
+  // pairs of plane k+2 travel by cp.async with the pointwise fields of plane
+  // k (registers are the scarce resource there); with one they are loaded to
+  // registers a plane ahead.
+  constexpr bool kAsyncHalo = NS > 1;
+
   // running element offsets (advance by one plane per iteration)
   int oc = colOff + (it.z0 + 2) * pz;  // next column load
   int oh = hg + it.z0 * pz;            // next halo load
@@ -337,6 +383,17 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
     if (actA) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) cp_async16(&sm.pw[buf][f][tid], epi.f[f] + op);
+    }
+    if (kAsyncHalo) {
+      const int t = kAsyncHalo ? tid : 0;
+      if (hasH) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) cp_async16(&sm.hraw[buf][f][t], F[f] + oh);
+      }
+#pragma unroll
+      for (int f = 0; f < NS; ++f) cp_async16(&sm.craw[buf][f][t], F[f] + oc);
+      oh += pz;
+      oc += pz;
     }
     cp_async_commit();
     op += pz;
@@ -350,11 +407,15 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
     qb[f] = conv_at(f, ld2(F[f] + oc - 3 * pz), it.z0 - 1);
     qc[f] = conv_at(f, ld2(F[f] + oc - 2 * pz), it.z0);
     qd[f] = conv_at(f, ld2(F[f] + oc - pz), it.z0 + 1);
-    rc[f] = ld2(F[f] + oc);
-    rh[f] = ld2(F[f] + oh);
+    if (!kAsyncHalo) {
+      rc[f] = ld2(F[f] + oc);
+      rh[f] = ld2(F[f] + oh);
+    }
   }
-  oc += pz;
-  oh += pz;
+  if (!kAsyncHalo) {
+    oc += pz;
+    oh += pz;
+  }
   stage_pw(0);
 
   const int rowSelf = (ly + 2) * W + 2 * lx + 2;
@@ -365,27 +426,40 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
     const int oz = out_of(k, bx.nz);
 #pragma unroll
     for (int f = 0; f < NS; ++f) {
-      p2[f] = conv_at(f, rc[f], k + 2);
+      if (!kAsyncHalo) p2[f] = conv_at(f, rc[f], k + 2);
       T* buf = sm.tile + (2 * f + (kk & 1)) * bufElems;
       *reinterpret_cast<T2*>(buf + rowSelf) = c0[f];
-      if (hasH)
+      if (!kAsyncHalo && hasH)
         *reinterpret_cast<T2*>(buf + hs) =
             arith[f].conv(rh[f], hx0 + oz <= 1, hx1 + oz <= 1, err);
     }
     // issue the next plane's loads before waiting on this one
     if (kk + 1 < it.nzr) {
+      if (!kAsyncHalo) {
 #pragma unroll
-      for (int f = 0; f < NS; ++f) {
-        rc[f] = ld2(F[f] + oc);
-        rh[f] = ld2(F[f] + oh);
+        for (int f = 0; f < NS; ++f) {
+          rc[f] = ld2(F[f] + oc);
+          rh[f] = ld2(F[f] + oh);
+        }
+        oc += pz;
+        oh += pz;
       }
-      oc += pz;
-      oh += pz;
       stage_pw((kk + 1) & 1);
     } else {
       cp_async_commit();
     }
     cp_async_wait_one();
+    if (kAsyncHalo) {
+      // this thread's own copies are complete and visible to it
+      const int t = kAsyncHalo ? tid : 0;
+#pragma unroll
+      for (int f = 0; f < NS; ++f) {
+        if (hasH)
+          *reinterpret_cast<T2*>(sm.tile + (2 * f + (kk & 1)) * bufElems + hs) =
+              arith[f].conv(sm.hraw[kk & 1][f][t], hx0 + oz <= 1, hx1 + oz <= 1, err);
+        p2[f] = conv_at(f, sm.craw[kk & 1][f][t], k + 2);
+      }
+    }
     __syncthreads();
     if (actA) {
       T rA[NS], rB[NS];

@@ -65,6 +65,8 @@ struct PairArgs {
   double* out_u;     // A: w_2.u, w_2.pi.  B: y.u, y.pi (in place)
   double* out_p;
   double* ly;        // A: 12 h^2 L y.u
+  double* rec0;      // or NULL; else C_s L w_{s-1}.u of the pass's two stages,
+  double* rec1;      //   scaled as the stage kernel records them
   const StageCoef* coef;    // [4 ndom], stage s at s * ndom
   const unsigned* emax_in;  // [2 ndom]: exponent bounds of s0, s1
   unsigned* emax_out;       // [2 ndom]: of out_u, out_p (zero on entry)
@@ -83,20 +85,24 @@ struct LapArgs {
   unsigned* err;
 };
 
-struct AdjArgs {
+// Two applications of M = L(c2 .) per pass (see kernels.cu, adj2_kernel).
+struct Adj2Args {
   const DItem* items;
   int nitems;
   int ndom;
   const DBox* boxes;
-  const double* z_in;  // stencil input (ghosts filled)
+  const double* z0_in;  // stencil inputs, ghosts filled
+  const double* z1_in;
   const double* c2;
-  double* p_out;       // Phat = 12 h^2 L z_in
-  double* z_out;       // c2 Phat (adj_a only), ghosts pushed
+  double* p0_out;       // Phat = 12 h^2 L z_in
+  double* p1_out;
+  double* z0_out;       // first pass: c2 Phat, ghosts pushed
+  double* z1_out;
   const DPush* push;
   const int* push_gofs;
-  const unsigned* emax_in;
-  unsigned* emax_out;
-  unsigned* emax_clear;
+  const unsigned* emax_in;  // [2 ndom]
+  unsigned* emax_out;       // [2 ndom] (first pass)
+  unsigned* emax_clear;     // [2 ndom] zeroed for a later launch, or NULL
   unsigned* err;
 };
 
@@ -145,8 +151,7 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm);
 // two fields over one exchange list; block 0 zeroes clear[0..nclear)
 cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
                            double* g, unsigned* clear, int nclear, cudaStream_t s);
-// kind 0: adj_a (Phat and c2 Phat), kind 1: adj_b (Phat only)
-cudaError_t launch_adj(int kind, int arith, const AdjArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adj2(bool second, int arith, const Adj2Args& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chunks,
                                int nchunks, const AdjCombineArgs& a, int grid, cudaStream_t s);
 int stage_threads();

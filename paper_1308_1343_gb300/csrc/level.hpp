@@ -102,7 +102,8 @@ struct sc_level {
   std::vector<int> box_class;
   std::vector<sc::SizeClass> classes;
   int arith = SC_ARITH_FIXED;
-  int fuse = 1;  // RK4 stages per stencil pass of sc_level_rk4_step: 1 or 2
+  int fuse = 2;             // RK4 stages per stencil pass of sc_level_rk4_step: 1 or 2
+  bool fuse_fixed = false;  // set by sc_level_set_fusion; else the autotuner chooses
   int ctas_per_sm = 0;
   int version = 0;  // bumps when items change (invalidates graphs)
   int64_t launches = 0;

@@ -292,6 +292,7 @@ int sc_level_set_fusion(sc_level* L, int32_t stages_per_pass) {
   if (stages_per_pass != 1 && stages_per_pass != 2)
     return set_error(SC_EINVAL, "stages_per_pass must be 1 or 2");
   L->fuse = stages_per_pass;  // the step graphs are keyed by it
+  L->fuse_fixed = true;
   return SC_OK;
 }
 

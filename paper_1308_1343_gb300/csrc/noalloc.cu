@@ -11,7 +11,8 @@
 //
 // The arithmetic is the FP64 form of the level library's stage kernel (the
 // same tile traversal, stencil sum and nested RK4 stages), so results agree
-// with sc_level_rk4_step in SC_ARITH_FP64 on a one-box periodic level.
+// with sc_level_rk4_step in SC_ARITH_FP64 with one stage per pass on a one-box
+// periodic level.
 #include <mutex>
 
 #include "../../include/sc_level.h"

@@ -550,8 +550,10 @@ static cudaError_t enq_pair(const Enq& q, dev::PairArgs a, bool second) {
 // One RK4 step in two passes of two stages each (see kernels.cu): W[0], W[1]
 // receive w_2, W[2] receives 12 h^2 L y.u.  Exponent slots: X = emax[0, 2
 // ndom) holds the bounds of (u, pi), Y = emax[2 ndom, 4 ndom) those of w_2;
-// each gather zeroes the slots that the pass after it accumulates into.
-static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* const* W) {
+// each gather zeroes the slots that the pass after it accumulates into.  If
+// lapw is not NULL, lapw[s] receives C_{s+1} L w_s.u as enq_step records it.
+static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* const* W,
+                                  double* const* lapw = nullptr) {
   DeviceState* D = q.L->dev;
   const int nd = (int)q.L->doms.size();
   const bool fixed = q.L->arith == SC_ARITH_FIXED;
@@ -575,6 +577,8 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
   a.emax_in = X;
   a.emax_out = Y;
   a.err = D->err;
+  a.rec0 = lapw ? lapw[0] : nullptr;
+  a.rec1 = lapw ? lapw[1] : nullptr;
   if ((e = enq_pair(q, a, false)) != cudaSuccess) return e;
   if ((e = enq_fill2(q, W[0], W[1], fixed ? X : nullptr)) != cudaSuccess) return e;
   a.s0 = W[0];
@@ -585,6 +589,8 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
   a.ly = nullptr;
   a.emax_in = Y;
   a.emax_out = X;
+  a.rec0 = lapw ? lapw[2] : nullptr;
+  a.rec1 = lapw ? lapw[3] : nullptr;
   return enq_pair(q, a, true);
 }
 
@@ -814,8 +820,11 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
         (rc = get_field(L, "ck.pi." + std::to_string(c), &ckp[c])))
       return rc;
   L->tape_valid = false;
+  // two stages per pass exchange ghosts by gathers; one stage per pass has
+  // each stage kernel push the ghosts of what it writes
+  const bool pairs = L->fuse == 2;
   Enq q{L, s, &L->launches, false};
-  q.push = true;
+  q.push = !pairs;
   if (L->profile) {
     q.timed = true;
     D->ev_used = 0;
@@ -827,8 +836,9 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(cku[c], Su, bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(ckp[c], Sp, bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su, nullptr, c2, W));
-    for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, nullptr));
+    SC_CUDA(enq_prologue(q, Su, pairs ? Sp : nullptr, c2, W));
+    for (int n = 0; n < len; ++n)
+      SC_CUDA(pairs ? enq_step_pairs(q, Su, Sp, W) : enq_step(q, Su, Sp, c2, W, nullptr));
   }
   if (u_T) SC_CUDA(cudaMemcpyAsync(u_T, Su, bytes, cudaMemcpyDeviceToDevice, s));
   if (pi_T) SC_CUDA(cudaMemcpyAsync(pi_T, Sp, bytes, cudaMemcpyDeviceToDevice, s));
@@ -883,6 +893,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     D->ev_kind.clear();
   }
   const bool fixed = L->arith == SC_ARITH_FIXED;
+  const bool pairs = L->fuse == 2;  // form of the forward recomputation
   double *P4, *P3, *P2, *P1;
   if ((rc = get_field(L, "P4", &P4)) || (rc = get_field(L, "P3", &P3)) ||
       (rc = get_field(L, "P2", &P2)) || (rc = get_field(L, "P1", &P1)))
@@ -919,11 +930,17 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su, nullptr, c2, W));
-    for (int n = 0; n < len; ++n) SC_CUDA(enq_step(q, Su, Sp, c2, W, lapw.data() + 4 * n));
+    SC_CUDA(enq_prologue(q, Su, pairs ? Sp : nullptr, c2, W));
+    for (int n = 0; n < len; ++n) {
+      Enq qf = q;
+      qf.push = !pairs;
+      SC_CUDA(pairs ? enq_step_pairs(qf, Su, Sp, W, lapw.data() + 4 * n)
+                    : enq_step(qf, Su, Sp, c2, W, lapw.data() + 4 * n));
+    }
     for (int n = len - 1; n >= 0; --n, ++n_adj) {
       const int p = (int)(n_adj & 1), pn = 1 - p;
-      dev::AdjArgs a{};
+      // (Phat4, Phat3) = L^ (c2 b, c2 a), (X', Y') = c2 (Phat4, Phat3)
+      dev::Adj2Args a{};
       a.items = D->items;
       a.nitems = D->nitems;
       a.ndom = nd;
@@ -932,51 +949,33 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
       a.err = D->err;
       a.push = D->push;
       a.push_gofs = D->push_gofs;
-      // P4hat = L^(c2 b), X' = c2 P4hat
-      a.z_in = X;
-      a.p_out = P4;
-      a.z_out = Xp;
-      a.emax_in = slot(2 * p);
-      a.emax_out = slot(4 + 2 * p);
+      a.z0_in = X;
+      a.z1_in = Y;
+      a.p0_out = P4;
+      a.p1_out = P3;
+      a.z0_out = Xp;
+      a.z1_out = Yq;
+      a.emax_in = slot(2 * p);       // X, Y: slots 2p, 2p+1
+      a.emax_out = slot(4 + 2 * p);  // X', Y': slots 4+2p, 5+2p
       a.emax_clear = slot(2 * pn);
       L->launches++;
       {
         TimedLaunch t(q, SC_KERNEL_ADJ_A);
-        SC_CUDA(dev::launch_adj(0, L->arith, a, D->grid_stage, s));
+        SC_CUDA(dev::launch_adj2(false, L->arith, a, D->grid_pair, s));
       }
-      // P3hat = L^(c2 a), Y' = c2 P3hat
-      a.z_in = Y;
-      a.p_out = P3;
-      a.z_out = Yq;
-      a.emax_in = slot(2 * p + 1);
-      a.emax_out = slot(5 + 2 * p);
-      a.emax_clear = slot(2 * pn + 1);
-      L->launches++;
-      {
-        TimedLaunch t(q, SC_KERNEL_ADJ_A);
-        SC_CUDA(dev::launch_adj(0, L->arith, a, D->grid_stage, s));
-      }
-      // P2hat = L^ X'
-      a.z_in = Xp;
-      a.p_out = P2;
-      a.z_out = nullptr;
+      // (Phat2, Phat1) = L^ (X', Y')
+      a.z0_in = Xp;
+      a.z1_in = Yq;
+      a.p0_out = P2;
+      a.p1_out = P1;
+      a.z0_out = a.z1_out = nullptr;
       a.emax_in = slot(4 + 2 * p);
       a.emax_out = nullptr;
       a.emax_clear = slot(4 + 2 * pn);
       L->launches++;
       {
         TimedLaunch t(q, SC_KERNEL_ADJ_B);
-        SC_CUDA(dev::launch_adj(1, L->arith, a, D->grid_stage, s));
-      }
-      // P1hat = L^ Y'
-      a.z_in = Yq;
-      a.p_out = P1;
-      a.emax_in = slot(5 + 2 * p);
-      a.emax_clear = slot(5 + 2 * pn);
-      L->launches++;
-      {
-        TimedLaunch t(q, SC_KERNEL_ADJ_B);
-        SC_CUDA(dev::launch_adj(1, L->arith, a, D->grid_stage, s));
+        SC_CUDA(dev::launch_adj2(true, L->arith, a, D->grid_pair, s));
       }
       // the combination, pointwise
       dev::AdjCombineArgs b{};

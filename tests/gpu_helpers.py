@@ -19,11 +19,15 @@ def upload(lev, arrays, fill=0.0):
     return lev.to_device(list(arrays), fill=fill)
 
 
-def run_gpu(instances, nsteps, arith, mode, lev=None):
-    """Evolve every instance on the GPU; returns (lev, [u], [pi])."""
+def run_gpu(instances, nsteps, arith, mode, lev=None, fuse=1):
+    """Evolve every instance on the GPU; returns (lev, [u], [pi]).  A new
+    level runs `fuse` RK4 stages per stencil pass; a given one keeps its
+    setting."""
     import torch
     from paper_1308_1343_gb300 import binding as B
-    lev = lev or make_level(instances)
+    if lev is None:
+        lev = make_level(instances)
+        lev.set_fusion(fuse)
     lev.set_arith(arith)
     u = upload(lev, [i.u for i in instances])
     pi = upload(lev, [i.pi for i in instances])

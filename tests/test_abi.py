@@ -304,6 +304,8 @@ def test_fusion_setting_and_tile_query(B):
     from paper_1308_1343_gb300.level import Level
     n = (32, 24, 16)
     lev = Level([((0, 0, 0), n, 0)], [dict(hi=n, h=0.1)])
+    assert lev.get_fusion() == 2
+    lev.set_fusion(1)
     assert lev.get_fusion() == 1
     lev.set_fusion(2)
     assert lev.get_fusion() == 2

@@ -21,9 +21,10 @@ def _built():
     build.build()
 
 
-def _setup(inst, arith):
+def _setup(inst, arith, fuse=1):
     lev = make_level([inst])
     lev.set_arith(arith)
+    lev.set_fusion(fuse)
     t = lambda a, fill=0.0: upload(lev, [a], fill)
     return lev, t
 
@@ -38,13 +39,14 @@ def _gpu_forward(lev, t, inst, u0, c2, nsteps):
     return u, pi
 
 
+@pytest.mark.parametrize("fuse", [1, 2])
 @pytest.mark.parametrize("arith", [0, 1])
-def test_gradient_matches_oracle(orc, arith):
+def test_gradient_matches_oracle(orc, arith, fuse):
     import torch
     inst = W.gradient_problem(20, 4)
     nsteps, ckpt = 16, 5
     h, dt = inst.dom.h, inst.dt
-    lev, t = _setup(inst, arith)
+    lev, t = _setup(inst, arith, fuse)
     u_obs, _ = _gpu_forward(lev, t, inst, inst.u, inst.c2_obs, nsteps)
     u0, pi0, c2 = t(inst.u), t(inst.pi), t(inst.c2, 1.0)
     uT, piT = torch.empty_like(u0), torch.empty_like(u0)
@@ -77,15 +79,16 @@ def test_misfit_matches_oracle(orc):
     assert rel_err(lev.gather(seed)[0], orc.misfit_seed(inst.u, inst.c2_obs, inst.dom.h)) <= 1e-15
 
 
+@pytest.mark.parametrize("fuse", [1, 2])
 @pytest.mark.parametrize("n,nsteps,ckpt", [(20, 12, 5), (128, 200, 20)])
-def test_dot_identity_and_finite_differences(n, nsteps, ckpt):
+def test_dot_identity_and_finite_differences(n, nsteps, ckpt, fuse):
     """Linear in u0: <u_T(d), a> + <pi_T(d), b> = <d, g_u0(a, b)>; and central
     differences of the misfit along c2 and u0 directions (the 128^3 case is
     the differentiation workload's full size)."""
     import torch
     inst = W.gradient_problem(n, 4)
     h, dt = inst.dom.h, inst.dt
-    lev, t = _setup(inst, 1)
+    lev, t = _setup(inst, 1, fuse)
     sh = inst.dom.shape
     d = W.random_direction(sh, 41)
     a = W.random_direction(sh, 43)
@@ -150,8 +153,9 @@ def test_autograd_function():
     assert rel_err(lev.gather(c2.grad)[0], lev.gather(g[2])[0]) == 0
 
 
+@pytest.mark.parametrize("fuse", [1, 2])
 @pytest.mark.parametrize("arith", [0, 1])
-def test_gradient_on_uneven_level(orc, arith):
+def test_gradient_on_uneven_level(orc, arith, fuse):
     """Adjoint on an uneven multi-box level: equal to the one-box level's
     gradient bit for bit (decomposition independence) and to the oracle."""
     import torch
@@ -162,6 +166,7 @@ def test_gradient_on_uneven_level(orc, arith):
     for insts in ([inst], [W.Instance(inst.dom, inst.u, inst.pi, inst.c2, inst.dt)]):
         lev = make_level(insts)
         lev.set_arith(arith)
+        lev.set_fusion(fuse)
         t = lambda a, fill=0.0: upload(lev, [a], fill)
         seed_u = W.random_direction(inst.dom.shape, 43)
         g = [torch.empty(lev.field_size, dtype=torch.float64, device="cuda") for _ in range(3)]

@@ -163,3 +163,20 @@ def test_full_256_bumpy_vs_oracle(orc):
     _, u, pi = run_fused([inst], 2, 1, 0)
     assert rel_err(u[0], ou) <= TOL
     assert rel_err(pi[0], op) <= TOL
+
+
+def test_autotune_chooses_a_form(orc, tmp_path):
+    """Without a fixed form the tuner picks one; the result still matches the
+    oracle and equals that form's run with default tiles bit for bit."""
+    inst = W.uneven_level(n=(64, 64, 32), h=1.0 / 32, levels=3, seed=3, box_seed=30)
+    lev = make_level([inst])
+    lev.set_arith(1)
+    lev.autotune(seed=1, budget_ms=400.0, abort_factor=2.0, cache_path=str(tmp_path / "t.txt"))
+    form = lev.get_fusion()
+    assert form in (1, 2)
+    _, u, pi = run_gpu([inst], 3, 1, 0, lev=lev)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 3)
+    assert rel_err(u[0], ou) <= TOL
+    assert rel_err(pi[0], op) <= TOL
+    _, u1, p1 = run_gpu([inst], 3, 1, 0, fuse=form)
+    assert np.array_equal(u[0], u1[0]) and np.array_equal(pi[0], p1[0])

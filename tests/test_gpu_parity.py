@@ -265,14 +265,16 @@ def test_full_uneven_level_vs_oracle(orc):
 
 @pytest.mark.parametrize("arith", [0, 1])
 def test_ghosts_written_by_stage_kernels(orc, arith):
-    """In the taped forward the stage kernels write the ghost copies of every
-    value they produce; the final state's ghosts must equal a fresh exchange
-    of its interior, bit for bit, on a 64-box level and on a single box."""
+    """In the taped forward with one stage per pass the stage kernels write
+    the ghost copies of every value they produce; the final state's ghosts
+    must equal a fresh exchange of its interior, bit for bit, on a 64-box
+    level and on a single box."""
     import torch
     for inst in (W.uneven_level(n=(96, 80, 64), h=1.0 / 64, levels=6, seed=3, box_seed=30),
                  W.bumpy_instance(W.Domain((36, 28, 20), 1.0 / 28), 5)):
         lev = make_level([inst])
         lev.set_arith(arith)
+        lev.set_fusion(1)
         u = upload(lev, [inst.u], fill=np.nan)
         pi = upload(lev, [inst.pi])
         c2 = upload(lev, [inst.c2], fill=1.0)

@@ -47,6 +47,7 @@ def test_noalloc_matches_level_step_two_calls():
         inst = W.bumpy_instance(W.Domain(n, 1.0 / n[1]), seed)
         lev = Level.from_instances([inst])
         lev.set_arith(B.SC_ARITH_FP64)
+        lev.set_fusion(1)
         u = lev.to_device([inst.u])
         pi = lev.to_device([inst.pi])
         c2 = lev.to_device([inst.c2], fill=1.0)
