@@ -215,6 +215,73 @@ int oracle_rk4_periodic(double *u, double *pi, const double *c2,
 }
 
 /*
+ * One classic RK4 step on ONE padded box whose ghost ring holds boundary
+ * values (ghost width 2 on every side; u, pi, c2 dense, (nz+4)(ny+4)(nx+4),
+ * x fastest).  The ghost values of every stage input Y_s.u are those of u at
+ * the start of the step (boundary data held fixed over the step); only the
+ * interior of u and pi changes.  The stage expressions and their order are
+ * those of oracle_rk4_periodic, so interior points whose dependence cone
+ * stays inside the box get the same bits as a periodic run.
+ * Returns 0, or -1 if a temporary could not be allocated.
+ */
+int oracle_rk4_padded(double *u, double *pi, const double *c2,
+                      i64 nx, i64 ny, i64 nz, double h, double dt)
+{
+    const i64 px = nx + 4, py = ny + 4, pz = nz + 4;
+    const i64 n = nx * ny * nz, np = px * py * pz;
+    double *Ku[4], *Kp[4];
+    double *Yu = alloc_d(np), *Yp = alloc_d(n), *lap = alloc_d(n);
+    int ok = Yu && Yp && lap;
+    for (int s = 0; s < 4; ++s) {
+        Ku[s] = alloc_d(n);
+        Kp[s] = alloc_d(n);
+        ok = ok && Ku[s] && Kp[s];
+    }
+    if (!ok) {
+        free(Yu); free(Yp); free(lap);
+        for (int s = 0; s < 4; ++s) { free(Ku[s]); free(Kp[s]); }
+        return -1;
+    }
+#define IP(ii, jj, kk) ((((kk) + 2) * py + ((jj) + 2)) * px + ((ii) + 2))
+    memcpy(Yu, u, (size_t)np * sizeof(double));
+    for (i64 k = 0; k < nz; ++k)
+        for (i64 j = 0; j < ny; ++j)
+            for (i64 i = 0; i < nx; ++i)
+                Yp[(k * ny + j) * nx + i] = pi[IP(i, j, k)];
+    for (int s = 0; s < 4; ++s) {
+        oracle_lap_padded(Yu, lap, nx, ny, nz, h);
+        for (i64 k = 0; k < nz; ++k)
+            for (i64 j = 0; j < ny; ++j)
+                for (i64 i = 0; i < nx; ++i) {
+                    const i64 q = (k * ny + j) * nx + i;
+                    Ku[s][q] = Yp[q];
+                    Kp[s][q] = c2[IP(i, j, k)] * lap[q];
+                }
+        if (s < 3) {
+            const double a = RK_A[s + 1] * dt;
+            for (i64 k = 0; k < nz; ++k)
+                for (i64 j = 0; j < ny; ++j)
+                    for (i64 i = 0; i < nx; ++i) {
+                        const i64 q = (k * ny + j) * nx + i, g = IP(i, j, k);
+                        Yu[g] = u[g] + a * Ku[s][q];
+                        Yp[q] = pi[g] + a * Kp[s][q];
+                    }
+        }
+    }
+    for (i64 k = 0; k < nz; ++k)
+        for (i64 j = 0; j < ny; ++j)
+            for (i64 i = 0; i < nx; ++i) {
+                const i64 q = (k * ny + j) * nx + i, g = IP(i, j, k);
+                u[g] = u[g] + dt * (Ku[0][q] + 2.0 * Ku[1][q] + 2.0 * Ku[2][q] + Ku[3][q]) / 6.0;
+                pi[g] = pi[g] + dt * (Kp[0][q] + 2.0 * Kp[1][q] + 2.0 * Kp[2][q] + Kp[3][q]) / 6.0;
+            }
+#undef IP
+    free(Yu); free(Yp); free(lap);
+    for (int s = 0; s < 4; ++s) { free(Ku[s]); free(Kp[s]); }
+    return 0;
+}
+
+/*
  * Discrete energy E = 1/2 sum( pi^2 / c2 - u * (L u) ) h^3 over the periodic
  * domain.  For c2 > 0 and the symmetric negative semi-definite L this is a
  * non-negative quadratic form, conserved by the semi-discrete system.

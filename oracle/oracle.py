@@ -15,7 +15,8 @@ What each function follows:
   difference summed over the axes, the centred-difference idiom on padded
   arrays of the paper's Sec. 4.3 ("Iterators").
 * ``rk4_periodic`` -- classic RK4 stage form for y' = A y,
-  A(u, pi) = (pi, c2 * L u).
+  A(u, pi) = (pi, c2 * L u); ``rk4_padded`` -- the same step on one padded
+  box whose ghosts hold boundary values.
 * ``tlm_periodic`` / ``adj_step_periodic`` / ``grad_periodic`` -- the
   tangent-linear and adjoint of that step and the checkpointed reverse sweep.
 * ``fill_ghosts`` / ``ghost_owners`` -- the ghost exchange of a level of
@@ -66,6 +67,9 @@ def _configure(lib):
     lib.oracle_rk4_periodic.argtypes = [_dp, _dp, _dp, _i64, _i64, _i64,
                                         ctypes.c_double, ctypes.c_double, _i64]
     lib.oracle_rk4_periodic.restype = ctypes.c_int
+    lib.oracle_rk4_padded.argtypes = [_dp, _dp, _dp, _i64, _i64, _i64, ctypes.c_double,
+                                      ctypes.c_double]
+    lib.oracle_rk4_padded.restype = ctypes.c_int
     lib.oracle_energy_periodic.argtypes = [_dp, _dp, _dp, _i64, _i64, _i64,
                                            ctypes.c_double]
     lib.oracle_energy_periodic.restype = ctypes.c_double
@@ -171,6 +175,20 @@ def rk4_periodic(u, pi, c2, h: float, dt: float, nsteps: int):
     if rc:
         raise MemoryError("oracle_rk4_periodic: allocation failed")
     return u, pi
+
+
+def rk4_padded(up, pip, c2p, h: float, dt: float):
+    """One classic RK4 step on one padded box (ghost width 2) whose ghosts
+    hold boundary values, held fixed over the step; returns new padded
+    (u, pi) with the ghosts unchanged."""
+    up = _f64(up).copy()
+    pip = _f64(pip).copy()
+    c2p = _f64(c2p)
+    nz, ny, nx = (s - 4 for s in up.shape)
+    rc = _load().oracle_rk4_padded(_d(up), _d(pip), _d(c2p), nx, ny, nz, float(h), float(dt))
+    if rc:
+        raise MemoryError("oracle_rk4_padded: allocation failed")
+    return up, pip
 
 
 def energy(u, pi, c2, h: float) -> float:
