@@ -54,6 +54,13 @@ int sc_bboxset_expand_shift(const int64_t* a, int64_t na, const int64_t lo_by[3]
                             const int64_t hi_by[3], const int64_t v[3], int64_t* out,
                             int64_t cap, int64_t* n);
 
+/* Spacing change (Sec. 2): the points c of a grid with `ratio` times the
+ * spacing, sharing the origin, that coincide with points of the union of
+ * the boxes: {c : ratio * c in A} (vertex-centred).  Writes the normalized
+ * box list.  Errors: SC_EINVAL for ratio < 1. */
+int sc_bboxset_coarsen(const int64_t* a, int64_t na, int64_t ratio, int64_t* out, int64_t cap,
+                       int64_t* n);
+
 /* Number of points of the union of the boxes (the union, not the sum). */
 int sc_bboxset_size(const int64_t* a, int64_t na, int64_t* npoints);
 

@@ -87,6 +87,15 @@ _SIGS = {
     "sc_bboxset_derivative": (_i32, [_p64, _i64, _p64, _i64, _p64]),
     "sc_bboxset_expand_shift": (_i32, [_p64, _i64, _p64, _p64, _p64, _p64, _i64, _p64]),
     "sc_bboxset_size": (_i32, [_p64, _i64, _p64]),
+    "sc_bboxset_coarsen": (_i32, [_p64, _i64, _i64, _p64, _i64, _p64]),
+    "sc_hierarchy_create": (_i32, [_vp, _vp, _i32, _i32, ctypes.POINTER(_vp)]),
+    "sc_hierarchy_destroy": (None, [_vp]),
+    "sc_hierarchy_counts": (_i32, [_vp, _p64, _p64]),
+    "sc_hierarchy_prolongation_points": (_i32, [_vp, _p64, _i64, _p64]),
+    "sc_hierarchy_restriction_points": (_i32, [_vp, _p64, _i64, _p64]),
+    "sc_hierarchy_prolongate": (_i32, [_vp, _vp, _vp, _vp, _vp, _dbl, _vp, _vp, _vp]),
+    "sc_hierarchy_restrict": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sc_hierarchy_step": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i32, _i32, _vp]),
 }
 
 _lock = threading.Lock()

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsc_level.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "runtime.cu", "autotune.cu", "noalloc.cu", "level_host.cpp"]
+SOURCES = ["kernels.cu", "runtime.cu", "autotune.cu", "noalloc.cu", "hierarchy.cu",
+           "level_host.cpp"]
 
 
 def _nvcc() -> str:

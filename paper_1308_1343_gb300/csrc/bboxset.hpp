@@ -260,4 +260,24 @@ inline BBoxSet3 set_of(const std::vector<BBox3>& bs) {
   return s;
 }
 
+// Spacing change (Sec. 2 lists it among the bboxset operations): the
+// points c of the grid with r times the spacing whose position coincides
+// with a point of S, {c : r c in S} (vertex-centred grids sharing the
+// origin).  A preimage commutes with union, so the normalized boxes can be
+// mapped one by one: [lo, hi) -> [ceil(lo / r), ceil(hi / r)).
+inline int64_t ceil_div(int64_t a, int64_t r) { return a >= 0 ? (a + r - 1) / r : -((-a) / r); }
+
+inline BBoxSet3 coarsened(const BBoxSet3& S, int64_t r) {
+  BBoxSet3 out;
+  for (const BBox3& b : S.boxes()) {
+    BBox3 c;
+    for (int d = 0; d < 3; ++d) {
+      c.lo[d] = ceil_div(b.lo[d], r);
+      c.hi[d] = ceil_div(b.hi[d], r);
+    }
+    if (!c.empty()) out = out | BBoxSet3::box(c);
+  }
+  return out;
+}
+
 }  // namespace sc

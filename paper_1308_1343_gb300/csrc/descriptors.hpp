@@ -35,6 +35,28 @@ struct DRect {
   int x0, y0, z0;            // interior coordinates of the first point
 };
 
+// A rectangle of fine points that prolongation fills (interior points of
+// one fine box, or ghost points of its shell), all drawing on the interior
+// of one coarse box.
+struct DProl {
+  long long dst;       // fine element index of the first point
+  int dpy, dpz;        // fine box pitches
+  int ex, ey, ez;      // extent
+  int fx0, fy0, fz0;   // fine level index of the first point
+  long long cbase;     // coarse element index of coarse level index (0, 0, 0)
+                       // in the coarse box's layout (may lie outside the box)
+  int cpy, cpz;        // coarse box pitches
+};
+
+// A rectangle of coarse points that restriction sets from fine points 2c.
+struct DRestr {
+  long long dst;       // coarse element index of the first point
+  int dpy, dpz;        // coarse box pitches
+  int ex, ey, ez;      // extent
+  long long src;       // fine element index of the fine point under the first
+  int spy, spz;        // fine box pitches (the source advances by 2 per point)
+};
+
 // One ghost copy seen from its source: the source rectangle in the source
 // box's interior coordinates [lo, hi) and where its first point goes.  A
 // producer that writes point (x, y, z) of the source box inside the

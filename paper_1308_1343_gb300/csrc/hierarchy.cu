@@ -1,0 +1,353 @@
+// Two-level refinement hierarchy: the prolongation and restriction lists
+// derived with the bboxset algebra (arXiv 1308.1343, Sec. 2: AMR operators
+// determined from bboxsets), their kernels' launches, and the Berger-Oliger
+// step.  The readings (operators, buffer zone, sub-cycling) are stated in
+// include/sc_hierarchy.h.
+#include <algorithm>
+#include <array>
+#include <string>
+#include <vector>
+
+#include "../../include/sc_hierarchy.h"
+#include "bboxset.hpp"
+#include "level.hpp"
+
+using sc::BBox3;
+using sc::BBoxSet3;
+
+struct sc_hierarchy {
+  sc_level* coarse = nullptr;
+  sc_level* fine = nullptr;
+  int buffer = 4;
+  BBox3 R, T;
+  std::vector<sc::dev::DProl> prol;
+  std::vector<sc::dev::DChunk> prol_chunks;
+  std::vector<sc::dev::DRestr> restr;
+  std::vector<sc::dev::DChunk> restr_chunks;
+  // each list's rectangles in level coordinates (lo, hi), for the queries
+  std::vector<std::array<int64_t, 6>> prol_rects, restr_rects;
+  int64_t n_prol = 0, n_restr = 0;
+  // device copies (on the coarse level's device)
+  sc::dev::DProl* d_prol = nullptr;
+  sc::dev::DChunk* d_prol_chunks = nullptr;
+  sc::dev::DRestr* d_restr = nullptr;
+  sc::dev::DChunk* d_restr_chunks = nullptr;
+  int device = -1;
+};
+
+namespace sc {
+namespace {
+
+BBox3 box_of(const int64_t* lo, const int64_t* hi) {
+  BBox3 b;
+  for (int d = 0; d < 3; ++d) {
+    b.lo[d] = lo[d];
+    b.hi[d] = hi[d];
+  }
+  return b;
+}
+
+// Star-shaped ghost shell of a box: points outside along exactly one axis,
+// within 2 of it.
+BBoxSet3 star_shell(const BBox3& b) {
+  const BBoxSet3 B = BBoxSet3::box(b);
+  BBoxSet3 s;
+  for (int d = 0; d < 3; ++d) {
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    lo[d] = hi[d] = 2;
+    s = s | B.expanded(lo, hi);
+  }
+  return s - B;
+}
+
+// Element index of level point p in box b's padded layout.
+long long elem(const sc_level* L, int b, const int64_t* p) {
+  const sc_box& B = L->boxes[b];
+  return (long long)(L->off[b] + (p[0] - B.lo[0]) + (p[1] - B.lo[1]) * L->py[b] +
+                     (p[2] - B.lo[2]) * L->pz[b]);
+}
+
+// Fine points whose prolongation stencil lies inside coarse box [clo, chi):
+// along each axis, odd f needs coarse (f-3)/2 .. (f+3)/2 and even f needs f/2,
+// so f in [2 clo + 3, 2 chi - 4) always fits (a conservative box).
+BBox3 safe_fine(const sc_box& cb) {
+  BBox3 r;
+  for (int d = 0; d < 3; ++d) {
+    r.lo[d] = 2 * cb.lo[d] + 3;
+    r.hi[d] = 2 * cb.hi[d] - 4;
+  }
+  return r;
+}
+
+void add_chunks(int rect, int64_t n, std::vector<dev::DChunk>& out) {
+  for (int64_t f = 0; f < n; f += dev::kGatherChunk) out.push_back(dev::DChunk{rect, (int)f});
+}
+
+template <class T>
+int upload(T** dst, const std::vector<T>& v) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (v.empty()) return SC_OK;
+  if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SC_ENOMEM, "hierarchy: device allocation failed");
+  }
+  if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_error(SC_ECUDA, "hierarchy: upload failed");
+  return SC_OK;
+}
+
+int build_lists(sc_hierarchy* H) {
+  const sc_level* C = H->coarse;
+  const sc_level* F = H->fine;
+  const BBoxSet3 Rs = BBoxSet3::box(H->R), Ts = BBoxSet3::box(H->T);
+  // prolongation: per fine box, its buffer-band points and its shell points
+  // outside R, assigned to the first coarse box whose interior holds their
+  // stencils
+  for (size_t fb = 0; fb < F->boxes.size(); ++fb) {
+    const sc_box& B = F->boxes[fb];
+    const BBox3 bb = box_of(B.lo, B.hi);
+    BBoxSet3 todo = ((BBoxSet3::box(bb) - Ts) | (star_shell(bb) - Rs));
+    for (size_t cb = 0; cb < C->boxes.size() && !todo.empty(); ++cb) {
+      const sc_box& CB = C->boxes[cb];
+      const BBoxSet3 part = todo & BBoxSet3::box(safe_fine(CB));
+      if (part.empty()) continue;
+      todo = todo - part;
+      const long long cbase = (long long)(C->off[cb] - CB.lo[0] - CB.lo[1] * C->py[cb] -
+                                          CB.lo[2] * C->pz[cb]);
+      for (const BBox3& r : part.boxes()) {
+        dev::DProl p{};
+        p.dst = elem(F, (int)fb, r.lo.data());
+        p.dpy = (int)F->py[fb];
+        p.dpz = (int)F->pz[fb];
+        p.ex = (int)(r.hi[0] - r.lo[0]);
+        p.ey = (int)(r.hi[1] - r.lo[1]);
+        p.ez = (int)(r.hi[2] - r.lo[2]);
+        p.fx0 = (int)r.lo[0];
+        p.fy0 = (int)r.lo[1];
+        p.fz0 = (int)r.lo[2];
+        p.cbase = cbase;
+        p.cpy = (int)C->py[cb];
+        p.cpz = (int)C->pz[cb];
+        H->prol.push_back(p);
+        H->prol_rects.push_back({r.lo[0], r.lo[1], r.lo[2], r.hi[0], r.hi[1], r.hi[2]});
+        const int64_t n = (int64_t)p.ex * p.ey * p.ez;
+        add_chunks((int)H->prol.size() - 1, n, H->prol_chunks);
+        H->n_prol += n;
+      }
+    }
+    if (!todo.empty())
+      return set_error(SC_EINVAL, "hierarchy: prolongation stencil of fine box " +
+                                      std::to_string(fb) +
+                                      " lies in no coarse box interior (keep the fine "
+                                      "region 3 coarse points away from coarse box faces)");
+  }
+  // restriction: coarse points c with 2c in T, per (coarse box, fine box)
+  for (size_t cb = 0; cb < C->boxes.size(); ++cb) {
+    const sc_box& CB = C->boxes[cb];
+    for (size_t fb = 0; fb < F->boxes.size(); ++fb) {
+      const sc_box& B = F->boxes[fb];
+      const BBoxSet3 part =
+          coarsened(Ts & BBoxSet3::box(box_of(B.lo, B.hi)), 2) & BBoxSet3::box(box_of(CB.lo, CB.hi));
+      for (const BBox3& r : part.boxes()) {
+        dev::DRestr q{};
+        q.dst = elem(C, (int)cb, r.lo.data());
+        q.dpy = (int)C->py[cb];
+        q.dpz = (int)C->pz[cb];
+        q.ex = (int)(r.hi[0] - r.lo[0]);
+        q.ey = (int)(r.hi[1] - r.lo[1]);
+        q.ez = (int)(r.hi[2] - r.lo[2]);
+        const int64_t f0[3] = {2 * r.lo[0], 2 * r.lo[1], 2 * r.lo[2]};
+        q.src = elem(F, (int)fb, f0);
+        q.spy = (int)F->py[fb];
+        q.spz = (int)F->pz[fb];
+        H->restr.push_back(q);
+        H->restr_rects.push_back({r.lo[0], r.lo[1], r.lo[2], r.hi[0], r.hi[1], r.hi[2]});
+        const int64_t n = (int64_t)q.ex * q.ey * q.ez;
+        add_chunks((int)H->restr.size() - 1, n, H->restr_chunks);
+        H->n_restr += n;
+      }
+    }
+  }
+  return SC_OK;
+}
+
+int ensure_uploaded(sc_hierarchy* H) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return set_error(SC_ECUDA, "cudaGetDevice failed");
+  if (H->device == cur) return SC_OK;
+  if (H->device >= 0) return set_error(SC_EINVAL, "hierarchy was set up on another device");
+  int rc;
+  if ((rc = upload(&H->d_prol, H->prol)) || (rc = upload(&H->d_prol_chunks, H->prol_chunks)) ||
+      (rc = upload(&H->d_restr, H->restr)) ||
+      (rc = upload(&H->d_restr_chunks, H->restr_chunks)))
+    return rc;
+  H->device = cur;
+  return SC_OK;
+}
+
+int cuda_check(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return SC_OK;
+}
+
+bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int write_points(const std::vector<std::array<int64_t, 6>>& rects, int64_t* xyz, int64_t cap,
+                 int64_t* n) {
+  int64_t k = 0;
+  for (const auto& r : rects)
+    for (int64_t z = r[2]; z < r[5]; ++z)
+      for (int64_t y = r[1]; y < r[4]; ++y)
+        for (int64_t x = r[0]; x < r[3]; ++x, ++k)
+          if (xyz && k < cap) {
+            xyz[3 * k] = x;
+            xyz[3 * k + 1] = y;
+            xyz[3 * k + 2] = z;
+          }
+  *n = k;
+  return SC_OK;
+}
+
+}  // namespace
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+int sc_hierarchy_create(sc_level* coarse, sc_level* fine, int32_t ratio, int32_t buffer,
+                        sc_hierarchy** out) {
+  if (!coarse || !fine || !out) return set_error(SC_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (ratio != 2) return set_error(SC_EINVAL, "hierarchy: refinement ratio must be 2");
+  if (buffer < 4) return set_error(SC_EINVAL, "hierarchy: buffer must be >= 4");
+  if (coarse->doms.size() != 1 || fine->doms.size() != 1)
+    return set_error(SC_EINVAL, "hierarchy: each level must have exactly one domain");
+  const sc_domain& CD = coarse->doms[0];
+  const sc_domain& FD = fine->doms[0];
+  if (CD.periodic != 7u)
+    return set_error(SC_EINVAL, "hierarchy: the coarse domain must be periodic on every axis");
+  if (FD.periodic != 0u)
+    return set_error(SC_EINVAL, "hierarchy: the fine domain must be periodic on no axis");
+  if (!(FD.h == 0.5 * CD.h))
+    return set_error(SC_EINVAL, "hierarchy: the fine spacing must be half the coarse spacing");
+  sc_hierarchy* H = new sc_hierarchy;
+  H->coarse = coarse;
+  H->fine = fine;
+  H->buffer = buffer;
+  H->R = box_of(FD.lo, FD.hi);
+  for (int d = 0; d < 3; ++d) {
+    H->T.lo[d] = FD.lo[d] + buffer;
+    H->T.hi[d] = FD.hi[d] - buffer;
+  }
+  if (H->T.empty()) {
+    delete H;
+    return set_error(SC_EINVAL, "hierarchy: the fine domain has no points beyond its buffer");
+  }
+  const int rc = build_lists(H);
+  if (rc) {
+    delete H;
+    return rc;
+  }
+  *out = H;
+  return SC_OK;
+}
+
+void sc_hierarchy_destroy(sc_hierarchy* H) {
+  if (!H) return;
+  if (H->device >= 0) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != H->device) cudaSetDevice(H->device);
+    cudaDeviceSynchronize();
+    cudaFree(H->d_prol);
+    cudaFree(H->d_prol_chunks);
+    cudaFree(H->d_restr);
+    cudaFree(H->d_restr_chunks);
+    if (cur != H->device && cur >= 0) cudaSetDevice(cur);
+  }
+  delete H;
+}
+
+int sc_hierarchy_counts(const sc_hierarchy* H, int64_t* n_prolong, int64_t* n_restrict) {
+  if (!H || !n_prolong || !n_restrict) return set_error(SC_EINVAL, "NULL argument");
+  *n_prolong = H->n_prol;
+  *n_restrict = H->n_restr;
+  return SC_OK;
+}
+
+int sc_hierarchy_prolongation_points(const sc_hierarchy* H, int64_t* xyz, int64_t cap,
+                                     int64_t* n) {
+  if (!H || !n) return set_error(SC_EINVAL, "NULL argument");
+  return write_points(H->prol_rects, xyz, cap, n);
+}
+
+int sc_hierarchy_restriction_points(const sc_hierarchy* H, int64_t* xyz, int64_t cap,
+                                    int64_t* n) {
+  if (!H || !n) return set_error(SC_EINVAL, "NULL argument");
+  return write_points(H->restr_rects, xyz, cap, n);
+}
+
+int sc_hierarchy_prolongate(sc_hierarchy* H, const double* u0, const double* u1, const double* p0,
+                            const double* p1, double alpha, double* fu, double* fpi,
+                            void* stream) {
+  if (!H) return set_error(SC_EINVAL, "NULL hierarchy");
+  if (!aligned16(u0) || !aligned16(u1) || !aligned16(p0) || !aligned16(p1) || !aligned16(fu) ||
+      !aligned16(fpi))
+    return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
+  int rc = ensure_uploaded(H);
+  if (rc) return rc;
+  dev::launch_prolong(H->d_prol, H->d_prol_chunks, (int)H->prol_chunks.size(), u0, u1, p0, p1,
+                      alpha, fu, fpi, (cudaStream_t)stream);
+  H->fine->launches++;
+  return cuda_check("prolongation");
+}
+
+int sc_hierarchy_restrict(sc_hierarchy* H, const double* fu, const double* fpi, double* cu,
+                          double* cpi, void* stream) {
+  if (!H) return set_error(SC_EINVAL, "NULL hierarchy");
+  if (!aligned16(fu) || !aligned16(fpi) || !aligned16(cu) || !aligned16(cpi))
+    return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
+  int rc = ensure_uploaded(H);
+  if (rc) return rc;
+  dev::launch_restrict(H->d_restr, H->d_restr_chunks, (int)H->restr_chunks.size(), fu, fpi, cu,
+                       cpi, (cudaStream_t)stream);
+  H->coarse->launches++;
+  return cuda_check("restriction");
+}
+
+int sc_hierarchy_step(sc_hierarchy* H, double* cu, double* cpi, const double* cc2, double* fu,
+                      double* fpi, const double* fc2, double dt, int32_t nsteps, int32_t mode,
+                      void* stream) {
+  if (!H) return set_error(SC_EINVAL, "NULL hierarchy");
+  if (nsteps < 0 || !(dt >= 0.0)) return set_error(SC_EINVAL, "nsteps < 0 or dt < 0");
+  int rc = ensure_uploaded(H);
+  if (rc) return rc;
+  if ((rc = ensure_device(H->coarse))) return rc;
+  double *ou, *op;
+  if ((rc = get_field(H->coarse, "hier.old.u", &ou)) ||
+      (rc = get_field(H->coarse, "hier.old.pi", &op)))
+    return rc;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)H->coarse->field_size;
+  const double dtf = 0.5 * dt;
+  for (int n = 0; n < nsteps; ++n) {
+    // the coarse level at t, then one coarse step to t + dt
+    if (cudaMemcpyAsync(ou, cu, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(op, cpi, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return cuda_check("hierarchy: copy of the coarse level");
+    if ((rc = sc_level_rk4_step(H->coarse, cu, cpi, cc2, &dt, 1, 1, mode, stream))) return rc;
+    // two fine steps of dt/2, boundary data at t and t + dt/2
+    for (int k = 0; k < 2; ++k) {
+      if ((rc = sc_hierarchy_prolongate(H, ou, cu, op, cpi, 0.5 * k, fu, fpi, stream)))
+        return rc;
+      if ((rc = sc_level_rk4_step(H->fine, fu, fpi, fc2, &dtf, 1, 1, mode, stream))) return rc;
+    }
+    if ((rc = sc_hierarchy_restrict(H, fu, fpi, cu, cpi, stream))) return rc;
+  }
+  return SC_OK;
+}
+
+}  // extern "C"

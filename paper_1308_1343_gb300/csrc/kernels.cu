@@ -590,6 +590,93 @@ __global__ void __launch_bounds__(kGatherChunk) adj_combine_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Two-level hierarchy: prolongation and restriction
+// ---------------------------------------------------------------------------
+//
+// Prolongation: cubic Lagrange interpolation along each axis as a tensor
+// product (weights (-1, 9, 9, -1)/16 at odd fine indices, injection at even
+// ones), of data interpolated linearly in time, (1 - alpha) old + alpha new,
+// per coarse point.  The products and sums are rounded one by one (no FMA
+// contraction) and summed z outermost, then y, then x.  One fine point per
+// thread, both fields.
+
+__device__ __forceinline__ void prol_axis(int f, int& c0, int& n, double* w) {
+  if ((f & 1) == 0) {
+    c0 = f >> 1;
+    n = 1;
+    w[0] = 1.0;
+  } else {
+    c0 = ((f - 1) >> 1) - 1;
+    n = 4;
+    w[0] = -0.0625;
+    w[1] = 0.5625;
+    w[2] = 0.5625;
+    w[3] = -0.0625;
+  }
+}
+
+__global__ void __launch_bounds__(kGatherChunk) prolong_kernel(
+    const DProl* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
+    const double* __restrict__ u0, const double* __restrict__ u1,
+    const double* __restrict__ p0, const double* __restrict__ p1, double alpha,
+    double* __restrict__ fu, double* __restrict__ fp) {
+  const double beta = 1.0 - alpha;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const DChunk ch = chunks[c];
+    const DProl r = rects[ch.rect];
+    const int p = ch.first + (int)threadIdx.x;
+    if (p >= r.ex * r.ey * r.ez) continue;
+    const int t = p / r.ex;
+    const int x = p - t * r.ex;
+    const int z = t / r.ey;
+    const int y = t - z * r.ey;
+    int cx, cy, cz, nx, ny, nz;
+    double wx[4], wy[4], wz[4];
+    prol_axis(r.fx0 + x, cx, nx, wx);
+    prol_axis(r.fy0 + y, cy, ny, wy);
+    prol_axis(r.fz0 + z, cz, nz, wz);
+    double su = 0.0, sp = 0.0;
+    for (int a = 0; a < nz; ++a)
+      for (int b = 0; b < ny; ++b) {
+        const double wzy = __dmul_rn(wz[a], wy[b]);
+        const long long row = r.cbase + (long long)(cz + a) * r.cpz + (long long)(cy + b) * r.cpy;
+        for (int e = 0; e < nx; ++e) {
+          const double w = __dmul_rn(wzy, wx[e]);
+          const long long i = row + cx + e;
+          const double du = __dadd_rn(__dmul_rn(beta, u0[i]), __dmul_rn(alpha, u1[i]));
+          const double dp = __dadd_rn(__dmul_rn(beta, p0[i]), __dmul_rn(alpha, p1[i]));
+          su = __dadd_rn(su, __dmul_rn(w, du));
+          sp = __dadd_rn(sp, __dmul_rn(w, dp));
+        }
+      }
+    const long long o = r.dst + x + (long long)y * r.dpy + (long long)z * r.dpz;
+    fu[o] = su;
+    fp[o] = sp;
+  }
+}
+
+// Restriction by injection: coarse point c takes the fine value at 2c.
+__global__ void __launch_bounds__(kGatherChunk) restrict_kernel(
+    const DRestr* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
+    const double* __restrict__ fu, const double* __restrict__ fp, double* __restrict__ cu,
+    double* __restrict__ cp) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const DChunk ch = chunks[c];
+    const DRestr r = rects[ch.rect];
+    const int p = ch.first + (int)threadIdx.x;
+    if (p >= r.ex * r.ey * r.ez) continue;
+    const int t = p / r.ex;
+    const int x = p - t * r.ex;
+    const int z = t / r.ey;
+    const int y = t - z * r.ey;
+    const long long d = r.dst + x + (long long)y * r.dpy + (long long)z * r.dpz;
+    const long long s = r.src + 2ll * x + 2ll * y * r.spy + 2ll * z * r.spz;
+    cu[d] = fu[s];
+    cp[d] = fp[s];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 
@@ -768,6 +855,24 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {
                                                          pair_kernel<FixedI, true, true>, NT, 0);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
                                                        pair_kernel<Fp64, true, true>, NT, 0);
+}
+
+cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks,
+                           const double* u0, const double* u1, const double* p0,
+                           const double* p1, double alpha, double* fu, double* fp,
+                           cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  prolong_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, u0, u1, p0, p1, alpha,
+                                                  fu, fp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchunks,
+                            const double* fu, const double* fp, double* cu, double* cp,
+                            cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  restrict_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, fu, fp, cu, cp);
+  return cudaGetLastError();
 }
 
 int stage_threads() { return NT; }

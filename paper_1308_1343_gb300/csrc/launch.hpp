@@ -11,6 +11,8 @@ struct DItem;
 struct DRect;
 struct DChunk;
 struct DPush;
+struct DProl;
+struct DRestr;
 
 // Per (stage, domain) coefficients of the nested RK4 form.
 struct StageCoef {
@@ -154,6 +156,13 @@ cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks
 cudaError_t launch_adj2(bool second, int arith, const Adj2Args& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chunks,
                                int nchunks, const AdjCombineArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks,
+                           const double* u0, const double* u1, const double* p0,
+                           const double* p1, double alpha, double* fu, double* fp,
+                           cudaStream_t s);
+cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchunks,
+                            const double* fu, const double* fp, double* cu, double* cp,
+                            cudaStream_t s);
 int stage_threads();
 cudaError_t stage_occupancy(int arith, int* blocks_per_sm);
 

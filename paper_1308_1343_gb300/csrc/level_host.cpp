@@ -387,6 +387,16 @@ int sc_bboxset_expand_shift(const int64_t* a, int64_t na, const int64_t lo_by[3]
   return write_boxes(A.expanded(lo_by, hi_by).shifted(v), out, cap, n);
 }
 
+int sc_bboxset_coarsen(const int64_t* a, int64_t na, int64_t ratio, int64_t* out, int64_t cap,
+                       int64_t* n) {
+  if (!n) return set_error(SC_EINVAL, "NULL argument");
+  if (ratio < 1) return set_error(SC_EINVAL, "ratio must be >= 1");
+  BBoxSet3 A;
+  int rc = read_set(a, na, &A);
+  if (rc) return rc;
+  return write_boxes(coarsened(A, ratio), out, cap, n);
+}
+
 int sc_bboxset_size(const int64_t* a, int64_t na, int64_t* npoints) {
   if (!npoints) return set_error(SC_EINVAL, "NULL argument");
   BBoxSet3 A;

@@ -612,9 +612,17 @@ static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const doubl
   if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
   e = cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
   if (e != cudaSuccess) return e;
-  e = enq_maxexp(q, u, D->emax, false);
+  // With a non-periodic domain the boundary ghosts hold caller data that
+  // the stencils read: the bound then covers interior and ghosts, taken
+  // after an exchange has refreshed the owned ghosts.
+  const bool star = !q.L->all_periodic;
+  if (star && !q.push) {
+    e = pi ? enq_fill2(q, u, pi, nullptr) : enq_fill(q, u);
+    if (e != cudaSuccess) return e;
+  }
+  e = enq_maxexp(q, u, D->emax, star);
   if (e != cudaSuccess || !pi) return e;
-  return enq_maxexp(q, pi, D->emax + q.L->doms.size(), false);  // slot X.pi of the pair form
+  return enq_maxexp(q, pi, D->emax + q.L->doms.size(), star);  // slot X.pi of the pair form
 }
 
 // Stage scratch: Wa.u, Wa.pi, Wb.u, Wb.pi and the two pre-scaled wave speeds.
@@ -724,8 +732,10 @@ int sc_level_rk4_step(sc_level* L, double* u, double* pi, const double* c2, cons
   if (mode != SC_MODE_GRAPH && mode != SC_MODE_PER_BOX && mode != SC_MODE_BATCHED &&
       mode != SC_MODE_TIMED)
     return set_error(SC_EINVAL, "unknown mode");
-  if (!L->all_periodic)
-    return set_error(SC_EINVAL, "rk4_step needs domains periodic on every axis");
+  if (!L->all_periodic && nsteps > 1)
+    return set_error(SC_EINVAL,
+                     "a level with a non-periodic domain takes one step per call (its "
+                     "boundary ghosts are refreshed between steps)");
   int rc = ensure_device(L);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;

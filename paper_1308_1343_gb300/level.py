@@ -320,3 +320,62 @@ def wave_rk4(level: Level, u0, pi0, c2, dt, nsteps: int, ckpt_every: int = 20):
             return g_u0, g_pi0, g_c2
 
     return WaveRK4.apply(u0, pi0, c2)
+
+
+class Hierarchy:
+    """Two-level refinement hierarchy over a coarse periodic level and a fine
+    level of half the spacing (see include/sc_hierarchy.h)."""
+
+    def __init__(self, coarse: Level, fine: Level, ratio: int = 2, buffer: int = 4):
+        h = ctypes.c_void_p()
+        B.check(B.lib().sc_hierarchy_create(coarse.handle, fine.handle, int(ratio), int(buffer),
+                                            ctypes.byref(h)))
+        self._h = h
+        self.coarse, self.fine, self.buffer = coarse, fine, int(buffer)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.lib().sc_hierarchy_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def counts(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        B.check(B.lib().sc_hierarchy_counts(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def _points(self, fn) -> np.ndarray:
+        n = ctypes.c_int64()
+        B.check(fn(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 3), dtype=np.int64)
+        B.check(fn(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n.value,
+                   ctypes.byref(n)))
+        return out[:n.value]
+
+    def prolongation_points(self) -> np.ndarray:
+        """Fine (x, y, z) points that prolongation fills."""
+        return self._points(B.lib().sc_hierarchy_prolongation_points)
+
+    def restriction_points(self) -> np.ndarray:
+        """Coarse (x, y, z) points that restriction sets."""
+        return self._points(B.lib().sc_hierarchy_restriction_points)
+
+    def prolongate(self, u0, u1, p0, p1, alpha: float, fu, fpi, stream=None):
+        B.check(B.lib().sc_hierarchy_prolongate(self._h, _ptr(u0), _ptr(u1), _ptr(p0), _ptr(p1),
+                                                float(alpha), _ptr(fu), _ptr(fpi),
+                                                _stream(stream)))
+
+    def restrict(self, fu, fpi, cu, cpi, stream=None):
+        B.check(B.lib().sc_hierarchy_restrict(self._h, _ptr(fu), _ptr(fpi), _ptr(cu), _ptr(cpi),
+                                              _stream(stream)))
+
+    def step(self, cu, cpi, cc2, fu, fpi, fc2, dt: float, nsteps: int,
+             mode: int = B.SC_MODE_GRAPH, stream=None):
+        B.check(B.lib().sc_hierarchy_step(self._h, _ptr(cu), _ptr(cpi), _ptr(cc2), _ptr(fu),
+                                          _ptr(fpi), _ptr(fc2), float(dt), int(nsteps), int(mode),
+                                          _stream(stream)))

@@ -180,6 +180,18 @@ def ensemble(count: int = 256, seed: int = 5, edges=tuple(range(24, 97, 8))) -> 
     return out
 
 
+def refined_pair(n: int, seed: int, r_lo, r_hi, width: float = 0.05) -> Instance:
+    """Inputs of a two-level hierarchy on the unit periodic cube: the fine grid
+    (2n)^3 (spacing 1/(2n)) carries seed's bumpy wave speed and a Gaussian
+    pulse of the given width centred in the refined region [r_lo, r_hi)
+    (fine indices).  The coarse level's fields are these fields at even
+    fine indices, the points the two grids share."""
+    fine = bumpy_instance(Domain((2 * n,) * 3, 0.5 / n), seed)
+    centre = [(r_lo[d] + r_hi[d] - 1) * 0.5 * fine.dom.h for d in range(3)]
+    fine.u = np.ascontiguousarray(gaussian(fine.dom, centre, width))
+    return fine
+
+
 def random_direction(shape, seed: int) -> np.ndarray:
     """N(0,1) per point, scaled to unit RMS."""
     d = np.random.default_rng(seed).normal(size=shape)
