@@ -306,6 +306,10 @@ def _extras(torch, W, B, Level, arith, stream):
     del lev, u, pi, c2
     torch.cuda.empty_cache()
 
+    # two-level hierarchy: coarse 256^3 periodic, fine region 256^3 points
+    # (the central eighth of the domain at half the spacing), 20 steps
+    out["two_level"] = _two_level(torch, W, B, Level, arith, stream)
+
     # adjoint / forward ratio on the 128^3, 200-step differentiation workload
     inst = W.gradient_problem(128, 4)
     lev = Level.from_instances([inst])
@@ -353,6 +357,53 @@ def _extras(torch, W, B, Level, arith, stream):
                       "ratio_total_over_forward": (t2 - t0) / t_fwd,
                       "backward_kernels": kern}
     return out
+
+
+def _two_level(torch, W, B, Level, arith, stream):
+    """Berger-Oliger steps of a two-level hierarchy; updates count both levels
+    (coarse points once, fine points twice per step)."""
+    from paper_1308_1343_gb300.level import Hierarchy
+    n = 256
+    lo, hi = (n // 2,) * 3, (3 * n // 2,) * 3
+    coarse, (fu_h, fp_h, fc_h) = W.refined_fields(n, 7, lo, hi)
+    c = Level.from_instances([coarse])
+    f = Level([(lo, hi, 0)], [dict(lo=lo, hi=hi, h=0.5 / n, periodic=0)])
+    for lev in (c, f):
+        lev.set_arith(arith)
+        lev.autotune(seed=6, budget_ms=2000.0, abort_factor=2.0, cache_path=TUNE_CACHE,
+                     stream=stream)
+    h = Hierarchy(c, f)
+    cu, cp = c.to_device([coarse.u]), c.to_device([coarse.pi])
+    cc = c.to_device([coarse.c2], fill=1.0)
+    fu, fp, fc = f.to_device([fu_h]), f.to_device([fp_h]), f.to_device([fc_h], fill=1.0)
+    nsteps = 20
+    h.step(cu, cp, cc, fu, fp, fc, coarse.dt, 2, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.step(cu, cp, cc, fu, fp, fc, coarse.dt, nsteps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    c.sync(stream)
+    f.sync(stream)
+    t = e0.elapsed_time(e1) / 1e3
+    nc, nf = coarse.u.size, fu_h.size
+    npro, nres = h.counts()
+    # the levels alone, for the split of the time
+    tc = _time_steps(torch, c, cu, cp, cc, coarse.dt, nsteps, B.SC_MODE_GRAPH, 1, stream)
+    tf = 0.0
+    for _ in range(2 * nsteps):
+        tf += _time_steps(torch, f, fu, fp, fc, 0.5 * coarse.dt, 1, B.SC_MODE_GRAPH, 1, stream)
+    h.close()
+    return {"workload": "periodic 256^3 coarse level (h = 1/256) + fine region of 256^3 points "
+                        "(h = 1/512, the central eighth), buffer 4, 20 Berger-Oliger steps",
+            "coarse_points": nc, "fine_points": nf, "prolongated_points_per_fine_step": npro,
+            "restricted_points_per_step": nres,
+            "stages_per_pass": [c.get_fusion(), f.get_fusion()],
+            "updates_per_s": (nc + 2 * nf) * nsteps / t, "ms_per_step": 1e3 * t / nsteps,
+            "coarse_level_alone_ms_per_step": 1e3 * tc / nsteps,
+            "fine_level_alone_ms_per_two_steps": 1e3 * tf / nsteps}
 
 
 def run_ours(a, ws, rank, local):

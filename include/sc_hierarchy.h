@@ -83,7 +83,8 @@ int sc_hierarchy_restrict(sc_hierarchy* hierarchy, const double* fu, const doubl
 /* nsteps hierarchy steps of dt (see the top of this header) on the coarse
  * fields (cu, cpi, cc2) and the fine fields (fu, fpi, fc2), in place.  mode
  * is the levels' launch mode (SC_MODE_*).  c2 ghosts need not be filled.
- * Library-owned scratch: two coarse fields (the coarse level at t). */
+ * Library-owned scratch: four coarse fields (the coarse level at t and its
+ * time interpolation, written only where prolongation reads them). */
 int sc_hierarchy_step(sc_hierarchy* hierarchy, double* cu, double* cpi, const double* cc2,
                       double* fu, double* fpi, const double* fc2, double dt, int32_t nsteps,
                       int32_t mode, void* stream);

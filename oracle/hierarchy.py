@@ -68,14 +68,16 @@ def prolongate(c_old, c_new, alpha: float, fpts) -> np.ndarray:
     fpts = np.asarray(fpts, dtype=np.int64).reshape(-1, 3)
 
     def axis(f):
-        idx = np.empty((len(f), 4), dtype=np.int64)
-        w = np.zeros((len(f), 4))
-        for n, fv in enumerate(f):
+        # stencil_1d of every distinct coordinate, mapped back to the points
+        vals, inv = np.unique(f, return_inverse=True)
+        idx = np.empty((len(vals), 4), dtype=np.int64)
+        w = np.zeros((len(vals), 4))
+        for n, fv in enumerate(vals):
             ci, wi = stencil_1d(int(fv))
             idx[n, :] = ci[0]
             idx[n, :len(ci)] = ci
             w[n, :len(wi)] = wi
-        return idx, w
+        return idx[inv], w[inv]
 
     (ix, wx), (iy, wy), (iz, wz) = axis(fpts[:, 0]), axis(fpts[:, 1]), axis(fpts[:, 2])
     data = (1.0 - alpha) * c_old + alpha * c_new

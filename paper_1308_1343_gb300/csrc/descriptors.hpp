@@ -35,13 +35,14 @@ struct DRect {
   int x0, y0, z0;            // interior coordinates of the first point
 };
 
-// A rectangle of fine points that prolongation fills (interior points of
-// one fine box, or ghost points of its shell), all drawing on the interior
-// of one coarse box.
+// A set of fine points that prolongation fills (interior points of one fine
+// box, or ghost points of its shell), all of one index parity per axis (so
+// spaced 2 apart along every axis) and all drawing on the interior of one
+// coarse box.
 struct DProl {
   long long dst;       // fine element index of the first point
   int dpy, dpz;        // fine box pitches
-  int ex, ey, ez;      // extent
+  int ex, ey, ez;      // number of points per axis (stride 2)
   int fx0, fy0, fz0;   // fine level index of the first point
   long long cbase;     // coarse element index of coarse level index (0, 0, 0)
                        // in the coarse box's layout (may lie outside the box)

@@ -4,6 +4,7 @@
 // step.  The readings (operators, buffer zone, sub-cycling) are stated in
 // include/sc_hierarchy.h.
 #include <algorithm>
+#include <cstdint>
 #include <array>
 #include <string>
 #include <vector>
@@ -22,6 +23,10 @@ struct sc_hierarchy {
   BBox3 R, T;
   std::vector<sc::dev::DProl> prol;
   std::vector<sc::dev::DChunk> prol_chunks;
+  // per coarse box, the bounding box of the prolongation stencils' coarse
+  // points: where time interpolation is needed
+  std::vector<sc::dev::DRect> blend;
+  std::vector<sc::dev::DChunk> blend_chunks;
   std::vector<sc::dev::DRestr> restr;
   std::vector<sc::dev::DChunk> restr_chunks;
   // each list's rectangles in level coordinates (lo, hi), for the queries
@@ -30,6 +35,8 @@ struct sc_hierarchy {
   // device copies (on the coarse level's device)
   sc::dev::DProl* d_prol = nullptr;
   sc::dev::DChunk* d_prol_chunks = nullptr;
+  sc::dev::DRect* d_blend = nullptr;
+  sc::dev::DChunk* d_blend_chunks = nullptr;
   sc::dev::DRestr* d_restr = nullptr;
   sc::dev::DChunk* d_restr_chunks = nullptr;
   int device = -1;
@@ -79,9 +86,14 @@ BBox3 safe_fine(const sc_box& cb) {
   return r;
 }
 
-void add_chunks(int rect, int64_t n, std::vector<dev::DChunk>& out) {
-  for (int64_t f = 0; f < n; f += dev::kGatherChunk) out.push_back(dev::DChunk{rect, (int)f});
+void add_chunks(int rect, int64_t n, std::vector<dev::DChunk>& out,
+                int chunk = dev::kGatherChunk) {
+  for (int64_t f = 0; f < n; f += chunk) out.push_back(dev::DChunk{rect, (int)f});
 }
+
+// First coarse index of fine index f's stencil, and one past its last.
+int64_t stencil_lo(int64_t f) { return (f & 1) ? (f - 3) / 2 : f / 2; }
+int64_t stencil_hi(int64_t f) { return (f & 1) ? (f + 3) / 2 + 1 : f / 2 + 1; }
 
 template <class T>
 int upload(T** dst, const std::vector<T>& v) {
@@ -101,6 +113,12 @@ int build_lists(sc_hierarchy* H) {
   const sc_level* C = H->coarse;
   const sc_level* F = H->fine;
   const BBoxSet3 Rs = BBoxSet3::box(H->R), Ts = BBoxSet3::box(H->T);
+  std::vector<BBox3> foot(C->boxes.size());  // stencil footprint per coarse box
+  for (auto& b : foot)
+    for (int d = 0; d < 3; ++d) {
+      b.lo[d] = INT64_MAX;
+      b.hi[d] = INT64_MIN;
+    }
   // prolongation: per fine box, its buffer-band points and its shell points
   // outside R, assigned to the first coarse box whose interior holds their
   // stencils
@@ -116,24 +134,41 @@ int build_lists(sc_hierarchy* H) {
       const long long cbase = (long long)(C->off[cb] - CB.lo[0] - CB.lo[1] * C->py[cb] -
                                           CB.lo[2] * C->pz[cb]);
       for (const BBox3& r : part.boxes()) {
-        dev::DProl p{};
-        p.dst = elem(F, (int)fb, r.lo.data());
-        p.dpy = (int)F->py[fb];
-        p.dpz = (int)F->pz[fb];
-        p.ex = (int)(r.hi[0] - r.lo[0]);
-        p.ey = (int)(r.hi[1] - r.lo[1]);
-        p.ez = (int)(r.hi[2] - r.lo[2]);
-        p.fx0 = (int)r.lo[0];
-        p.fy0 = (int)r.lo[1];
-        p.fz0 = (int)r.lo[2];
-        p.cbase = cbase;
-        p.cpy = (int)C->py[cb];
-        p.cpz = (int)C->pz[cb];
-        H->prol.push_back(p);
         H->prol_rects.push_back({r.lo[0], r.lo[1], r.lo[2], r.hi[0], r.hi[1], r.hi[2]});
-        const int64_t n = (int64_t)p.ex * p.ey * p.ez;
-        add_chunks((int)H->prol.size() - 1, n, H->prol_chunks);
-        H->n_prol += n;
+        H->n_prol += r.size();
+        for (int d = 0; d < 3; ++d) {
+          foot[cb].lo[d] = std::min(foot[cb].lo[d], stencil_lo(r.lo[d]));
+          foot[cb].hi[d] = std::max(foot[cb].hi[d], stencil_hi(r.hi[d] - 1));
+          if (r.hi[d] - r.lo[d] > 1) {
+            foot[cb].lo[d] = std::min(foot[cb].lo[d], stencil_lo(r.lo[d] + 1));
+            foot[cb].hi[d] = std::max(foot[cb].hi[d], stencil_hi(r.hi[d] - 2));
+          }
+        }
+        // one entry per parity class: points 2 apart along every axis
+        for (int k = 0; k < 8; ++k) {
+          int64_t s0[3];
+          int e[3];
+          for (int d = 0; d < 3; ++d) {
+            s0[d] = r.lo[d] + ((k >> d) & 1);
+            e[d] = s0[d] < r.hi[d] ? (int)((r.hi[d] - s0[d] + 1) / 2) : 0;
+          }
+          if (!e[0] || !e[1] || !e[2]) continue;
+          dev::DProl p{};
+          p.dst = elem(F, (int)fb, s0);
+          p.dpy = (int)F->py[fb];
+          p.dpz = (int)F->pz[fb];
+          p.ex = e[0];
+          p.ey = e[1];
+          p.ez = e[2];
+          p.fx0 = (int)s0[0];
+          p.fy0 = (int)s0[1];
+          p.fz0 = (int)s0[2];
+          p.cbase = cbase;
+          p.cpy = (int)C->py[cb];
+          p.cpz = (int)C->pz[cb];
+          H->prol.push_back(p);
+          add_chunks((int)H->prol.size() - 1, (int64_t)e[0] * e[1] * e[2], H->prol_chunks);
+        }
       }
     }
     if (!todo.empty())
@@ -141,6 +176,19 @@ int build_lists(sc_hierarchy* H) {
                                       std::to_string(fb) +
                                       " lies in no coarse box interior (keep the fine "
                                       "region 3 coarse points away from coarse box faces)");
+  }
+  for (size_t cb = 0; cb < C->boxes.size(); ++cb) {
+    if (foot[cb].lo[0] == INT64_MAX) continue;
+    dev::DRect r{};
+    r.src = r.dst = elem(C, (int)cb, foot[cb].lo.data());
+    r.spy = r.dpy = C->py[cb];
+    r.spz = r.dpz = C->pz[cb];
+    r.ex = (int)(foot[cb].hi[0] - foot[cb].lo[0]);
+    r.ey = (int)(foot[cb].hi[1] - foot[cb].lo[1]);
+    r.ez = (int)(foot[cb].hi[2] - foot[cb].lo[2]);
+    H->blend.push_back(r);
+    add_chunks((int)H->blend.size() - 1, (int64_t)r.ex * r.ey * r.ez, H->blend_chunks,
+               dev::kChunk);
   }
   // restriction: coarse points c with 2c in T, per (coarse box, fine box)
   for (size_t cb = 0; cb < C->boxes.size(); ++cb) {
@@ -179,6 +227,7 @@ int ensure_uploaded(sc_hierarchy* H) {
   if (H->device >= 0) return set_error(SC_EINVAL, "hierarchy was set up on another device");
   int rc;
   if ((rc = upload(&H->d_prol, H->prol)) || (rc = upload(&H->d_prol_chunks, H->prol_chunks)) ||
+      (rc = upload(&H->d_blend, H->blend)) || (rc = upload(&H->d_blend_chunks, H->blend_chunks)) ||
       (rc = upload(&H->d_restr, H->restr)) ||
       (rc = upload(&H->d_restr_chunks, H->restr_chunks)))
     return rc;
@@ -264,6 +313,8 @@ void sc_hierarchy_destroy(sc_hierarchy* H) {
     cudaDeviceSynchronize();
     cudaFree(H->d_prol);
     cudaFree(H->d_prol_chunks);
+    cudaFree(H->d_blend);
+    cudaFree(H->d_blend_chunks);
     cudaFree(H->d_restr);
     cudaFree(H->d_restr_chunks);
     if (cur != H->device && cur >= 0) cudaSetDevice(cur);
@@ -299,8 +350,23 @@ int sc_hierarchy_prolongate(sc_hierarchy* H, const double* u0, const double* u1,
     return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
   int rc = ensure_uploaded(H);
   if (rc) return rc;
-  dev::launch_prolong(H->d_prol, H->d_prol_chunks, (int)H->prol_chunks.size(), u0, u1, p0, p1,
-                      alpha, fu, fpi, (cudaStream_t)stream);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const double* du = u0;
+  const double* dp = p0;
+  if (alpha != 0.0) {
+    // the coarse data at t + alpha dt, once per point of the stencils' reach
+    double *bu, *bp;
+    if ((rc = ensure_device(H->coarse)) || (rc = get_field(H->coarse, "hier.blend.u", &bu)) ||
+        (rc = get_field(H->coarse, "hier.blend.pi", &bp)))
+      return rc;
+    dev::launch_blend(H->d_blend, H->d_blend_chunks, (int)H->blend_chunks.size(), u0, u1, p0,
+                      p1, alpha, bu, bp, H->coarse->dev->grid_small, s);
+    H->coarse->launches++;
+    du = bu;
+    dp = bp;
+  }
+  dev::launch_prolong(H->d_prol, H->d_prol_chunks, (int)H->prol_chunks.size(), du, dp, fu, fpi,
+                      s);
   H->fine->launches++;
   return cuda_check("prolongation");
 }
@@ -331,19 +397,23 @@ int sc_hierarchy_step(sc_hierarchy* H, double* cu, double* cpi, const double* cc
       (rc = get_field(H->coarse, "hier.old.pi", &op)))
     return rc;
   const cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(double) * (size_t)H->coarse->field_size;
   const double dtf = 0.5 * dt;
   for (int n = 0; n < nsteps; ++n) {
-    // the coarse level at t, then one coarse step to t + dt
-    if (cudaMemcpyAsync(ou, cu, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(op, cpi, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return cuda_check("hierarchy: copy of the coarse level");
-    if ((rc = sc_level_rk4_step(H->coarse, cu, cpi, cc2, &dt, 1, 1, mode, stream))) return rc;
+    // the coarse level at t where prolongation reads it (the blend with
+    // alpha = 0 of a field with itself is that field), then one coarse step
+    dev::launch_blend(H->d_blend, H->d_blend_chunks, (int)H->blend_chunks.size(), cu, cu, cpi,
+                      cpi, 0.0, ou, op, H->coarse->dev->grid_small, s);
+    H->coarse->launches++;
+    if ((rc = cuda_check("hierarchy: copy of the coarse level"))) return rc;
+    // c2 and dt are fixed within the call: the pre-scaled wave speeds are
+    // computed on each level's first step only
+    if ((rc = level_steps(H->coarse, cu, cpi, cc2, dt, 1, mode, s, n == 0))) return rc;
     // two fine steps of dt/2, boundary data at t and t + dt/2
     for (int k = 0; k < 2; ++k) {
       if ((rc = sc_hierarchy_prolongate(H, ou, cu, op, cpi, 0.5 * k, fu, fpi, stream)))
         return rc;
-      if ((rc = sc_level_rk4_step(H->fine, fu, fpi, fc2, &dtf, 1, 1, mode, stream))) return rc;
+      if ((rc = level_steps(H->fine, fu, fpi, fc2, dtf, 1, mode, s, n == 0 && k == 0)))
+        return rc;
     }
     if ((rc = sc_hierarchy_restrict(H, fu, fpi, cu, cpi, stream))) return rc;
   }

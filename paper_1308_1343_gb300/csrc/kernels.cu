@@ -597,30 +597,52 @@ __global__ void __launch_bounds__(kGatherChunk) adj_combine_kernel(
 // product (weights (-1, 9, 9, -1)/16 at odd fine indices, injection at even
 // ones), of data interpolated linearly in time, (1 - alpha) old + alpha new,
 // per coarse point.  The products and sums are rounded one by one (no FMA
-// contraction) and summed z outermost, then y, then x.  One fine point per
-// thread, both fields.
+// contraction) and summed z outermost, then y, then x.  Each list entry
+// holds points of one parity per axis, so a warp runs one stencil shape.
+// At alpha != 0 the time interpolation is done once per coarse point by
+// blend_kernel into scratch coarse fields (the same rounding).
 
-__device__ __forceinline__ void prol_axis(int f, int& c0, int& n, double* w) {
-  if ((f & 1) == 0) {
-    c0 = f >> 1;
-    n = 1;
-    w[0] = 1.0;
-  } else {
-    c0 = ((f - 1) >> 1) - 1;
-    n = 4;
-    w[0] = -0.0625;
-    w[1] = 0.5625;
-    w[2] = 0.5625;
-    w[3] = -0.0625;
-  }
+// Weight k of the cubic stencil along an axis of parity P (1: odd index).
+template <int P>
+__device__ __forceinline__ constexpr double prol_w(int k) {
+  return P == 0 ? 1.0 : (k == 0 || k == 3 ? -0.0625 : 0.5625);
+}
+
+// Sum of one fine point of parity (PX, PY, PZ): weights are compile-time
+// constants (their products fold), the sum order is z, y, x as above.
+template <int PX, int PY, int PZ>
+__device__ __forceinline__ void prol_point(const DProl& r, int x, int y, int z,
+                                           const double* __restrict__ du,
+                                           const double* __restrict__ dp, double* __restrict__ fu,
+                                           double* __restrict__ fp) {
+  constexpr int NX = PX ? 4 : 1, NY = PY ? 4 : 1, NZ = PZ ? 4 : 1;
+  const int fx = r.fx0 + 2 * x, fy = r.fy0 + 2 * y, fz = r.fz0 + 2 * z;
+  const int cx = PX ? ((fx - 1) >> 1) - 1 : fx >> 1;
+  const int cy = PY ? ((fy - 1) >> 1) - 1 : fy >> 1;
+  const int cz = PZ ? ((fz - 1) >> 1) - 1 : fz >> 1;
+  double su = 0.0, sp = 0.0;
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < NY; ++b) {
+      const long long row = r.cbase + (long long)(cz + a) * r.cpz + (long long)(cy + b) * r.cpy;
+#pragma unroll
+      for (int e = 0; e < NX; ++e) {
+        const double w = prol_w<PZ>(a) * prol_w<PY>(b) * prol_w<PX>(e);  // exact constants
+        const long long i = row + cx + e;
+        su = __dadd_rn(su, __dmul_rn(w, du[i]));
+        sp = __dadd_rn(sp, __dmul_rn(w, dp[i]));
+      }
+    }
+  const long long o = r.dst + 2ll * x + 2ll * y * r.dpy + 2ll * z * r.dpz;
+  fu[o] = su;
+  fp[o] = sp;
 }
 
 __global__ void __launch_bounds__(kGatherChunk) prolong_kernel(
     const DProl* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
-    const double* __restrict__ u0, const double* __restrict__ u1,
-    const double* __restrict__ p0, const double* __restrict__ p1, double alpha,
-    double* __restrict__ fu, double* __restrict__ fp) {
-  const double beta = 1.0 - alpha;
+    const double* __restrict__ du, const double* __restrict__ dp, double* __restrict__ fu,
+    double* __restrict__ fp) {
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const DChunk ch = chunks[c];
     const DProl r = rects[ch.rect];
@@ -630,28 +652,44 @@ __global__ void __launch_bounds__(kGatherChunk) prolong_kernel(
     const int x = p - t * r.ex;
     const int z = t / r.ey;
     const int y = t - z * r.ey;
-    int cx, cy, cz, nx, ny, nz;
-    double wx[4], wy[4], wz[4];
-    prol_axis(r.fx0 + x, cx, nx, wx);
-    prol_axis(r.fy0 + y, cy, ny, wy);
-    prol_axis(r.fz0 + z, cz, nz, wz);
-    double su = 0.0, sp = 0.0;
-    for (int a = 0; a < nz; ++a)
-      for (int b = 0; b < ny; ++b) {
-        const double wzy = __dmul_rn(wz[a], wy[b]);
-        const long long row = r.cbase + (long long)(cz + a) * r.cpz + (long long)(cy + b) * r.cpy;
-        for (int e = 0; e < nx; ++e) {
-          const double w = __dmul_rn(wzy, wx[e]);
-          const long long i = row + cx + e;
-          const double du = __dadd_rn(__dmul_rn(beta, u0[i]), __dmul_rn(alpha, u1[i]));
-          const double dp = __dadd_rn(__dmul_rn(beta, p0[i]), __dmul_rn(alpha, p1[i]));
-          su = __dadd_rn(su, __dmul_rn(w, du));
-          sp = __dadd_rn(sp, __dmul_rn(w, dp));
-        }
-      }
-    const long long o = r.dst + x + (long long)y * r.dpy + (long long)z * r.dpz;
-    fu[o] = su;
-    fp[o] = sp;
+    // one parity class per list entry: a uniform branch
+    switch ((r.fx0 & 1) | ((r.fy0 & 1) << 1) | ((r.fz0 & 1) << 2)) {
+      case 0: prol_point<0, 0, 0>(r, x, y, z, du, dp, fu, fp); break;
+      case 1: prol_point<1, 0, 0>(r, x, y, z, du, dp, fu, fp); break;
+      case 2: prol_point<0, 1, 0>(r, x, y, z, du, dp, fu, fp); break;
+      case 3: prol_point<1, 1, 0>(r, x, y, z, du, dp, fu, fp); break;
+      case 4: prol_point<0, 0, 1>(r, x, y, z, du, dp, fu, fp); break;
+      case 5: prol_point<1, 0, 1>(r, x, y, z, du, dp, fu, fp); break;
+      case 6: prol_point<0, 1, 1>(r, x, y, z, du, dp, fu, fp); break;
+      default: prol_point<1, 1, 1>(r, x, y, z, du, dp, fu, fp); break;
+    }
+  }
+}
+
+// out = (1 - alpha) a + alpha b on the rectangles, rounded step by step.
+__global__ void __launch_bounds__(256) blend_kernel(const DRect* __restrict__ rects,
+                                                    const DChunk* __restrict__ chunks,
+                                                    int nchunks, const double* __restrict__ a0,
+                                                    const double* __restrict__ a1,
+                                                    const double* __restrict__ b0,
+                                                    const double* __restrict__ b1, double alpha,
+                                                    double* __restrict__ ao,
+                                                    double* __restrict__ bo) {
+  const double beta = 1.0 - alpha;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const DChunk ch = chunks[c];
+    const DRect r = rects[ch.rect];
+    const int n = r.ex * r.ey * r.ez;
+    const int end = min(ch.first + kChunk, n);
+    for (int p = ch.first + threadIdx.x; p < end; p += blockDim.x) {
+      const int t = p / r.ex;
+      const int x = p - t * r.ex;
+      const int z = t / r.ey;
+      const int y = t - z * r.ey;
+      const long long i = r.src + x + (long long)y * r.spy + (long long)z * r.spz;
+      ao[i] = __dadd_rn(__dmul_rn(beta, a0[i]), __dmul_rn(alpha, a1[i]));
+      bo[i] = __dadd_rn(__dmul_rn(beta, b0[i]), __dmul_rn(alpha, b1[i]));
+    }
   }
 }
 
@@ -858,12 +896,19 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {
 }
 
 cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks,
-                           const double* u0, const double* u1, const double* p0,
-                           const double* p1, double alpha, double* fu, double* fp,
+                           const double* du, const double* dp, double* fu, double* fp,
                            cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
-  prolong_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, u0, u1, p0, p1, alpha,
-                                                  fu, fp);
+  prolong_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, du, dp, fu, fp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend(const DRect* rects, const DChunk* chunks, int nchunks, const double* a0,
+                         const double* a1, const double* b0, const double* b1, double alpha,
+                         double* ao, double* bo, int grid, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  blend_kernel<<<min(grid, nchunks), 256, 0, s>>>(rects, chunks, nchunks, a0, a1, b0, b1, alpha,
+                                                  ao, bo);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,10 @@ int get_field(sc_level* L, const std::string& name, double** p);
 int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s);
 int scratch4(sc_level* L, double* W[6]);
 int upload_items(sc_level* L);
+// nsteps RK4 steps as sc_level_rk4_step; qprep = false reuses the pre-scaled
+// wave speeds of the previous call (same c2 and dt)
+int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt, int nsteps,
+                int mode, cudaStream_t s, bool qprep);
 
 struct SizeClass {
   std::array<int64_t, 3> ext;  // interior extent rounded up to a multiple of 8

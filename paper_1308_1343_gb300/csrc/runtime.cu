@@ -372,6 +372,9 @@ struct Enq {
   // stage (best when a CUDA graph hides the launches), true = every stage
   // kernel writes the ghost copies of what it produces (fewer launches)
   bool push = false;
+  // recompute the pre-scaled wave speeds in the prologue (false: a caller
+  // that keeps c2 and dt knows they are current)
+  bool qprep = true;
 };
 
 // Event pair around one launch when timing is on.
@@ -605,10 +608,13 @@ static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const doubl
     cudaError_t e0 = enq_fill(q, u);  // ghosts of the run's first stencil input
     if (e0 != cudaSuccess) return e0;
   }
-  (*q.count)++;
-  cudaError_t e = dev::launch_qprep(D->irects, D->ichunks, D->nichunks, c2, W[4], W[5],
-                                    D->qfac, D->grid_small, q.s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (q.qprep) {
+    (*q.count)++;
+    e = dev::launch_qprep(D->irects, D->ichunks, D->nichunks, c2, W[4], W[5], D->qfac,
+                          D->grid_small, q.s);
+    if (e != cudaSuccess) return e;
+  }
   if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
   e = cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
   if (e != cudaSuccess) return e;
@@ -636,12 +642,13 @@ int scratch4(sc_level* L, double* W[6]) {
 }
 
 static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int nsteps, int mode,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool qprep = true) {
   DeviceState* D = L->dev;
   double* W[6];
   int rc = scratch4(L, W);
   if (rc) return rc;
   Enq q{L, s, &L->launches, mode == SC_MODE_PER_BOX};
+  q.qprep = qprep;
   if (mode == SC_MODE_TIMED) {
     q.timed = true;
     D->ev_used = 0;
@@ -684,6 +691,13 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     L->launches += it->second.second;
   }
   return SC_OK;
+}
+
+int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt, int nsteps,
+                int mode, cudaStream_t s, bool qprep) {
+  int rc = sc_level_rk4_step(L, u, pi, c2, &dt, 1, 0, mode, s);  // validation and set-up
+  if (rc || nsteps == 0) return rc;
+  return run_steps(L, u, pi, c2, nsteps, mode, s, qprep);
 }
 
 }  // namespace sc

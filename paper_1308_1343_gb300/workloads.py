@@ -192,6 +192,40 @@ def refined_pair(n: int, seed: int, r_lo, r_hi, width: float = 0.05) -> Instance
     return fine
 
 
+def refined_fields(n: int, seed: int, r_lo, r_hi, width: float = 0.05):
+    """The fields of refined_pair(n, seed, r_lo, r_hi, width) without the
+    whole fine grid: returns (coarse Instance on n^3, (u, pi, c2) on the fine
+    region [r_lo, r_hi) only).  Same draws and the same per-point operations
+    in the same order, so the values are refined_pair's, bit for bit."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.0, 1.0, size=(8, 3))
+    widths = rng.uniform(0.05, 0.2, size=8)
+    amps = rng.normal(0.0, 1.0, size=8)
+    hf = 0.5 / n
+    pulse = [(r_lo[d] + r_hi[d] - 1) * 0.5 * hf for d in range(3)]
+
+    def on(ix, iy, iz, h, m):
+        """Fields at integer grid indices (per axis) of spacing h, period m."""
+        def g(c, w):
+            f = []
+            for idx, cd in zip((ix, iy, iz), c):
+                d = np.abs(np.asarray(idx, dtype=np.float64) * h - cd)
+                d = np.minimum(d, m * h - d)
+                f.append(np.exp(-(d * d) / (2.0 * w * w)))
+            return f[2][:, None, None] * (f[1][None, :, None] * f[0][None, None, :])
+        s = np.zeros((len(iz), len(iy), len(ix)))
+        for k in range(8):
+            s += amps[k] * g(centres[k], widths[k])
+        return np.ascontiguousarray(g(pulse, width)), np.zeros(s.shape), 1.0 + 0.5 * np.tanh(s)
+
+    a = np.arange(n)
+    cu, cpi, cc2 = on(a, a, a, 1.0 / n, n)
+    coarse = Instance(Domain((n, n, n), 1.0 / n), cu, cpi, np.ascontiguousarray(cc2), 0.25 / n)
+    rng_ = [np.arange(r_lo[d], r_hi[d]) for d in range(3)]
+    fine = on(rng_[0], rng_[1], rng_[2], hf, 2 * n)
+    return coarse, fine
+
+
 def random_direction(shape, seed: int) -> np.ndarray:
     """N(0,1) per point, scaled to unit RMS."""
     d = np.random.default_rng(seed).normal(size=shape)

@@ -186,3 +186,39 @@ def test_non_periodic_level_takes_one_step_per_call():
     z = torch.zeros(f.field_size, dtype=torch.float64, device="cuda")
     with pytest.raises(B.ScError, match="one step per call"):
         f.rk4_step(z, z.clone(), z.clone() + 1.0, 0.01, 2)
+
+
+def test_full_size_step_vs_oracle(orc):
+    """The benchmark's configuration (coarse 256^3, fine region of 256^3
+    points, buffer 4, default launch form), one hierarchy step."""
+    import os
+    import torch
+    from oracle import hierarchy as H
+    n = 256
+    lo, hi = (n // 2,) * 3, (3 * n // 2,) * 3
+    coarse, (fu_h, fp_h, fc_h) = W.refined_fields(n, 7, lo, hi)
+    from paper_1308_1343_gb300.level import Hierarchy, Level
+    c = Level.from_instances([coarse])
+    f = Level([(lo, hi, 0)], [dict(lo=lo, hi=hi, h=0.5 / n, periodic=0)])
+    h = Hierarchy(c, f)
+    cu, cp = c.to_device([coarse.u]), c.to_device([coarse.pi])
+    cc = c.to_device([coarse.c2], fill=1.0)
+    fu, fp, fc = f.to_device([fu_h]), f.to_device([fp_h]), f.to_device([fc_h], fill=1.0)
+    h.step(cu, cp, cc, fu, fp, fc, coarse.dt, 1)
+    c.sync()
+    f.sync()
+    torch.cuda.synchronize()
+    gcu, gfu, gfp = c.gather(cu)[0], f.gather(fu)[0], f.gather(fp)[0]
+    h.close()
+
+    def pad(a):
+        return np.pad(a, 2)  # ghosts: filled by prolongation before use
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        ou, op, fu_p, fp_p = H.bo_step(coarse.u, coarse.pi, coarse.c2, 1.0 / n, coarse.dt,
+                                       pad(fu_h), pad(fp_h), pad(fc_h), lo, hi, 4)
+    finally:
+        orc.set_threads(1)
+    assert rel_err(gcu, ou) <= TOL
+    assert _t_err(gfu, fu_p[2:-2, 2:-2, 2:-2]) <= TOL
+    assert _t_err(gfp, fp_p[2:-2, 2:-2, 2:-2]) <= TOL

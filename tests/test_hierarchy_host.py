@@ -143,3 +143,17 @@ def test_coarse_level_of_several_boxes(B):
     c2, f2 = _levels(n, lo2, hi2, coarse_boxes=cb)
     with pytest.raises(B.ScError, match="no coarse box interior"):
         Hierarchy(c2, f2)
+
+
+def test_region_fields_equal_the_whole_fine_grid():
+    """The benchmark's inputs, evaluated only on the coarse grid and the fine
+    region, are the whole fine grid's values there, bit for bit."""
+    from paper_1308_1343_gb300 import workloads as W
+    n, lo, hi = 16, (5, 7, 6), (25, 23, 27)
+    fine = W.refined_pair(n, 9, lo, hi)
+    coarse, (u, pi, c2) = W.refined_fields(n, 9, lo, hi)
+    sub = (slice(None, None, 2),) * 3
+    reg = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    assert np.array_equal(fine.u[reg], u) and np.array_equal(fine.c2[reg], c2)
+    assert np.array_equal(fine.u[sub], coarse.u) and np.array_equal(fine.c2[sub], coarse.c2)
+    assert not np.any(pi) and not np.any(coarse.pi)
