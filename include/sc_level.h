@@ -227,13 +227,13 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
  * mode is one of SC_MODE_*.  Scratch stage arrays are allocated on the first
  * call.
  * A level with a domain that is not periodic on every axis takes ONE step
- * per call (SC_EINVAL for nsteps > 1): the caller writes boundary data into
- * the ghosts of u and pi that no box owns before each call, and they are held
- * over the step (ghosts of these points are filled by the exchange; every
- * star ghost value of u and pi must be finite).  Later stages see zeros in
- * those ghosts, so after the step the interior points within 4 of such a
- * face are boundary-influenced and the rest equal the exact step's (the
- * refinement hierarchy's buffer zone, include/sc_hierarchy.h). */
+ * per call (SC_EINVAL for nsteps > 1).  Before each call the caller writes
+ * boundary data into the ghosts of u and pi that no box owns; they are held
+ * over the step.  Ghosts that a box owns are filled by the exchange, and
+ * every star ghost value of u and pi must be finite.  Later stages see zeros
+ * in the unowned ghosts, so after the step the interior points within 4 of
+ * such a face are boundary-influenced and the rest equal the exact step's
+ * (the refinement hierarchy's buffer zone, include/sc_hierarchy.h). */
 int sc_level_rk4_step(sc_level* level, double* u, double* pi, const double* c2,
                       const double* dt, int32_t ndt, int32_t nsteps, int32_t mode,
                       void* stream);
