@@ -181,3 +181,32 @@ def test_gradient_on_uneven_level(orc, arith, fuse):
     assert rel_err(res[0][0], ou) <= 1e-10
     assert rel_err(res[0][1], op) <= 1e-10
     assert rel_err(res[0][2], oc) <= 1e-10
+
+
+@pytest.mark.parametrize("fuse", [1, 2])
+def test_gradient_of_an_ensemble(orc, fuse):
+    """One level of several periodic domains with their own sizes, wave
+    speeds, seeds and step sizes (the ensemble workload's structure): every
+    instance's gradient matches the oracle's."""
+    import torch
+    insts = [W.bumpy_instance(W.Domain((n, n, n), 1.0 / n), 5000 + i)
+             for i, n in enumerate((24, 32, 16, 40))]
+    nsteps, ckpt = 7, 3
+    lev = make_level(insts)
+    lev.set_arith(1)
+    lev.set_fusion(fuse)
+    up = lambda arrs, fill=0.0: upload(lev, arrs, fill)
+    seeds_u = [W.random_direction(i.dom.shape, 60 + k) for k, i in enumerate(insts)]
+    seeds_p = [W.random_direction(i.dom.shape, 70 + k) for k, i in enumerate(insts)]
+    g = [torch.empty(lev.field_size, dtype=torch.float64, device="cuda") for _ in range(3)]
+    lev.grad(up([i.u for i in insts]), up([i.pi for i in insts]),
+             up([i.c2 for i in insts], 1.0), [i.dt for i in insts], nsteps, ckpt,
+             up(seeds_u), up(seeds_p), *g)
+    lev.sync()
+    got = [lev.gather(x) for x in g]
+    for k, inst in enumerate(insts):
+        ou, op, oc = orc.grad_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, nsteps,
+                                       ckpt, seeds_u[k], seeds_p[k])
+        assert rel_err(got[0][k], ou) <= 1e-10, k
+        assert rel_err(got[1][k], op) <= 1e-10, k
+        assert rel_err(got[2][k], oc) <= 1e-10, k
