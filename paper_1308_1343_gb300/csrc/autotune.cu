@@ -89,11 +89,7 @@ struct Timer {
       const bool mine = L->box_class[b] == cls;
       const int tx = mine ? c.tx : L->classes[L->box_class[b]].tile.tile_x;
       const int tz = mine ? c.tz : L->classes[L->box_class[b]].tile.tile_z;
-      const int ty = 2 * dev_threads() / tx;
-      for (int z0 = 0; z0 < nz; z0 += tz)
-        for (int y0 = 0; y0 < ny; y0 += ty)
-          for (int x0 = 0; x0 < nx; x0 += tx)
-            items.push_back(dev::DItem{(int)b, x0, y0, z0, std::min(tz, nz - z0), tx / 2});
+      append_box_items(items, (int)b, nx, ny, nz, tx, 2 * dev_threads() / tx, tz);
     }
     if (items.size() > cap) {
       if (ditems) cudaFree(ditems);
@@ -197,6 +193,15 @@ std::vector<Cand> neighbours(const Cand& c, int64_t nz) {
     }
   if (c.tz > 4) v.push_back(Cand{c.tx, c.tz / 2});
   if (c.tz < nz) v.push_back(Cand{c.tx, c.tz * 2});
+  // finer steps: one z-run more or fewer per box column (the runs of a box
+  // have near-equal lengths), which moves the item count against the
+  // persistent grid's waves
+  const int64_t runs = (nz + c.tz - 1) / c.tz;
+  for (int64_t r : {runs - 1, runs + 1})
+    if (r >= 1 && r <= nz) {
+      const int tz = (int)((nz + r - 1) / r);
+      if (tz >= 4 && tz != c.tz) v.push_back(Cand{c.tx, tz});
+    }
   return v;
 }
 

@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
 template <class A, bool SECOND, bool RECORD>
 struct PairEpi {
   static constexpr int NF = 4;  // y.u, y.pi, q = c2 dt/(12 h^2), then A: q/3, B: L y.u
+  static constexpr bool kDefer = SECOND;  // measured: faster for pass B only
   const double* f[NF];
   double* out_u;
   double* out_p;
@@ -370,7 +371,7 @@ struct PairEpi {
 
 template <class A, bool SECOND, bool RECORD>
 __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
-  __shared__ Smem<NT, A, 4, 2> smem;
+  __shared__ Smem<NT, A, 4, 2, SECOND> smem;
   __shared__ unsigned red[2 * NT / 32];
   unsigned err = 0;
   const double* const F[2] = {a.s0, a.s1};
@@ -773,7 +774,8 @@ cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
   return cudaGetLastError();
 }
 
-// Four 46 KB CTAs per SM need the largest shared-memory carveout.
+// Four 46 KB stage CTAs, or two 108 KB pass-B CTAs, per SM need the largest
+// shared-memory carveout.
 template <class K>
 void prefer_shared(K kernel) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -788,6 +790,11 @@ static void set_carveouts() {
   prefer_shared(fwd_stage_kernel<Fixed, false>);
   prefer_shared(fwd_stage_kernel<Fp64, true>);
   prefer_shared(fwd_stage_kernel<Fp64, false>);
+  // pass B keeps three planes of pointwise fields: two 108 KB CTAs per SM
+  prefer_shared(pair_kernel<FixedI, true, false>);
+  prefer_shared(pair_kernel<FixedI, true, true>);
+  prefer_shared(pair_kernel<Fp64, true, false>);
+  prefer_shared(pair_kernel<Fp64, true, true>);
   prefer_shared(lap_kernel<Fixed>);
   prefer_shared(lap_kernel<Fp64>);
   prefer_shared(pair_kernel<FixedI, false, false>);

@@ -31,6 +31,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "descriptors.hpp"
@@ -280,15 +281,26 @@ struct TileSmem {
 };
 
 // NS stencil fields share the traversal (one pipeline, one barrier per
-// plane); field f uses tile buffers 2f and 2f+1.
-template <int NT, class A, int NF, int NS = 1>
+// plane); field f uses tile buffers 2f and 2f+1.  A deferred epilogue (see
+// run_items) keeps three planes of pointwise fields instead of two.
+template <int NT, class A, int NF, int NS = 1, bool DEFER = false>
 struct Smem {
   typename A::T tile[2 * NS * TileSmem<NT>::kMaxElems];
-  double2 pw[2][NF > 0 ? NF : 1][NT];
+  double2 pw[DEFER ? 3 : 2][NF > 0 ? NF : 1][NT];
   // raw halo pairs and raw column pairs staged by cp.async (several stencil
   // fields only)
   double2 hraw[2][NS][NS > 1 ? NT : 1];
   double2 craw[2][NS][NS > 1 ? NT : 1];
+};
+
+// Epi::kDefer if the epilogue declares it, else false
+template <class E, class = void>
+struct DeferOf {
+  static constexpr bool value = false;
+};
+template <class E>
+struct DeferOf<E, std::void_t<decltype(E::kDefer)>> {
+  static constexpr bool value = E::kDefer;
 };
 
 // a point is read by some stencil iff it lies outside the interior along at
@@ -306,12 +318,14 @@ __device__ __forceinline__ int out_of(int c, int n) {
 // on the threads owning interior points, with idx the element index of the
 // thread's first point (x, y, k), pw[j] its pair of pointwise field j, and
 // rA[f], rB[f] the unscaled sums r = 12 h^2 (L F[f]) at both points in the
-// policy's integer or FP64 form.
+// policy's integer or FP64 form.  With several stencil fields the epilogue
+// may be deferred (Epi::kDefer): plane k's runs after plane k+1's
+// conversions, before its barrier, which shortens the register lifetimes
+// around the stencil; the arithmetic and its results are unchanged.
 template <int NT, int NS, class A, class Epi>
-__device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
-                                          const double* const (&F)[NS], const A (&arith)[NS],
-                                          Smem<NT, A, Epi::NF, NS>& sm, unsigned& err,
-                                          Epi& epi) {
+__device__ __forceinline__ void run_items(
+    const DItem& it, const DBox& bx, const double* const (&F)[NS], const A (&arith)[NS],
+    Smem<NT, A, Epi::NF, NS, (NS > 1 && DeferOf<Epi>::value)>& sm, unsigned& err, Epi& epi) {
   using T = typename A::T;
   using T2 = typename A::T2;
   constexpr int NF = Epi::NF;
@@ -373,16 +387,18 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
   // k (registers are the scarce resource there); with one they are loaded to
   // registers a plane ahead.
   constexpr bool kAsyncHalo = NS > 1;
+  constexpr bool kDefer = kAsyncHalo && DeferOf<Epi>::value;
 
   // running element offsets (advance by one plane per iteration)
   int oc = colOff + (it.z0 + 2) * pz;  // next column load
   int oh = hg + it.z0 * pz;            // next halo load
   int op = colOff + it.z0 * pz;        // next pointwise stage
   int oi = op;                         // current plane
-  auto stage_pw = [&](int buf) {
+  // buf: the halo/column buffer (plane parity); pbuf: the pointwise buffer
+  auto stage_pw = [&](int buf, int pbuf) {
     if (actA) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async16(&sm.pw[buf][f][tid], epi.f[f] + op);
+      for (int f = 0; f < NF; ++f) cp_async16(&sm.pw[pbuf][f][tid], epi.f[f] + op);
     }
     if (kAsyncHalo) {
       const int t = kAsyncHalo ? tid : 0;
@@ -416,7 +432,11 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
     oc += pz;
     oh += pz;
   }
-  stage_pw(0);
+  stage_pw(0, 0);
+  // deferred epilogue: the pointwise buffer of the current plane (mod 3) and
+  // the previous plane's sums
+  int b3 = 0;
+  typename A::T sA[NS], sB[NS];
 
   const int rowSelf = (ly + 2) * W + 2 * lx + 2;
   // one plane: m2..p1 hold planes k-2..k+1; p2 receives plane k+2
@@ -444,7 +464,7 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
         oc += pz;
         oh += pz;
       }
-      stage_pw((kk + 1) & 1);
+      stage_pw((kk + 1) & 1, kDefer ? (b3 == 2 ? 0 : b3 + 1) : ((kk + 1) & 1));
     } else {
       cp_async_commit();
     }
@@ -459,6 +479,13 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
               arith[f].conv(sm.hraw[kk & 1][f][t], hx0 + oz <= 1, hx1 + oz <= 1, err);
         p2[f] = conv_at(f, sm.craw[kk & 1][f][t], k + 2);
       }
+    }
+    if (kDefer && kk > 0 && actA) {
+      const int pb = b3 == 0 ? 2 : b3 - 1;
+      double2 pw[NF > 0 ? NF : 1];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) pw[f] = sm.pw[pb][f][tid];
+      epi.point(oi - pz, pw, sA, sB, actB, gx, gy, k - 1);
     }
     __syncthreads();
     if (actA) {
@@ -478,12 +505,21 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
         rB[f] = A::lap(c0[f].y, c0[f].x, xp.x, ym1.y, yp1.y, m1[f].y, p1[f].y,
                        xm.y, xp.y, ym2.y, yp2.y, m2[f].y, p2[f].y);
       }
-      double2 pw[NF > 0 ? NF : 1];
+      if (kDefer) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) pw[f] = sm.pw[kk & 1][f][tid];
-      epi.point(oi, pw, rA, rB, actB, gx, gy, k);
+        for (int f = 0; f < NS; ++f) {
+          sA[f] = rA[f];
+          sB[f] = rB[f];
+        }
+      } else {
+        double2 pw[NF > 0 ? NF : 1];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) pw[f] = sm.pw[kk & 1][f][tid];
+        epi.point(oi, pw, rA, rB, actB, gx, gy, k);
+      }
     }
     oi += pz;
+    b3 = b3 == 2 ? 0 : b3 + 1;
   };
   // unrolled by the queue length so the five z-values never move
   for (int kk = 0;;) {
@@ -497,6 +533,13 @@ __device__ __forceinline__ void run_items(const DItem& it, const DBox& bx,
     if (++kk >= it.nzr) break;
     plane(kk, qe, qa, qb, qc, qd);
     if (++kk >= it.nzr) break;
+  }
+  if (kDefer && actA) {
+    const int pb = b3 == 0 ? 2 : b3 - 1;
+    double2 pw[NF > 0 ? NF : 1];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) pw[f] = sm.pw[pb][f][tid];
+    epi.point(oi - pz, pw, sA, sB, actB, gx, gy, it.z0 + it.nzr - 1);
   }
   cp_async_wait_all();
   __syncthreads();  // the next item reuses the buffers

@@ -24,6 +24,11 @@ int get_field(sc_level* L, const std::string& name, double** p);
 int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s);
 int scratch4(sc_level* L, double* W[6]);
 int upload_items(sc_level* L);
+// Append the work items of box b (interior nx x ny x nz) for a tile of
+// tx x ty points and z-runs of at most tz planes, z-major: the z extent is
+// cut into ceil(nz / tz) runs whose lengths differ by at most one plane.
+void append_box_items(std::vector<dev::DItem>& items, int b, int nx, int ny, int nz, int tx,
+                      int ty, int tz);
 // nsteps RK4 steps as sc_level_rk4_step; qprep = false reuses the pre-scaled
 // wave speeds of the previous call (same c2 and dt)
 int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt, int nsteps,

@@ -53,17 +53,25 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
     box_items[b] = (int)items.size();
     const sc_box& B = L->boxes[b];
     const sc_tile& t = L->classes[L->box_class[b]].tile;
-    const int nx = (int)(B.hi[0] - B.lo[0]), ny = (int)(B.hi[1] - B.lo[1]),
-              nz = (int)(B.hi[2] - B.lo[2]);
-    for (int z0 = 0; z0 < nz; z0 += t.tile_z)
-      for (int y0 = 0; y0 < ny; y0 += t.tile_y)
-        for (int x0 = 0; x0 < nx; x0 += t.tile_x)
-          items.push_back(DItem{(int)b, x0, y0, z0, std::min(t.tile_z, nz - z0), t.tile_x / 2});
+    append_box_items(items, (int)b, (int)(B.hi[0] - B.lo[0]), (int)(B.hi[1] - B.lo[1]),
+                     (int)(B.hi[2] - B.lo[2]), t.tile_x, t.tile_y, t.tile_z);
   }
   box_items[L->boxes.size()] = (int)items.size();
 }
 
 }  // namespace
+
+void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, int tx, int ty,
+                      int tz) {
+  const int runs = (nz + tz - 1) / tz;
+  const int base = nz / runs, extra = nz % runs;
+  for (int r = 0, z0 = 0; r < runs; ++r) {
+    const int len = base + (r < extra ? 1 : 0);
+    for (int y0 = 0; y0 < ny; y0 += ty)
+      for (int x0 = 0; x0 < nx; x0 += tx) items.push_back(DItem{b, x0, y0, z0, len, tx / 2});
+    z0 += len;
+  }
+}
 
 int upload_items(sc_level* L) {
   DeviceState* D = L->dev;
