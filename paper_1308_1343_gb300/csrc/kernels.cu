@@ -454,6 +454,7 @@ __global__ void __launch_bounds__(NT, 4) lap_kernel(LapArgs a) {
 template <class A, bool SECOND>
 struct Adj2Epi {
   static constexpr int NF = SECOND ? 0 : 1;  // c2
+  static constexpr bool kHaloSplit = true;  // measured: faster here
   const double* f[1];
   double* __restrict__ p0;
   double* __restrict__ p1;

@@ -303,6 +303,16 @@ struct DeferOf<E, std::void_t<decltype(E::kDefer)>> {
   static constexpr bool value = E::kDefer;
 };
 
+// Epi::kHaloSplit if the epilogue declares it, else false
+template <class E, class = void>
+struct HaloSplitOf {
+  static constexpr bool value = false;
+};
+template <class E>
+struct HaloSplitOf<E, std::void_t<decltype(E::kHaloSplit)>> {
+  static constexpr bool value = E::kHaloSplit;
+};
+
 // a point is read by some stencil iff it lies outside the interior along at
 // most one axis, and there within the ghost width: 0 inside, 1 in the ghost
 // range [-2, 0) or [n, n+2), 2 beyond (row padding)
@@ -352,18 +362,27 @@ __device__ __forceinline__ void run_items(
   // this thread's halo pair of the plane tile, if any (at most one: the
   // halo of a tile has 4 txh + 2 TY <= NT pairs for every allowed shape)
   const int nhalo = 4 * txh + 2 * TY;
-  const bool hasH = tid < nhalo;
+  // With several stencil fields and Epi::kHaloSplit, when NS * nhalo <= NT,
+  // each thread takes one (pair, field) entry instead of one pair of every
+  // field: the halo conversions spread over NS times as many warps, which
+  // shortens the slowest warp's way to the plane barrier (measured: faster
+  // for the adjoint passes, slower for the forward ones).
+  const bool hsplit = NS > 1 && HaloSplitOf<Epi>::value && NS * nhalo <= NT;
+  const int hfield = hsplit ? tid / nhalo : 0;
+  const int hp = hsplit ? tid - hfield * nhalo : tid;  // the thread's halo pair
+  const bool hasH = hsplit ? tid < NS * nhalo : tid < nhalo;
+  auto mine = [&](int f) { return hasH && (!hsplit || f == hfield); };
   int hs = 0;                 // smem index of the pair
   int hg = off0;              // element index of the pair on plane 0
   int hx0 = 2, hx1 = 2;       // outside counts (>= 2: masked off)
   if (hasH) {
     int hx, hy;
-    if (tid < 4 * txh) {
-      const int r = tid / txh;
-      hx = 2 * (tid - r * txh);
+    if (hp < 4 * txh) {
+      const int r = hp / txh;
+      hx = 2 * (hp - r * txh);
       hy = r < 2 ? r - 2 : TY + r - 2;
     } else {
-      const int j = tid - 4 * txh;
+      const int j = hp - 4 * txh;
       const int side = j / TY;
       hy = j - side * TY;
       hx = side ? TX : -2;
@@ -402,10 +421,9 @@ __device__ __forceinline__ void run_items(
     }
     if (kAsyncHalo) {
       const int t = kAsyncHalo ? tid : 0;
-      if (hasH) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) cp_async16(&sm.hraw[buf][f][t], F[f] + oh);
-      }
+      for (int f = 0; f < NS; ++f)
+        if (mine(f)) cp_async16(&sm.hraw[buf][f][t], F[f] + oh);
 #pragma unroll
       for (int f = 0; f < NS; ++f) cp_async16(&sm.craw[buf][f][t], F[f] + oc);
       oh += pz;
@@ -474,7 +492,7 @@ __device__ __forceinline__ void run_items(
       const int t = kAsyncHalo ? tid : 0;
 #pragma unroll
       for (int f = 0; f < NS; ++f) {
-        if (hasH)
+        if (mine(f))
           *reinterpret_cast<T2*>(sm.tile + (2 * f + (kk & 1)) * bufElems + hs) =
               arith[f].conv(sm.hraw[kk & 1][f][t], hx0 + oz <= 1, hx1 + oz <= 1, err);
         p2[f] = conv_at(f, sm.craw[kk & 1][f][t], k + 2);
