@@ -180,3 +180,25 @@ def test_autotune_chooses_a_form(orc, tmp_path):
     assert rel_err(pi[0], op) <= TOL
     _, u1, p1 = run_gpu([inst], 3, 1, 0, fuse=form)
     assert np.array_equal(u[0], u1[0]) and np.array_equal(pi[0], p1[0])
+
+
+@pytest.mark.parametrize("fuse", [1, 2])
+def test_tiles_and_z_runs_change_no_bit(orc, fuse):
+    """Tile widths 16, 32, 64 and z-run lengths that do or do not divide
+    the box (runs of near-equal length: 37 on 75 planes gives 38 + 37, 5
+    gives fifteen runs of 5, 100 one run), on a ragged box: every setting
+    gives the same bits, and the oracle's values within the bar."""
+    dom = W.Domain((44, 38, 75), 1.0 / 40)
+    inst = W.bumpy_instance(dom, 12)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, dom.h, inst.dt, 3)
+    lev = make_level([inst])
+    lev.set_fusion(fuse)
+    ref = None
+    for tx, tz in ((32, 32), (32, 37), (16, 5), (64, 100), (16, 74), (64, 3)):
+        lev.set_tuning(0, tx, tz)
+        assert lev.get_tuning(0) == (tx, 512 // tx, tz)
+        _, u, pi = run_gpu([inst], 3, 1, 0, lev=lev)
+        if ref is None:
+            ref = (u[0], pi[0])
+            assert rel_err(u[0], ou) <= TOL and rel_err(pi[0], op) <= TOL
+        assert np.array_equal(u[0], ref[0]) and np.array_equal(pi[0], ref[1]), (tx, tz)
