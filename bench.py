@@ -46,6 +46,13 @@ BYTES_PER_POINT_PASS = {"A": 8 * 7, "B": 8 * 8}
 # and need 4 FMAs per pass, i.e. 2 per stage)
 FP64_OPS_PER_POINT_STAGE = {"fp64": 15, "fixed": 3}
 FP64_OPS_PER_POINT_PASS = {"fp64": 28, "fixed": 4}
+# FP64 FMA rate of this GPU (G FMA/s), measured with a probe kernel of
+# back-to-back independent DFMAs timed by CUDA events: about 2 lanes per
+# clock per SM at 2.07 GHz
+FP64_FMA_RATE_G = 597.0
+# bytes per point and RK4 step of the classic unfused stage form (each of
+# the 3-register stage arrays streamed once per stage): 38 doubles
+BYTES_PER_POINT_STEP_CLASSIC = 304
 # seconds of CPU work the oracle's cpu_baseline sample aims at
 CPU_SAMPLE_S = 12.0
 # RK4 steps of the oracle per step of the reference arm
@@ -532,11 +539,16 @@ def run_ours(a, ws, rank, local):
                          "launches": nlaunch, "avg_launch_ms": avg_ms,
                          "gather_avg_launch_ms": gather_ms / max(gather_n, 1),
                          "fp64_tflops_est": fp64_achieved,
+                         "fp64_fraction_of_measured": fp64_achieved / (2e-3 * FP64_FMA_RATE_G),
+                         "classic_equivalent_gbs": value * BYTES_PER_POINT_STEP_CLASSIC / 1e9,
                          "hbm_fraction_of_nominal_7900": achieved / 7900.0,
                          "kernel_hash": khash,
                          "note": ("two RK4 stages per pass halve the DRAM bytes of a step; "
-                                  "these kernels are then limited by SM instruction issue "
-                                  "(fixed-point integer work and FP64 FMAs), not by HBM")
+                                  "these kernels are then limited by the SM (latency of "
+                                  "shared-memory loads, FP64 results and integer chains at "
+                                  "15 warps per SM), not by HBM; classic_equivalent_gbs is "
+                                  "the rate times the 304 B per point and step of an unfused "
+                                  "stage form")
                          if form == 2 else "one stage per pass, HBM-bound"},
             "cpu_baseline": cpu,
             "e2e": e2e,
