@@ -342,9 +342,16 @@ struct PairEpi {
     one(rA[0], rA[1], u0.x, p0.x, q.x, x.x, un.x, pn.x, lv.x, q0.x, q1.x);
     one(rB[0], rB[1], u0.y, p0.y, q.y, x.y, un.y, pn.y, lv.y, q0.y, q1.y);
     if (actB) {
-      st2(out_u + i, un);
-      st2(out_p + i, pn);
-      if (!SECOND) st2(ly + i, lv);
+      // pass A's outputs go out with an evict-first hint (measured: 4 %
+      // faster; pass B was 3 % slower with it)
+      if (!SECOND) {
+        st2cs(out_u + i, un);
+        st2cs(out_p + i, pn);
+        st2cs(ly + i, lv);
+      } else {
+        st2(out_u + i, un);
+        st2(out_p + i, pn);
+      }
       if (RECORD) {
         st2(r0 + i, q0);
         st2(r1 + i, q1);

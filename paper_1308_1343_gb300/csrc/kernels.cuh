@@ -49,6 +49,10 @@ __device__ __forceinline__ double2 ld2(const double* p) {
 __device__ __forceinline__ void st2(double* p, double2 v) {
   *reinterpret_cast<double2*>(p) = v;
 }
+// the same with the streaming (evict-first) cache hint
+__device__ __forceinline__ void st2cs(double* p, double2 v) {
+  __stcs(reinterpret_cast<double2*>(p), v);
+}
 
 __device__ __forceinline__ unsigned biased_exp(double x) {
   return (unsigned)((__double_as_longlong(x) >> 52) & 0x7ff);
