@@ -69,7 +69,9 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--arith", choices=["fixed", "fp64"], default="fixed")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the uneven-level, ensemble and adjoint measurements")
+                   help="skip the uneven-level, ensemble, two-level and adjoint measurements")
+    p.add_argument("--extras", default=",".join(EXTRAS),
+                   help="comma-separated subset of %s to measure" % ",".join(EXTRAS))
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
 
@@ -266,9 +268,26 @@ def _time_steps(torch, lev, u, pi, c2, dt, nsteps, mode, reps, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-def _extras(torch, W, B, Level, arith, stream):
+EXTRAS = ("uneven", "ensemble", "two_level", "adjoint")
+
+
+def _extras(torch, W, B, Level, arith, stream, which=EXTRAS):
     out = {}
-    # uneven 64-box level: batched graph vs per-box launches, 50 RK4 steps
+    if "uneven" in which:
+        out["uneven_level"] = _uneven(torch, W, B, Level, arith, stream)
+    if "ensemble" in which:
+        out["ensemble"] = _ensemble(torch, W, B, Level, arith, stream)
+    if "two_level" in which:
+        # two-level hierarchy: coarse 256^3 periodic, fine region 256^3 points
+        # (the central eighth of the domain at half the spacing), 20 steps
+        out["two_level"] = _two_level(torch, W, B, Level, arith, stream)
+    if "adjoint" in which:
+        out["adjoint"] = _adjoint(torch, W, B, Level, arith, stream)
+    return out
+
+
+def _uneven(torch, W, B, Level, arith, stream):
+    """Uneven 64-box level: batched graph vs per-box launches, 50 RK4 steps."""
     inst = W.uneven_level()
     lev = Level.from_instances([inst])
     lev.set_arith(arith)
@@ -284,7 +303,7 @@ def _extras(torch, W, B, Level, arith, stream):
         res[name] = n * 50 / t
     lev.rk4_step(u, pi, c2, inst.dt, 10, B.SC_MODE_TIMED, stream=stream)
     gbs, _, _, _, kname = _stencil_roofline(lev, B, n)
-    out["uneven_level"] = {
+    out = {
         "workload": "512x512x256 periodic domain, 64 bisected boxes, 50 RK4 steps",
         "boxes": len(inst.boxes), "points": n, "stages_per_pass": lev.get_fusion(),
         "graph_updates_per_s": res["graph"], "per_box_updates_per_s": res["per_box"],
@@ -292,8 +311,11 @@ def _extras(torch, W, B, Level, arith, stream):
     }
     del lev, u, pi, c2
     torch.cuda.empty_cache()
+    return out
 
-    # ensemble: 256 independent periodic cubes of edge 24..96, 100 RK4 steps
+
+def _ensemble(torch, W, B, Level, arith, stream):
+    """256 independent periodic cubes of edge 24..96, 100 RK4 steps."""
     insts = W.ensemble()
     lev = Level.from_instances(insts)
     lev.set_arith(arith)
@@ -306,18 +328,18 @@ def _extras(torch, W, B, Level, arith, stream):
                  stream=stream)
     _time_steps(torch, lev, u, pi, c2, dts, 5, B.SC_MODE_GRAPH, 1, stream)
     t = _time_steps(torch, lev, u, pi, c2, dts, 100, B.SC_MODE_GRAPH, 1, stream)
-    out["ensemble"] = {"workload": "256 periodic cubes, edges 24..96, own c2 and pulse, "
-                                   "100 RK4 steps, autotuned tiles",
-                       "points": n, "stages_per_pass": lev.get_fusion(),
-                       "graph_updates_per_s": n * 100 / t}
+    out = {"workload": "256 periodic cubes, edges 24..96, own c2 and pulse, "
+                       "100 RK4 steps, autotuned tiles",
+           "points": n, "stages_per_pass": lev.get_fusion(),
+           "graph_updates_per_s": n * 100 / t}
     del lev, u, pi, c2
     torch.cuda.empty_cache()
+    return out
 
-    # two-level hierarchy: coarse 256^3 periodic, fine region 256^3 points
-    # (the central eighth of the domain at half the spacing), 20 steps
-    out["two_level"] = _two_level(torch, W, B, Level, arith, stream)
 
-    # adjoint / forward ratio on the 128^3, 200-step differentiation workload
+def _adjoint(torch, W, B, Level, arith, stream):
+    """Adjoint / forward ratio on the 128^3, 200-step differentiation
+    workload, and where the backward's device time goes."""
     inst = W.gradient_problem(128, 4)
     lev = Level.from_instances([inst])
     lev.set_arith(arith)
@@ -358,12 +380,11 @@ def _extras(torch, W, B, Level, arith, stream):
         ms, n = lev.kernel_time(k)
         kern[name] = {"ms": ms, "launches": n}
     lev.set_profiling(False)
-    out["adjoint"] = {"workload": "128^3 periodic box, 200 RK4 steps, checkpoints every 20",
-                      "stages_per_pass": lev.get_fusion(), "t_forward_s": t_fwd, "t_forward_tape_s": t1 - t0,
-                      "t_backward_s": t2 - t1, "ratio_backward_over_forward": (t2 - t1) / t_fwd,
-                      "ratio_total_over_forward": (t2 - t0) / t_fwd,
-                      "backward_kernels": kern}
-    return out
+    return {"workload": "128^3 periodic box, 200 RK4 steps, checkpoints every 20",
+            "stages_per_pass": lev.get_fusion(), "t_forward_s": t_fwd,
+            "t_forward_tape_s": t1 - t0, "t_backward_s": t2 - t1,
+            "ratio_backward_over_forward": (t2 - t1) / t_fwd,
+            "ratio_total_over_forward": (t2 - t0) / t_fwd, "backward_kernels": kern}
 
 
 def _two_level(torch, W, B, Level, arith, stream):
@@ -503,7 +524,8 @@ def run_ours(a, ws, rank, local):
     extras = {}
     if not a.no_extras and rank == 0:
         del hu, hp, hc, ou, op
-        extras = _extras(torch, W, B, Level, arith, stream)
+        extras = _extras(torch, W, B, Level, arith, stream,
+                         which=[x for x in a.extras.split(",") if x])
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu:

@@ -534,9 +534,12 @@ __global__ void __launch_bounds__(NT, 2) adj2_kernel(Adj2Args a) {
 }
 
 // The combination of one adjoint step, pointwise over interior points: one
-// point per thread (chunks of kGatherChunk points), all fields distinct.
+// point per thread (chunks of kGatherChunk points), all fields distinct.  It
+// streams 12 fields in and 5 out, so memory parallelism sets its speed: 32
+// registers give 8 CTAs per SM (measured: faster than 40 registers and 6
+// CTAs, and than two points per thread with 16-byte accesses).
 template <bool FIXED>
-__global__ void __launch_bounds__(kGatherChunk) adj_combine_kernel(
+__global__ void __launch_bounds__(kGatherChunk, 8) adj_combine_kernel(
     const DRect* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
     AdjCombineArgs a) {
   __shared__ unsigned red[32];
