@@ -11,7 +11,9 @@
 //       w_s.pi = y.pi + g_s * c2 * (L w_{s-1}.u).
 // Each stage is one fused pass: the stencil of w_{s-1}.u, two FMAs per
 // point, and no K accumulators (26 instead of 38 doubles moved per point per
-// step).
+// step).  The pass kernels (pair_kernel) take two stages per pass, forming
+// L w_1.u and L w_3.u by linearity from the stencils of the pass's two
+// fields (15 doubles per point per step; see PairEpi).
 #include "kernels.cuh"
 #include "launch.hpp"
 

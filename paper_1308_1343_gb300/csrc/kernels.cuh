@@ -14,10 +14,15 @@
 // outside the box are loaded only where they are ghosts, and never stored.
 //
 // Latency hiding is a one-plane software pipeline: while plane k is
-// computed, the column value of plane k+3 and the halo of plane k+1 are in
-// flight to registers, and the pointwise fields of plane k+1 are in flight
-// to shared memory by cp.async (no registers held); nothing loaded in an
-// iteration is consumed in the same iteration.
+// computed, the pointwise fields of plane k+1 are in flight to shared memory
+// by cp.async (no registers held), and so are the next raw column and halo
+// values: to registers with one stencil field, by cp.async with several
+// (where registers are the scarce resource).  Nothing loaded in an iteration
+// is consumed in the same iteration.  With several stencil fields, two
+// per-epilogue options reorder work without changing any result: a deferred
+// epilogue (kDefer: plane k's pointwise work runs after plane k+1's
+// conversions) and a halo split by (pair, field) over more warps
+// (kHaloSplit).
 //
 // The Laplacian's 13-point integer-weighted sum has two arithmetic forms:
 //  * Fp64:  FP64 adds and FMAs.
