@@ -224,6 +224,12 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
  * ghosts of every stencil input are gathered before the pass that reads it
  * (one batched launch, inside the step's CUDA graph in SC_MODE_GRAPH), so on
  * return the ghosts of u hold the input of the last pass, not the result.
+ * A box that alone tiles a domain periodic on every axis, with an even x
+ * extent and x, y extents >= 2 (a self-periodic box), is an exception: the
+ * kernels read the periodic images of its interior for its x and y ghosts,
+ * which are not written, and only its z ghosts are gathered (in
+ * SC_MODE_PER_BOX every ghost is gathered).  sc_level_fill_ghosts always
+ * fills every ghost.
  * mode is one of SC_MODE_*.  Scratch stage arrays are allocated on the first
  * call.
  * A level with a domain that is not periodic on every axis takes ONE step

@@ -14,6 +14,10 @@ struct DBox {
   long long pz;   // plane pitch (elements)
   int nx, ny, nz; // interior extent
   int dom;        // domain index
+  int wrap;       // 1: the box alone tiles a domain periodic on every axis
+                  // (nx even, nx and ny >= 2), so the stencil kernels read
+                  // the periodic images of its interior in x and y directly,
+                  // and only its z ghosts are gathered
 };
 
 struct DItem {

@@ -360,11 +360,18 @@ __device__ __forceinline__ void run_items(
   const bool actA = (gx < bx.nx) && (gy < bx.ny);
   const bool actB = (gx + 1 < bx.nx) && (gy < bx.ny);
   const int pz = (int)bx.pz;
+  // in-plane coordinate c in [-2, n + 2) of a self-periodic box (bx.wrap):
+  // its periodic image in [0, n), i.e. the owner of the ghost point;
+  // otherwise c.  Computed once per item, outside the plane loop (the z
+  // ghosts of such a box are still gathered: wrapping z would cost the
+  // loop address arithmetic and registers)
+  const bool wrap = bx.wrap != 0;
+  auto wr = [wrap](int c, int n) { return !wrap ? c : (c < 0 ? c + n : (c >= n ? c - n : c)); };
   // element index of the thread's pair on plane 0 (32-bit: a field holds
   // fewer than 2^31 doubles); columns outside the padded box read the box's
   // interior corner instead (in bounds, masked off below, never used)
   const int off0 = (int)bx.off, py = (int)bx.py;
-  const int colOff = colLoad ? off0 + gx + gy * py : off0;
+  const int colOff = colLoad ? off0 + wr(gx, bx.nx) + wr(gy, bx.ny) * py : off0;
   const int oy = out_of(gy, bx.ny);
   const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
 
@@ -399,7 +406,7 @@ __device__ __forceinline__ void run_items(
     const int ax = it.x0 + hx, ay = it.y0 + hy;
     hs = (hy + 2) * W + hx + 2;
     if (ax < bx.nx + 2 && ay < bx.ny + 2) {
-      hg = off0 + ax + ay * py;
+      hg = off0 + wr(ax, bx.nx) + wr(ay, bx.ny) * py;
       const int o = out_of(ay, bx.ny);
       hx0 = out_of(ax, bx.nx) + o;
       hx1 = out_of(ax + 1, bx.nx) + o;
@@ -418,10 +425,10 @@ __device__ __forceinline__ void run_items(
   constexpr bool kDefer = kAsyncHalo && DeferOf<Epi>::value;
 
   // running element offsets (advance by one plane per iteration)
-  int oc = colOff + (it.z0 + 2) * pz;  // next column load
-  int oh = hg + it.z0 * pz;            // next halo load
-  int op = colOff + it.z0 * pz;        // next pointwise stage
-  int oi = op;                         // current plane
+  int oc = colOff + (it.z0 + 2) * pz;                         // next column load
+  int oh = hg + it.z0 * pz;                                   // next halo load
+  int op = off0 + (colLoad ? gx + gy * py : 0) + it.z0 * pz;  // next pointwise stage
+  int oi = op;                                                // current plane
   // buf: the halo/column buffer (plane parity); pbuf: the pointwise buffer
   auto stage_pw = [&](int buf, int pbuf) {
     if (actA) {

@@ -57,6 +57,11 @@ struct DeviceState {
   dev::DChunk* gchunks = nullptr;
   int ngchunks = 0;
   std::vector<int> box_gchunks;
+  // the chunks of the gather list whose destination box is not
+  // self-periodic (DBox::wrap): the exchange that stencil inputs need
+  dev::DChunk* gchunks_nw = nullptr;
+  int ngchunks_nw = 0;
+  std::vector<char> box_wrap;
   // interior rectangles (one per box) + chunks
   dev::DRect* irects = nullptr;
   dev::DChunk* ichunks = nullptr;

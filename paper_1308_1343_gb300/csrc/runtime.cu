@@ -120,7 +120,7 @@ void release_device(sc_level* L) {
     cudaEventDestroy(pr.second);
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
-  void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->irects, D->ichunks,
+  void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->gchunks_nw, D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial};
   for (void* p : ptrs)
@@ -152,10 +152,21 @@ int ensure_device(sc_level* L) {
 
   const int nb = (int)L->boxes.size(), nd = (int)L->doms.size();
   std::vector<DBox> boxes(nb);
+  D->box_wrap.assign(nb, 0);
   for (int b = 0; b < nb; ++b) {
     const sc_box& B = L->boxes[b];
+    const sc_domain& Dm = L->doms[B.domain];
+    // self-periodic: the box is its domain, periodic on every axis; the
+    // kernels then read the owners of its x and y ghosts by wrapping the
+    // coordinates (pairs of x-points stay 16-byte aligned for an even x
+    // extent), and only its z ghosts are gathered
+    bool self = Dm.periodic == 7u;
+    for (int d = 0; d < 3; ++d) self = self && B.lo[d] == Dm.lo[d] && B.hi[d] == Dm.hi[d];
+    self = self && B.hi[0] - B.lo[0] >= 2 && B.hi[1] - B.lo[1] >= 2 &&
+           (B.hi[0] - B.lo[0]) % 2 == 0;
+    D->box_wrap[b] = self ? 1 : 0;
     boxes[b] = DBox{L->off[b], L->py[b], L->pz[b], (int)(B.hi[0] - B.lo[0]),
-                    (int)(B.hi[1] - B.lo[1]), (int)(B.hi[2] - B.lo[2]), B.domain};
+                    (int)(B.hi[1] - B.lo[1]), (int)(B.hi[2] - B.lo[2]), B.domain, self ? 1 : 0};
   }
   int rc = upload(&D->boxes, boxes);
   if (rc) return rc;
@@ -168,6 +179,7 @@ int ensure_device(sc_level* L) {
   // ghost copies, chunked, grouped by destination box
   std::vector<DRect> grects;
   std::vector<DChunk> gchunks;
+  std::vector<char> zface;  // per rect: it fills z ghosts of its box
   D->box_gchunks.assign(nb + 1, 0);
   {
     size_t c = 0;
@@ -187,6 +199,7 @@ int ensure_device(sc_level* L) {
         r.ez = (int)C.ext[2];
         r.dom = L->boxes[b].domain;
         grects.push_back(r);
+        zface.push_back(C.dst_lo[2] < L->boxes[b].lo[2] || C.dst_lo[2] >= L->boxes[b].hi[2]);
         add_chunks((int)grects.size() - 1, C.ext[0] * C.ext[1] * C.ext[2], gchunks,
                    dev::kGatherChunk);
       }
@@ -197,6 +210,16 @@ int ensure_device(sc_level* L) {
   if (!rc) rc = upload(&D->gchunks, gchunks);
   if (rc) return rc;
   D->ngchunks = (int)gchunks.size();
+  {
+    // the exchange the stencil kernels need: every ghost of an ordinary
+    // box, the z ghosts of a self-periodic one
+    std::vector<DChunk> nw;
+    for (int b = 0; b < nb; ++b)
+      for (int c = D->box_gchunks[b]; c < D->box_gchunks[b + 1]; ++c)
+        if (!D->box_wrap[b] || zface[gchunks[c].rect]) nw.push_back(gchunks[c]);
+    D->ngchunks_nw = (int)nw.size();
+    if (!nw.empty() && (rc = upload(&D->gchunks_nw, nw))) return rc;
+  }
 
   // the same copies seen from their sources: a ghost on the low (high) side
   // of its box along axis d is owned by a point in the high (low) two-deep
@@ -383,6 +406,9 @@ struct Enq {
   // recompute the pre-scaled wave speeds in the prologue (false: a caller
   // that keeps c2 and dt knows they are current)
   bool qprep = true;
+  // gathers refresh the ghosts of every box (sc_level_fill_ghosts); false:
+  // only those the stencil kernels read (not those of self-periodic boxes)
+  bool all_ghosts = false;
 };
 
 // Event pair around one launch when timing is on.
@@ -411,13 +437,16 @@ struct TimedLaunch {
 static cudaError_t enq_fill(const Enq& q, double* f) {
   DeviceState* D = q.L->dev;
   if (!q.per_box) {
+    const int n = q.all_ghosts ? D->ngchunks : D->ngchunks_nw;
+    if (n <= 0) return cudaSuccess;
     (*q.count)++;
     TimedLaunch t(q, SC_KERNEL_GATHER);
-    return dev::launch_gather(D->grects, D->gchunks, D->ngchunks, f, D->grid_small, q.s);
+    return dev::launch_gather(D->grects, q.all_ghosts ? D->gchunks : D->gchunks_nw, n, f,
+                              D->grid_small, q.s);
   }
   for (size_t b = 0; b + 1 < D->box_gchunks.size(); ++b) {
     const int n = D->box_gchunks[b + 1] - D->box_gchunks[b];
-    if (n <= 0) continue;
+    if (n <= 0) continue;  // per box: every ghost (simplest; not the fast path)
     (*q.count)++;
     TimedLaunch t(q, SC_KERNEL_GATHER);
     cudaError_t e = dev::launch_gather(D->grects, D->gchunks + D->box_gchunks[b], n, f,
@@ -513,18 +542,19 @@ static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear
   const int nclear = clear ? 2 * (int)q.L->doms.size() : 0;
   bool cleared = clear == nullptr;
   if (!q.per_box) {
-    if (D->ngchunks > 0) {
+    const int n = q.all_ghosts ? D->ngchunks : D->ngchunks_nw;
+    if (n > 0) {
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
-      cudaError_t e = dev::launch_gather2(D->grects, D->gchunks, D->ngchunks, f, g, clear,
-                                          nclear, q.s);
+      cudaError_t e = dev::launch_gather2(D->grects, q.all_ghosts ? D->gchunks : D->gchunks_nw,
+                                          n, f, g, clear, nclear, q.s);
       if (e != cudaSuccess) return e;
       cleared = true;
     }
   } else {
     for (size_t b = 0; b + 1 < D->box_gchunks.size(); ++b) {
       const int n = D->box_gchunks[b + 1] - D->box_gchunks[b];
-      if (n <= 0) continue;
+      if (n <= 0) continue;  // per box: every ghost (simplest; not the fast path)
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
       cudaError_t e = dev::launch_gather2(D->grects, D->gchunks + D->box_gchunks[b], n, f, g,
@@ -720,6 +750,7 @@ int sc_level_fill_ghosts(sc_level* L, double* field, void* stream) {
   int rc = ensure_device(L);
   if (rc) return rc;
   Enq q{L, (cudaStream_t)stream, &L->launches, false};
+  q.all_ghosts = true;
   SC_CUDA(enq_fill(q, field));
   return SC_OK;
 }

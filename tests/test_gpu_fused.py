@@ -144,13 +144,22 @@ def test_zero_steps_and_zero_field():
 
 
 def test_timed_mode_counts_two_passes():
+    """Two pass launches and two gathers per step, on a box that alone
+    tiles its periodic domain (its x and y ghosts are read from their owners
+    directly, its z ghosts gathered) and on a level of two boxes."""
     from paper_1308_1343_gb300 import binding as B
     inst = W.bumpy_instance(W.Domain((32, 24, 16), 1.0 / 24), 4)
-    lev, _, _ = run_fused([inst], 3, 1, B.SC_MODE_TIMED)
-    assert lev.kernel_time(B.SC_KERNEL_PAIR_A)[1] == 3
-    assert lev.kernel_time(B.SC_KERNEL_PAIR_B)[1] == 3
-    assert lev.kernel_time(B.SC_KERNEL_GATHER)[1] == 6
-    assert lev.kernel_time(B.SC_KERNEL_STAGE)[1] == 0
+    two = W.Instance(inst.dom, inst.u, inst.pi, inst.c2, inst.dt)
+    two.boxes = [((0, 0, 0), (16, 24, 16)), ((16, 0, 0), (32, 24, 16))]
+    res = []
+    for case in (inst, two):
+        lev, u, pi = run_fused([case], 3, 1, B.SC_MODE_TIMED)
+        assert lev.kernel_time(B.SC_KERNEL_PAIR_A)[1] == 3
+        assert lev.kernel_time(B.SC_KERNEL_PAIR_B)[1] == 3
+        assert lev.kernel_time(B.SC_KERNEL_GATHER)[1] == 6
+        assert lev.kernel_time(B.SC_KERNEL_STAGE)[1] == 0
+        res.append((u[0], pi[0]))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
 def test_full_256_bumpy_vs_oracle(orc):
