@@ -261,7 +261,8 @@ int sc_level_misfit(sc_level* level, const double* u, const double* u_obs,
 /* Forward pass for differentiation: runs nsteps RK4 steps from (u0, pi0)
  * (batched launches; with one stage per pass the ghosts of each stage
  * output are written by the stage kernel itself, from the level's exchange
- * list grouped by source box and face slab, so u_T's ghosts are filled;
+ * list grouped by source box and face slab, so u_T's ghosts are filled --
+ * for a self-periodic box (see sc_level_rk4_step) its z ghosts only;
  * with two stages per pass they are gathered before each pass and u_T's
  * ghosts are not refreshed), keeping the state every ckpt_every steps in
  * library-owned checkpoint fields (the level's tape, replacing any earlier

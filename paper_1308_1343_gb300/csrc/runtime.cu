@@ -235,6 +235,9 @@ int ensure_device(sc_level* L) {
         else if (C.dst_lo[a] >= Bd.hi[a]) { d = a; side = 0; }
       }
       if (d < 0) return set_error(SC_EINVAL, "exchange copy does not target a ghost region");
+      // a self-periodic box's x and y ghosts are never read (the kernels
+      // wrap those coordinates): push its z ghosts only
+      if (D->box_wrap[C.dst_box] && d < 2) continue;
       DPush e{};
       e.lo0 = (int)(C.src_lo[0] - Bs.lo[0]);
       e.lo1 = (int)(C.src_lo[1] - Bs.lo[1]);

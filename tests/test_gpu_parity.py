@@ -268,7 +268,9 @@ def test_ghosts_written_by_stage_kernels(orc, arith):
     """In the taped forward with one stage per pass the stage kernels write
     the ghost copies of every value they produce; the final state's ghosts
     must equal a fresh exchange of its interior, bit for bit, on a 64-box
-    level and on a single box."""
+    level, and on a single box alone in its periodic domain for the z ghosts
+    (the kernels read the owners of its x and y ghosts directly, so those
+    are not written)."""
     import torch
     for inst in (W.uneven_level(n=(96, 80, 64), h=1.0 / 64, levels=6, seed=3, box_seed=30),
                  W.bumpy_instance(W.Domain((36, 28, 20), 1.0 / 28), 5)):
@@ -286,8 +288,15 @@ def test_ghosts_written_by_stage_kernels(orc, arith):
         want = lev.padded_boxes(lev.scatter([lev.gather(uT)[0]], fill=np.nan))
         n = inst.dom.n
         orc.fill_ghosts([lo + hi for lo, hi in inst.boxes], (0, 0, 0) + tuple(n), 7, want)
+        single = len(inst.boxes) == 1
         for a, b in zip(got, want):
             m = ~np.isnan(b)
+            if single:  # z ghosts and interior only
+                m[:, :2, :] = False
+                m[:, -2:, :] = False
+                m[:, :, :2] = False
+                m[:, :, -2:] = False
+                assert m[:2].any() and m[-2:].any()
             assert np.array_equal(a[m], b[m])
         _, ug, _ = run_gpu([inst], 3, arith, 0)
         assert np.array_equal(lev.gather(uT)[0], ug[0])
