@@ -321,6 +321,26 @@ def test_thin_and_odd_boxes(orc, arith):
         assert rel_err(pi[0], op) <= TOL
 
 
+@pytest.mark.parametrize("fuse", [1, 2])
+def test_small_self_periodic_boxes(orc, fuse):
+    """A box that alone tiles its periodic domain reads the owners of its x
+    and y ghosts directly (coordinates wrap by the extent), also when the
+    extent is 2 or 3 so that a ghost's owner lies two periods away from the
+    box's other side; an odd x extent keeps the gathered ghosts.  Every
+    shape matches the oracle and, bit for bit, the same domain split into
+    two boxes (which gathers every ghost)."""
+    for n in ((2, 3, 5), (4, 2, 3), (6, 7, 2), (5, 6, 4), (12, 10, 3)):
+        inst = W.bumpy_instance(W.Domain(n, 1.0 / 8), 11)
+        ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 3)
+        _, u, pi = run_gpu([inst], 3, 1, 0, fuse=fuse)
+        assert rel_err(u[0], ou) <= TOL and rel_err(pi[0], op) <= TOL, n
+        split = W.Instance(inst.dom, inst.u, inst.pi, inst.c2, inst.dt)
+        k = n[2] // 2 if n[2] >= 2 else 1
+        split.boxes = [((0, 0, 0), (n[0], n[1], k)), ((0, 0, k), n)]
+        _, u2, p2 = run_gpu([split], 3, 1, 0, fuse=fuse)
+        assert np.array_equal(u[0], u2[0]) and np.array_equal(pi[0], p2[0]), n
+
+
 def test_zero_steps_and_zero_field():
     inst = W.bumpy_instance(W.Domain((20, 16, 12), 1.0 / 16), 3)
     lev, u, pi = run_gpu([inst], 0, 1, 0)
