@@ -335,8 +335,12 @@ def test_small_self_periodic_boxes(orc, fuse):
         _, u, pi = run_gpu([inst], 3, 1, 0, fuse=fuse)
         assert rel_err(u[0], ou) <= TOL and rel_err(pi[0], op) <= TOL, n
         split = W.Instance(inst.dom, inst.u, inst.pi, inst.c2, inst.dt)
-        k = n[2] // 2 if n[2] >= 2 else 1
-        split.boxes = [((0, 0, 0), (n[0], n[1], k)), ((0, 0, k), n)]
+        d = int(np.argmax(n))  # halves of edge >= 2 along the longest axis
+        hi0 = list(n)
+        hi0[d] = n[d] // 2
+        lo1 = [0, 0, 0]
+        lo1[d] = n[d] // 2
+        split.boxes = [((0, 0, 0), tuple(hi0)), (tuple(lo1), n)]
         _, u2, p2 = run_gpu([split], 3, 1, 0, fuse=fuse)
         assert np.array_equal(u[0], u2[0]) and np.array_equal(pi[0], p2[0]), n
 
