@@ -37,6 +37,9 @@ struct DRect {
   int dom;                   // domain of the points
   int box;                   // box of the points (interior rectangles)
   int x0, y0, z0;            // interior coordinates of the first point
+  int pairs;                 // gathers: 1 if ex, src and dst are even, so the
+                             // rectangle is copied in 16-byte pairs of x-points
+                             // (its chunks then count pairs, not points)
 };
 
 // A set of fine points that prolongation fills (interior points of one fine

@@ -38,16 +38,22 @@ __global__ void __launch_bounds__(kGatherChunk) gather_kernel(
     const DChunk ch = chunks[c];
     const DRect r = rects[ch.rect];
     const int p = ch.first + (int)threadIdx.x;
-    if (p < r.ex * r.ey * r.ez) {
-      const int t = p / r.ex;
-      const int x = p - t * r.ex;
+    const int ux = r.pairs ? r.ex >> 1 : r.ex;  // units per row: pairs or points
+    if (p < ux * r.ey * r.ez) {
+      const int t = p / ux;
+      const int x = (p - t * ux) << r.pairs;
       const int z = t / r.ey;
       const int y = t - z * r.ey;
       // offsets fit 32 bits: a field holds fewer than 2^31 doubles
       const int dst = (int)r.dst + x + y * (int)r.dpy + z * (int)r.dpz;
       const int src = (int)r.src + x + y * (int)r.spy + z * (int)r.spz;
-      f[dst] = f[src];
-      if (TWO) g[dst] = g[src];
+      if (r.pairs) {
+        st2(f + dst, ld2(f + src));
+        if (TWO) st2(g + dst, ld2(g + src));
+      } else {
+        f[dst] = f[src];
+        if (TWO) g[dst] = g[src];
+      }
     }
   }
 }

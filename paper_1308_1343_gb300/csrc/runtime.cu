@@ -198,10 +198,13 @@ int ensure_device(sc_level* L) {
         r.ey = (int)C.ext[1];
         r.ez = (int)C.ext[2];
         r.dom = L->boxes[b].domain;
+        // 16-byte pairs when both ends of every row start on an even element
+        // (pitches are multiples of 16 doubles)
+        r.pairs = (C.ext[0] % 2 == 0 && r.src % 2 == 0 && r.dst % 2 == 0) ? 1 : 0;
         grects.push_back(r);
         zface.push_back(C.dst_lo[2] < L->boxes[b].lo[2] || C.dst_lo[2] >= L->boxes[b].hi[2]);
-        add_chunks((int)grects.size() - 1, C.ext[0] * C.ext[1] * C.ext[2], gchunks,
-                   dev::kGatherChunk);
+        add_chunks((int)grects.size() - 1, (C.ext[0] >> r.pairs) * C.ext[1] * C.ext[2],
+                   gchunks, dev::kGatherChunk);
       }
     }
     D->box_gchunks[nb] = (int)gchunks.size();
