@@ -341,9 +341,31 @@ int sc_hierarchy_restriction_points(const sc_hierarchy* H, int64_t* xyz, int64_t
   return write_points(H->restr_rects, xyz, cap, n);
 }
 
+namespace {
+// Prolongation; emax (or NULL): exponent-bound slots that take the written
+// values' exponents in (see sc_hierarchy_step)
+int prolongate(sc_hierarchy* H, const double* u0, const double* u1, const double* p0,
+               const double* p1, double alpha, double* fu, double* fpi, unsigned* emax,
+               void* stream);
+int restrict_to(sc_hierarchy* H, const double* fu, const double* fpi, double* cu, double* cpi,
+                unsigned* emax, void* stream);
+}  // namespace
+
 int sc_hierarchy_prolongate(sc_hierarchy* H, const double* u0, const double* u1, const double* p0,
                             const double* p1, double alpha, double* fu, double* fpi,
                             void* stream) {
+  return prolongate(H, u0, u1, p0, p1, alpha, fu, fpi, nullptr, stream);
+}
+
+int sc_hierarchy_restrict(sc_hierarchy* H, const double* fu, const double* fpi, double* cu,
+                          double* cpi, void* stream) {
+  return restrict_to(H, fu, fpi, cu, cpi, nullptr, stream);
+}
+
+namespace {
+int prolongate(sc_hierarchy* H, const double* u0, const double* u1, const double* p0,
+               const double* p1, double alpha, double* fu, double* fpi, unsigned* emax,
+               void* stream) {
   if (!H) return set_error(SC_EINVAL, "NULL hierarchy");
   if (!aligned16(u0) || !aligned16(u1) || !aligned16(p0) || !aligned16(p1) || !aligned16(fu) ||
       !aligned16(fpi))
@@ -366,23 +388,24 @@ int sc_hierarchy_prolongate(sc_hierarchy* H, const double* u0, const double* u1,
     dp = bp;
   }
   dev::launch_prolong(H->d_prol, H->d_prol_chunks, (int)H->prol_chunks.size(), du, dp, fu, fpi,
-                      s);
+                      emax, s);
   H->fine->launches++;
   return cuda_check("prolongation");
 }
 
-int sc_hierarchy_restrict(sc_hierarchy* H, const double* fu, const double* fpi, double* cu,
-                          double* cpi, void* stream) {
+int restrict_to(sc_hierarchy* H, const double* fu, const double* fpi, double* cu, double* cpi,
+                unsigned* emax, void* stream) {
   if (!H) return set_error(SC_EINVAL, "NULL hierarchy");
   if (!aligned16(fu) || !aligned16(fpi) || !aligned16(cu) || !aligned16(cpi))
     return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
   int rc = ensure_uploaded(H);
   if (rc) return rc;
   dev::launch_restrict(H->d_restr, H->d_restr_chunks, (int)H->restr_chunks.size(), fu, fpi, cu,
-                       cpi, (cudaStream_t)stream);
+                       cpi, emax, (cudaStream_t)stream);
   H->coarse->launches++;
   return cuda_check("restriction");
 }
+}  // namespace
 
 int sc_hierarchy_step(sc_hierarchy* H, double* cu, double* cpi, const double* cc2, double* fu,
                       double* fpi, const double* fc2, double dt, int32_t nsteps, int32_t mode,
@@ -398,6 +421,13 @@ int sc_hierarchy_step(sc_hierarchy* H, double* cu, double* cpi, const double* cc
     return rc;
   const cudaStream_t s = (cudaStream_t)stream;
   const double dtf = 0.5 * dt;
+  if ((rc = ensure_device(H->fine))) return rc;
+  // Exponent bounds: after its first step in this call a level reuses the
+  // bounds its last pass left in the slots of (u, pi) (two stages per pass),
+  // raised by the restriction (coarse) or prolongation (fine) that wrote
+  // into it since, instead of scanning its fields again
+  unsigned* ce = H->coarse->dev->emax;
+  unsigned* fe = H->fine->dev->emax;
   for (int n = 0; n < nsteps; ++n) {
     // the coarse level at t where prolongation reads it (the blend with
     // alpha = 0 of a field with itself is that field), then one coarse step
@@ -407,15 +437,15 @@ int sc_hierarchy_step(sc_hierarchy* H, double* cu, double* cpi, const double* cc
     if ((rc = cuda_check("hierarchy: copy of the coarse level"))) return rc;
     // c2 and dt are fixed within the call: the pre-scaled wave speeds are
     // computed on each level's first step only
-    if ((rc = level_steps(H->coarse, cu, cpi, cc2, dt, 1, mode, s, n == 0))) return rc;
+    if ((rc = level_steps(H->coarse, cu, cpi, cc2, dt, 1, mode, s, n == 0, n > 0))) return rc;
     // two fine steps of dt/2, boundary data at t and t + dt/2
     for (int k = 0; k < 2; ++k) {
-      if ((rc = sc_hierarchy_prolongate(H, ou, cu, op, cpi, 0.5 * k, fu, fpi, stream)))
+      const bool first = n == 0 && k == 0;
+      if ((rc = prolongate(H, ou, cu, op, cpi, 0.5 * k, fu, fpi, first ? nullptr : fe, stream)))
         return rc;
-      if ((rc = level_steps(H->fine, fu, fpi, fc2, dtf, 1, mode, s, n == 0 && k == 0)))
-        return rc;
+      if ((rc = level_steps(H->fine, fu, fpi, fc2, dtf, 1, mode, s, first, !first))) return rc;
     }
-    if ((rc = sc_hierarchy_restrict(H, fu, fpi, cu, cpi, stream))) return rc;
+    if ((rc = restrict_to(H, fu, fpi, cu, cpi, ce, stream))) return rc;
   }
   return SC_OK;
 }

@@ -634,7 +634,7 @@ template <int PX, int PY, int PZ>
 __device__ __forceinline__ void prol_point(const DProl& r, int x, int y, int z,
                                            const double* __restrict__ du,
                                            const double* __restrict__ dp, double* __restrict__ fu,
-                                           double* __restrict__ fp) {
+                                           double* __restrict__ fp, unsigned& mu, unsigned& mp) {
   constexpr int NX = PX ? 4 : 1, NY = PY ? 4 : 1, NZ = PZ ? 4 : 1;
   const int fx = r.fx0 + 2 * x, fy = r.fy0 + 2 * y, fz = r.fz0 + 2 * z;
   const int cx = PX ? ((fx - 1) >> 1) - 1 : fx >> 1;
@@ -657,12 +657,16 @@ __device__ __forceinline__ void prol_point(const DProl& r, int x, int y, int z,
   const long long o = r.dst + 2ll * x + 2ll * y * r.dpy + 2ll * z * r.dpz;
   fu[o] = su;
   fp[o] = sp;
+  mu = max(mu, biased_exp(su));
+  mp = max(mp, biased_exp(sp));
 }
 
 __global__ void __launch_bounds__(kGatherChunk) prolong_kernel(
     const DProl* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
     const double* __restrict__ du, const double* __restrict__ dp, double* __restrict__ fu,
-    double* __restrict__ fp) {
+    double* __restrict__ fp, unsigned* emax) {
+  __shared__ unsigned red[2 * kGatherChunk / 32];
+  unsigned mu = 0, mp = 0;
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const DChunk ch = chunks[c];
     const DProl r = rects[ch.rect];
@@ -674,16 +678,18 @@ __global__ void __launch_bounds__(kGatherChunk) prolong_kernel(
     const int y = t - z * r.ey;
     // one parity class per list entry: a uniform branch
     switch ((r.fx0 & 1) | ((r.fy0 & 1) << 1) | ((r.fz0 & 1) << 2)) {
-      case 0: prol_point<0, 0, 0>(r, x, y, z, du, dp, fu, fp); break;
-      case 1: prol_point<1, 0, 0>(r, x, y, z, du, dp, fu, fp); break;
-      case 2: prol_point<0, 1, 0>(r, x, y, z, du, dp, fu, fp); break;
-      case 3: prol_point<1, 1, 0>(r, x, y, z, du, dp, fu, fp); break;
-      case 4: prol_point<0, 0, 1>(r, x, y, z, du, dp, fu, fp); break;
-      case 5: prol_point<1, 0, 1>(r, x, y, z, du, dp, fu, fp); break;
-      case 6: prol_point<0, 1, 1>(r, x, y, z, du, dp, fu, fp); break;
-      default: prol_point<1, 1, 1>(r, x, y, z, du, dp, fu, fp); break;
+      case 0: prol_point<0, 0, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 1: prol_point<1, 0, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 2: prol_point<0, 1, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 3: prol_point<1, 1, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 4: prol_point<0, 0, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 5: prol_point<1, 0, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 6: prol_point<0, 1, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      default: prol_point<1, 1, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
     }
   }
+  // the fine level's exponent bounds of u and pi take the written values in
+  if (emax) cta_max2_to(mu, mp, emax, emax + 1, red);
 }
 
 // out = (1 - alpha) a + alpha b on the rectangles, rounded step by step.
@@ -717,7 +723,9 @@ __global__ void __launch_bounds__(256) blend_kernel(const DRect* __restrict__ re
 __global__ void __launch_bounds__(kGatherChunk) restrict_kernel(
     const DRestr* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
     const double* __restrict__ fu, const double* __restrict__ fp, double* __restrict__ cu,
-    double* __restrict__ cp) {
+    double* __restrict__ cp, unsigned* emax) {
+  __shared__ unsigned red[2 * kGatherChunk / 32];
+  unsigned mu = 0, mp = 0;
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const DChunk ch = chunks[c];
     const DRestr r = rects[ch.rect];
@@ -729,9 +737,14 @@ __global__ void __launch_bounds__(kGatherChunk) restrict_kernel(
     const int y = t - z * r.ey;
     const long long d = r.dst + x + (long long)y * r.dpy + (long long)z * r.dpz;
     const long long s = r.src + 2ll * x + 2ll * y * r.spy + 2ll * z * r.spz;
-    cu[d] = fu[s];
-    cp[d] = fp[s];
+    const double vu = fu[s], vp = fp[s];
+    cu[d] = vu;
+    cp[d] = vp;
+    mu = max(mu, biased_exp(vu));
+    mp = max(mp, biased_exp(vp));
   }
+  // the coarse level's exponent bounds of u and pi take the written values in
+  if (emax) cta_max2_to(mu, mp, emax, emax + 1, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -923,9 +936,9 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {
 
 cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks,
                            const double* du, const double* dp, double* fu, double* fp,
-                           cudaStream_t s) {
+                           unsigned* emax, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
-  prolong_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, du, dp, fu, fp);
+  prolong_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, du, dp, fu, fp, emax);
   return cudaGetLastError();
 }
 
@@ -940,9 +953,10 @@ cudaError_t launch_blend(const DRect* rects, const DChunk* chunks, int nchunks, 
 
 cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchunks,
                             const double* fu, const double* fp, double* cu, double* cp,
-                            cudaStream_t s) {
+                            unsigned* emax, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
-  restrict_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, fu, fp, cu, cp);
+  restrict_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, fu, fp, cu, cp,
+                                                   emax);
   return cudaGetLastError();
 }
 

@@ -156,17 +156,20 @@ cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks
 cudaError_t launch_adj2(bool second, int arith, const Adj2Args& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_combine(int arith, const DRect* rects, const DChunk* chunks,
                                int nchunks, const AdjCombineArgs& a, int grid, cudaStream_t s);
-// du, dp: the coarse data at the prolongation's time (see blend)
+// du, dp: the coarse data at the prolongation's time (see blend); emax (or
+// NULL): the fine level's two exponent-bound slots of (u, pi), which take
+// the largest biased exponent written (atomicMax)
 cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks,
                            const double* du, const double* dp, double* fu, double* fp,
-                           cudaStream_t s);
+                           unsigned* emax, cudaStream_t s);
 // ao = (1 - alpha) a0 + alpha a1, bo likewise, on the rectangles
 cudaError_t launch_blend(const DRect* rects, const DChunk* chunks, int nchunks, const double* a0,
                          const double* a1, const double* b0, const double* b1, double alpha,
                          double* ao, double* bo, int grid, cudaStream_t s);
+// emax (or NULL): as for launch_prolong, the coarse level's slots
 cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchunks,
                             const double* fu, const double* fp, double* cu, double* cp,
-                            cudaStream_t s);
+                            unsigned* emax, cudaStream_t s);
 int stage_threads();
 cudaError_t stage_occupancy(int arith, int* blocks_per_sm);
 

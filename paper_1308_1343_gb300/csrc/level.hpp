@@ -30,9 +30,12 @@ int upload_items(sc_level* L);
 void append_box_items(std::vector<dev::DItem>& items, int b, int nx, int ny, int nz, int tx,
                       int ty, int tz);
 // nsteps RK4 steps as sc_level_rk4_step; qprep = false reuses the pre-scaled
-// wave speeds of the previous call (same c2 and dt)
+// wave speeds of the previous call (same c2 and dt); bounds = true reuses
+// the exponent bounds of (u, pi) left by the previous call's last pass, which
+// every write to u and pi since must have raised (two stages per pass, fixed
+// arithmetic; otherwise they are computed)
 int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt, int nsteps,
-                int mode, cudaStream_t s, bool qprep);
+                int mode, cudaStream_t s, bool qprep, bool bounds = false);
 
 struct SizeClass {
   std::array<int64_t, 3> ext;  // interior extent rounded up to a multiple of 8

@@ -415,6 +415,9 @@ struct Enq {
   // gathers refresh the ghosts of every box (sc_level_fill_ghosts); false:
   // only those the stencil kernels read (not those of self-periodic boxes)
   bool all_ghosts = false;
+  // the exponent bounds of the run's input are already in place (see
+  // level_steps)
+  bool bounds = false;
 };
 
 // Event pair around one launch when timing is on.
@@ -660,6 +663,7 @@ static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const doubl
     if (e != cudaSuccess) return e;
   }
   if (q.L->arith != SC_ARITH_FIXED) return cudaSuccess;
+  if (q.bounds && pi && q.L->fuse == 2) return cudaSuccess;  // slots X hold them
   e = cudaMemsetAsync(D->emax, 0, sizeof(unsigned) * 4 * q.L->doms.size(), q.s);
   if (e != cudaSuccess) return e;
   // With a non-periodic domain the boundary ghosts hold caller data that
@@ -686,13 +690,14 @@ int scratch4(sc_level* L, double* W[6]) {
 }
 
 static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int nsteps, int mode,
-                     cudaStream_t s, bool qprep = true) {
+                     cudaStream_t s, bool qprep = true, bool bounds = false) {
   DeviceState* D = L->dev;
   double* W[6];
   int rc = scratch4(L, W);
   if (rc) return rc;
   Enq q{L, s, &L->launches, mode == SC_MODE_PER_BOX};
   q.qprep = qprep;
+  q.bounds = bounds;
   if (mode == SC_MODE_TIMED) {
     q.timed = true;
     D->ev_used = 0;
@@ -738,10 +743,10 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
 }
 
 int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt, int nsteps,
-                int mode, cudaStream_t s, bool qprep) {
+                int mode, cudaStream_t s, bool qprep, bool bounds) {
   int rc = sc_level_rk4_step(L, u, pi, c2, &dt, 1, 0, mode, s);  // validation and set-up
   if (rc || nsteps == 0) return rc;
-  return run_steps(L, u, pi, c2, nsteps, mode, s, qprep);
+  return run_steps(L, u, pi, c2, nsteps, mode, s, qprep, bounds);
 }
 
 }  // namespace sc
