@@ -8,8 +8,9 @@
  *    fine index f (per axis) lies at coarse coordinate f / 2.
  *  - Prolongation: cubic Lagrange interpolation along each axis as a tensor
  *    product (weights (-1, 9, 9, -1) / 16 at odd fine indices, injection at
- *    even ones; exact for polynomials of degree <= 3 per axis), of data
- *    interpolated linearly in time between two coarse time levels.
+ *    even ones; exact for polynomials of degree <= 3 per axis), evaluated as
+ *    successive one-dimensional interpolations along z, then y, then x, of
+ *    data interpolated linearly in time between two coarse time levels.
  *  - Restriction: injection, coarse point c takes the fine value at 2c.
  *  - Time stepping (sub-cycling): one hierarchy step of dt is one coarse
  *    RK4 step of dt, two fine RK4 steps of dt/2 (before each, the fine

@@ -13,12 +13,14 @@ Berger 1984), but defines none of them.  The readings taken here:
 * Vertex-centred refinement by 2: fine index f (per axis) lies at coarse
   coordinate f / 2, so even fine indices coincide with coarse points.
 * Prolongation: cubic Lagrange interpolation along each axis, applied as a
-  tensor product.  At an odd fine index f the coarse points (f-3)/2 ...
-  (f+3)/2 get the weights (-1, 9, 9, -1) / 16, at an even one the coarse
-  point f/2 gets weight 1.  It is exact for polynomials of degree <= 3 per
-  axis.  In time, linear interpolation between the coarse levels at t and
-  t + dt: data = (1 - alpha) * old + alpha * new, applied before the
-  spatial sum.
+  tensor product, i.e. as successive one-dimensional interpolations: along
+  z for each coarse (y, x) column of the stencil, then along y, then along
+  x.  At an odd fine index f the coarse points (f-3)/2 ... (f+3)/2 get the
+  weights (-1, 9, 9, -1) / 16, at an even one the coarse point f/2 gets
+  weight 1.  It is exact for polynomials of degree <= 3 per axis.  In time,
+  linear interpolation between the coarse levels at t and t + dt:
+  data = (1 - alpha) * old + alpha * new, applied before the spatial
+  interpolation.
 * Restriction: injection, coarse point c takes the fine value at 2c.
 * Berger-Oliger sub-cycling with a buffer zone.  The fine level's region R
   (a box of fine points, not periodic) carries a buffer band of width B >= 4
@@ -58,10 +60,12 @@ def stencil_1d(f: int):
 def prolongate(c_old, c_new, alpha: float, fpts) -> np.ndarray:
     """Values at fine points fpts (int array (n, 3) of fine (x, y, z)) from
     the coarse periodic levels c_old (time t) and c_new (t + dt), at time
-    t + alpha dt.  Each term is az * ay * ax * data with data = (1 - alpha)
-    old + alpha new at the coarse point; terms are summed z offsets
-    outermost, then y, then x (an even index has one term along its axis;
-    the zero weights padding it to four add exact zeros)."""
+    t + alpha dt, with data = (1 - alpha) old + alpha new at each coarse
+    point.  One-dimensional interpolation along z of each of the 4 x 4
+    coarse (y, x) columns of the stencil, then along y of the four results
+    per x, then along x: each is 0 plus its four weighted terms in order,
+    every product and sum rounded (an even index has one term along its
+    axis; the zero weights padding it to four add exact zeros)."""
     c_old = np.asarray(c_old, dtype=np.float64)
     c_new = np.asarray(c_new, dtype=np.float64)
     nz, ny, nx = c_old.shape
@@ -81,13 +85,20 @@ def prolongate(c_old, c_new, alpha: float, fpts) -> np.ndarray:
 
     (ix, wx), (iy, wy), (iz, wz) = axis(fpts[:, 0]), axis(fpts[:, 1]), axis(fpts[:, 2])
     data = (1.0 - alpha) * c_old + alpha * c_new
-    acc = np.zeros(len(fpts))
-    for a in range(4):
-        for b in range(4):
-            for c in range(4):
-                acc += wz[:, a] * wy[:, b] * wx[:, c] * data[iz[:, a] % nz, iy[:, b] % ny,
-                                                             ix[:, c] % nx]
-    return acc
+
+    def interp(w, vals):  # 0 + w0 v0 + w1 v1 + w2 v2 + w3 v3, left to right
+        acc = np.zeros(len(fpts))
+        for k in range(4):
+            acc = acc + w[:, k] * vals[k]
+        return acc
+
+    along_x = []
+    for c in range(4):
+        along_y = [interp(wz, [data[iz[:, a] % nz, iy[:, b] % ny, ix[:, c] % nx]
+                               for a in range(4)])
+                   for b in range(4)]
+        along_x.append(interp(wy, along_y))
+    return interp(wx, along_x)
 
 
 def shell_and_buffer(r_lo, r_hi, buffer: int):

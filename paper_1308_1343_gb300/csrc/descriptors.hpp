@@ -56,6 +56,10 @@ struct DProl {
   int cpy, cpz;        // coarse box pitches
 };
 
+// Prolongation runs one CTA per tile of kProlTX x kProlTY x kProlTZ points of
+// a DProl entry; its chunk list holds (entry, tile index) pairs.
+constexpr int kProlTX = 16, kProlTY = 8, kProlTZ = 4;
+
 // A rectangle of coarse points that restriction sets from fine points 2c.
 struct DRestr {
   long long dst;       // coarse element index of the first point

@@ -167,7 +167,12 @@ int build_lists(sc_hierarchy* H) {
           p.cpy = (int)C->py[cb];
           p.cpz = (int)C->pz[cb];
           H->prol.push_back(p);
-          add_chunks((int)H->prol.size() - 1, (int64_t)e[0] * e[1] * e[2], H->prol_chunks);
+          // one chunk per tile of the entry (the tile index in `first`)
+          const int ntiles = ((e[0] + dev::kProlTX - 1) / dev::kProlTX) *
+                             ((e[1] + dev::kProlTY - 1) / dev::kProlTY) *
+                             ((e[2] + dev::kProlTZ - 1) / dev::kProlTZ);
+          for (int t = 0; t < ntiles; ++t)
+            H->prol_chunks.push_back(dev::DChunk{(int)H->prol.size() - 1, t});
         }
       }
     }

@@ -616,76 +616,137 @@ __global__ void __launch_bounds__(kGatherChunk, 8) adj_combine_kernel(
 // Prolongation: cubic Lagrange interpolation along each axis as a tensor
 // product (weights (-1, 9, 9, -1)/16 at odd fine indices, injection at even
 // ones), of data interpolated linearly in time, (1 - alpha) old + alpha new,
-// per coarse point.  The products and sums are rounded one by one (no FMA
-// contraction) and summed z outermost, then y, then x.  Each list entry
-// holds points of one parity per axis, so a warp runs one stencil shape.
-// At alpha != 0 the time interpolation is done once per coarse point by
-// blend_kernel into scratch coarse fields (the same rounding).
+// per coarse point.  The tensor product is applied as successive
+// one-dimensional interpolations, along z, then y, then x, each with its
+// products and sums rounded one by one (no FMA contraction); a tile's
+// points share the z- and y-interpolated intermediates (shared memory).
+// Each list entry holds points of one parity per axis, so a CTA runs one
+// stencil shape.  At alpha != 0 the time interpolation is done once per
+// coarse point by blend_kernel into scratch coarse fields (the same
+// rounding).
 
-// Weight k of the cubic stencil along an axis of parity P (1: odd index).
+// One-dimensional interpolation along an axis of parity P (1: odd index):
+// 0 + w_0 v_0 + w_1 v_1 + w_2 v_2 + w_3 v_3 with w = (-1, 9, 9, -1)/16, each
+// product and sum rounded in that order; at an even index 0 + v_0.  The
+// values are v_k = f[i + k * stride].
+__device__ __forceinline__ double plus_zero(double v) {  // 0.0 + v
+  return (__double_as_longlong(v) << 1) == 0 ? 0.0 : v;
+}
 template <int P>
-__device__ __forceinline__ constexpr double prol_w(int k) {
-  return P == 0 ? 1.0 : (k == 0 || k == 3 ? -0.0625 : 0.5625);
+__device__ __forceinline__ double interp1(const double* __restrict__ f, long long i,
+                                          long long stride) {
+  if (!P) return plus_zero(f[i]);
+  double acc = plus_zero(__dmul_rn(-0.0625, f[i]));
+  acc = __dadd_rn(acc, __dmul_rn(0.5625, f[i + stride]));
+  acc = __dadd_rn(acc, __dmul_rn(0.5625, f[i + 2 * stride]));
+  return __dadd_rn(acc, __dmul_rn(-0.0625, f[i + 3 * stride]));
 }
 
-// Sum of one fine point of parity (PX, PY, PZ): weights are compile-time
-// constants (their products fold), the sum order is z, y, x as above.
+// The tile of one prolongation entry: z interpolation of every coarse (y, x)
+// column the tile's stencils touch, then y, then x, staged in shared memory.
 template <int PX, int PY, int PZ>
-__device__ __forceinline__ void prol_point(const DProl& r, int x, int y, int z,
-                                           const double* __restrict__ du,
-                                           const double* __restrict__ dp, double* __restrict__ fu,
-                                           double* __restrict__ fp, unsigned& mu, unsigned& mp) {
-  constexpr int NX = PX ? 4 : 1, NY = PY ? 4 : 1, NZ = PZ ? 4 : 1;
-  const int fx = r.fx0 + 2 * x, fy = r.fy0 + 2 * y, fz = r.fz0 + 2 * z;
-  const int cx = PX ? ((fx - 1) >> 1) - 1 : fx >> 1;
-  const int cy = PY ? ((fy - 1) >> 1) - 1 : fy >> 1;
-  const int cz = PZ ? ((fz - 1) >> 1) - 1 : fz >> 1;
-  double su = 0.0, sp = 0.0;
-#pragma unroll
-  for (int a = 0; a < NZ; ++a)
-#pragma unroll
-    for (int b = 0; b < NY; ++b) {
-      const long long row = r.cbase + (long long)(cz + a) * r.cpz + (long long)(cy + b) * r.cpy;
-#pragma unroll
-      for (int e = 0; e < NX; ++e) {
-        const double w = prol_w<PZ>(a) * prol_w<PY>(b) * prol_w<PX>(e);  // exact constants
-        const long long i = row + cx + e;
-        su = __dadd_rn(su, __dmul_rn(w, du[i]));
-        sp = __dadd_rn(sp, __dmul_rn(w, dp[i]));
-      }
+__device__ __forceinline__ void prol_tile(const DProl& r, int x0, int y0, int z0, int nx, int ny,
+                                          int nz, const double* __restrict__ du,
+                                          const double* __restrict__ dp, double* __restrict__ fu,
+                                          double* __restrict__ fp, double (*t1)[2], double (*t2)[2],
+                                          unsigned& mu, unsigned& mp) {
+  constexpr int NX = PX ? 4 : 1, NY = PY ? 4 : 1;
+  // coarse index of the first stencil point of the tile's first target
+  const int cx0 = (PX ? ((r.fx0 - 1) >> 1) - 1 : r.fx0 >> 1) + x0;
+  const int cy0 = (PY ? ((r.fy0 - 1) >> 1) - 1 : r.fy0 >> 1) + y0;
+  const int cz0 = (PZ ? ((r.fz0 - 1) >> 1) - 1 : r.fz0 >> 1) + z0;
+  const int wx = nx + NX - 1, wy = ny + NY - 1;
+  // along z: t1[(z * wy + j) * wx + i] for column (cx0 + i, cy0 + j)
+  const int n1 = nz * wy * wx;
+  for (int k = threadIdx.x; k < n1; k += blockDim.x) {
+    const int i = k % wx, jz = k / wx;
+    const int j = jz % wy, z = jz / wy;
+    const long long c =
+        r.cbase + (long long)(cz0 + z) * r.cpz + (long long)(cy0 + j) * r.cpy + cx0 + i;
+    t1[k][0] = interp1<PZ>(du, c, r.cpz);
+    t1[k][1] = interp1<PZ>(dp, c, r.cpz);
+  }
+  __syncthreads();
+  // along y: t2[(z * ny + y) * wx + i]
+  const int n2 = nz * ny * wx;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+    const int i = k % wx, yz = k / wx;
+    const int y = yz % ny, z = yz / ny;
+    const int b = (z * wy + y) * wx + i;
+    double a0, a1;
+    if (!PY) {
+      a0 = plus_zero(t1[b][0]);
+      a1 = plus_zero(t1[b][1]);
+    } else {
+      a0 = plus_zero(__dmul_rn(-0.0625, t1[b][0]));
+      a1 = plus_zero(__dmul_rn(-0.0625, t1[b][1]));
+      a0 = __dadd_rn(a0, __dmul_rn(0.5625, t1[b + wx][0]));
+      a1 = __dadd_rn(a1, __dmul_rn(0.5625, t1[b + wx][1]));
+      a0 = __dadd_rn(a0, __dmul_rn(0.5625, t1[b + 2 * wx][0]));
+      a1 = __dadd_rn(a1, __dmul_rn(0.5625, t1[b + 2 * wx][1]));
+      a0 = __dadd_rn(a0, __dmul_rn(-0.0625, t1[b + 3 * wx][0]));
+      a1 = __dadd_rn(a1, __dmul_rn(-0.0625, t1[b + 3 * wx][1]));
     }
-  const long long o = r.dst + 2ll * x + 2ll * y * r.dpy + 2ll * z * r.dpz;
-  fu[o] = su;
-  fp[o] = sp;
-  mu = max(mu, biased_exp(su));
-  mp = max(mp, biased_exp(sp));
+    t2[k][0] = a0;
+    t2[k][1] = a1;
+  }
+  __syncthreads();
+  // along x, and the fine points
+  const int n3 = nz * ny * nx;
+  for (int k = threadIdx.x; k < n3; k += blockDim.x) {
+    const int x = k % nx, yz = k / nx;
+    const int y = yz % ny, z = yz / ny;
+    const int b = (z * ny + y) * wx + x;
+    double su, sp;
+    if (!PX) {
+      su = plus_zero(t2[b][0]);
+      sp = plus_zero(t2[b][1]);
+    } else {
+      su = plus_zero(__dmul_rn(-0.0625, t2[b][0]));
+      sp = plus_zero(__dmul_rn(-0.0625, t2[b][1]));
+      su = __dadd_rn(su, __dmul_rn(0.5625, t2[b + 1][0]));
+      sp = __dadd_rn(sp, __dmul_rn(0.5625, t2[b + 1][1]));
+      su = __dadd_rn(su, __dmul_rn(0.5625, t2[b + 2][0]));
+      sp = __dadd_rn(sp, __dmul_rn(0.5625, t2[b + 2][1]));
+      su = __dadd_rn(su, __dmul_rn(-0.0625, t2[b + 3][0]));
+      sp = __dadd_rn(sp, __dmul_rn(-0.0625, t2[b + 3][1]));
+    }
+    const long long o = r.dst + 2ll * (x0 + x) + 2ll * (y0 + y) * r.dpy + 2ll * (z0 + z) * r.dpz;
+    fu[o] = su;
+    fp[o] = sp;
+    mu = max(mu, biased_exp(su));
+    mp = max(mp, biased_exp(sp));
+  }
+  __syncthreads();  // the next tile reuses the buffers
 }
 
-__global__ void __launch_bounds__(kGatherChunk) prolong_kernel(
-    const DProl* __restrict__ rects, const DChunk* __restrict__ chunks, int nchunks,
+__global__ void __launch_bounds__(256) prolong_kernel(
+    const DProl* __restrict__ rects, const DChunk* __restrict__ tiles, int ntiles,
     const double* __restrict__ du, const double* __restrict__ dp, double* __restrict__ fu,
     double* __restrict__ fp, unsigned* emax) {
-  __shared__ unsigned red[2 * kGatherChunk / 32];
+  __shared__ double t1[kProlTZ * (kProlTY + 3) * (kProlTX + 3)][2];
+  __shared__ double t2[kProlTZ * kProlTY * (kProlTX + 3)][2];
+  __shared__ unsigned red[2 * 256 / 32];
   unsigned mu = 0, mp = 0;
-  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const DChunk ch = chunks[c];
+  for (int c = blockIdx.x; c < ntiles; c += gridDim.x) {
+    const DChunk ch = tiles[c];
     const DProl r = rects[ch.rect];
-    const int p = ch.first + (int)threadIdx.x;
-    if (p >= r.ex * r.ey * r.ez) continue;
-    const int t = p / r.ex;
-    const int x = p - t * r.ex;
-    const int z = t / r.ey;
-    const int y = t - z * r.ey;
+    const int ntx = (r.ex + kProlTX - 1) / kProlTX, nty = (r.ey + kProlTY - 1) / kProlTY;
+    const int tx = ch.first % ntx, tyz = ch.first / ntx;
+    const int ty = tyz % nty, tz = tyz / nty;
+    const int x0 = tx * kProlTX, y0 = ty * kProlTY, z0 = tz * kProlTZ;
+    const int nx = min(kProlTX, r.ex - x0), ny = min(kProlTY, r.ey - y0);
+    const int nz = min(kProlTZ, r.ez - z0);
     // one parity class per list entry: a uniform branch
     switch ((r.fx0 & 1) | ((r.fy0 & 1) << 1) | ((r.fz0 & 1) << 2)) {
-      case 0: prol_point<0, 0, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      case 1: prol_point<1, 0, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      case 2: prol_point<0, 1, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      case 3: prol_point<1, 1, 0>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      case 4: prol_point<0, 0, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      case 5: prol_point<1, 0, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      case 6: prol_point<0, 1, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
-      default: prol_point<1, 1, 1>(r, x, y, z, du, dp, fu, fp, mu, mp); break;
+      case 0: prol_tile<0, 0, 0>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      case 1: prol_tile<1, 0, 0>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      case 2: prol_tile<0, 1, 0>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      case 3: prol_tile<1, 1, 0>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      case 4: prol_tile<0, 0, 1>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      case 5: prol_tile<1, 0, 1>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      case 6: prol_tile<0, 1, 1>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
+      default: prol_tile<1, 1, 1>(r, x0, y0, z0, nx, ny, nz, du, dp, fu, fp, t1, t2, mu, mp); break;
     }
   }
   // the fine level's exponent bounds of u and pi take the written values in
@@ -938,7 +999,7 @@ cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks
                            const double* du, const double* dp, double* fu, double* fp,
                            unsigned* emax, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
-  prolong_kernel<<<nchunks, kGatherChunk, 0, s>>>(rects, chunks, nchunks, du, dp, fu, fp, emax);
+  prolong_kernel<<<nchunks, 256, 0, s>>>(rects, chunks, nchunks, du, dp, fu, fp, emax);
   return cudaGetLastError();
 }
 
