@@ -438,7 +438,6 @@ def _two_level(torch, W, B, Level, arith, stream):
 
 
 def run_ours(a, ws, rank, local):
-    import numpy as np
     import torch
     from paper_1308_1343_gb300 import binding as B
     from paper_1308_1343_gb300 import build as BUILD

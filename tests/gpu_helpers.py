@@ -24,7 +24,6 @@ def run_gpu(instances, nsteps, arith, mode, lev=None, fuse=1):
     level runs `fuse` RK4 stages per stencil pass; a given one keeps its
     setting."""
     import torch
-    from paper_1308_1343_gb300 import binding as B
     if lev is None:
         lev = make_level(instances)
         lev.set_fusion(fuse)

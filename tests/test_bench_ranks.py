@@ -4,7 +4,6 @@ whole-job throughput (both replicas' units over that time)."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

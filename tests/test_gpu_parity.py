@@ -4,7 +4,6 @@ Bars: ghost copies bit-exact; u and pi within 1e-12 relative max norm of
 the oracle after the stated steps; decomposition independence and the three
 launch modes bit-identical; full-size checks on the 256^3 and 512x512x256
 workloads in the benchmark's launch configuration (graph mode)."""
-import math
 import os
 
 import numpy as np

@@ -2,7 +2,6 @@
 plausible error (a dropped term, a wrong sign, a wrong index, an operand on
 the wrong side) and checks that one of the oracle's pins rejects it, while
 the unmodified oracle passes the same pin.  Everything runs on the CPU."""
-import math
 import os
 
 import numpy as np
