@@ -222,3 +222,44 @@ def test_full_size_step_vs_oracle(orc):
     assert rel_err(gcu, ou) <= TOL
     assert _t_err(gfu, fu_p[2:-2, 2:-2, 2:-2]) <= TOL
     assert _t_err(gfp, fp_p[2:-2, 2:-2, 2:-2]) <= TOL
+
+
+@pytest.mark.parametrize("fuse", [1, 2])
+def test_bounds_follow_prolongated_and_restricted_values(fuse):
+    """After the first step of a call each level reuses the exponent bounds
+    of its last pass, raised by what prolongation or restriction wrote into
+    it since.  A spike 1e6 times the pulse in the coarse data just outside
+    the fine region reaches the fine level only through prolongation (band
+    and ghost shell): four hierarchy steps in one call must still match the
+    oracle, with no scale error raised."""
+    import torch
+    from oracle import hierarchy as H
+    n, lo, hi = 24, (8, 8, 8), (40, 40, 40)
+    fine = W.refined_pair(n, 31, lo, hi)
+    rng = np.random.default_rng(8)
+    # coarse points 1..2 outside R's low x face, on the coarse grid (even fine indices)
+    for cz, cy in ((12, 12), (14, 10)):
+        for cx in (2, 3):
+            fine.u[2 * cz, 2 * cy, 2 * cx] += 1e6 * rng.normal()
+    sub = (slice(None, None, 2),) * 3
+    cu_h, cp_h, cc_h = fine.u[sub].copy(), fine.pi[sub].copy(), fine.c2[sub].copy()
+    hgrid = 1.0 / n
+    dt = 0.25 * hgrid
+    c, f, h = _setup(n, lo, hi, fuse=fuse)
+    cu, cp, cc = c.to_device([cu_h]), c.to_device([cp_h]), c.to_device([cc_h], fill=1.0)
+    fu = f.to_device([_region(fine.u, lo, hi)])
+    fp = f.to_device([_region(fine.pi, lo, hi)])
+    fc = f.to_device([_region(fine.c2, lo, hi)], fill=1.0)
+    h.step(cu, cp, cc, fu, fp, fc, dt, 4)
+    c.sync()
+    f.sync()  # raises if a value exceeded its level's exponent bound
+    torch.cuda.synchronize()
+    ou, op = cu_h, cp_h
+    fu_p, fp_p = _region(fine.u, lo, hi, 2), _region(fine.pi, lo, hi, 2)
+    fc_p = _region(fine.c2, lo, hi, 2)
+    for _ in range(4):
+        ou, op, fu_p, fp_p = H.bo_step(ou, op, cc_h, hgrid, dt, fu_p, fp_p, fc_p, lo, hi, 4)
+    assert rel_err(c.gather(cu)[0], ou) <= TOL
+    assert rel_err(c.gather(cp)[0], op) <= TOL
+    assert _t_err(f.gather(fu)[0], fu_p[2:-2, 2:-2, 2:-2]) <= TOL
+    assert _t_err(f.gather(fp)[0], fp_p[2:-2, 2:-2, 2:-2]) <= TOL
