@@ -476,16 +476,17 @@ def run_ours(a, ws, rank, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
+    # an event between benchmark steps too: best and median step besides the total
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    evs[0].record(stream)
+    for k in range(a.steps):
         lev.rk4_step(u, pi, c2, inst.dt, nsub, B.SC_MODE_GRAPH, stream=stream)
-    e1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t = e0.elapsed_time(e1) / 1e3
+    t = evs[0].elapsed_time(evs[-1]) / 1e3
+    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps))
     clk = clocks.stop()
     lev.sync(stream)
     launches = lev.launch_count() - launches0
@@ -575,6 +576,8 @@ def run_ours(a, ws, rank, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
+            "step_ms": ({"best": per_step[0], "median": per_step[len(per_step) // 2],
+                         "steps": len(per_step)} if per_step else None),
             "clocks": clk,
         }
         line.update(extras)
