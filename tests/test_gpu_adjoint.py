@@ -210,3 +210,34 @@ def test_gradient_of_an_ensemble(orc, fuse):
         assert rel_err(got[0][k], ou) <= 1e-10, k
         assert rel_err(got[1][k], op) <= 1e-10, k
         assert rel_err(got[2][k], oc) <= 1e-10, k
+
+
+def test_gradient_of_the_full_ensemble(orc):
+    """The benchmark's ensemble (256 cubes, own sizes, fields and step sizes)
+    through the checkpointed adjoint, two steps with a checkpoint each: every
+    instance's gradient within 1e-10 of the oracle's."""
+    import os
+    import torch
+    insts = W.ensemble()
+    nsteps, ckpt = 2, 1
+    lev = make_level(insts)
+    lev.set_arith(1)
+    up = lambda arrs, fill=0.0: upload(lev, arrs, fill)
+    seeds_u = [W.random_direction(i.dom.shape, 900 + k) for k, i in enumerate(insts)]
+    seeds_p = [W.random_direction(i.dom.shape, 1900 + k) for k, i in enumerate(insts)]
+    g = [torch.empty(lev.field_size, dtype=torch.float64, device="cuda") for _ in range(3)]
+    lev.grad(up([i.u for i in insts]), up([i.pi for i in insts]),
+             up([i.c2 for i in insts], 1.0), [i.dt for i in insts], nsteps, ckpt,
+             up(seeds_u), up(seeds_p), *g)
+    lev.sync()
+    got = [lev.gather(x) for x in g]
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        for k, inst in enumerate(insts):
+            ou, op, oc = orc.grad_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt,
+                                           nsteps, ckpt, seeds_u[k], seeds_p[k])
+            assert rel_err(got[0][k], ou) <= 1e-10, k
+            assert rel_err(got[1][k], op) <= 1e-10, k
+            assert rel_err(got[2][k], oc) <= 1e-10, k
+    finally:
+        orc.set_threads(1)

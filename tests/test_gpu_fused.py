@@ -211,3 +211,20 @@ def test_tiles_and_z_runs_change_no_bit(orc, fuse):
             ref = (u[0], pi[0])
             assert rel_err(u[0], ou) <= TOL and rel_err(pi[0], op) <= TOL
         assert np.array_equal(u[0], ref[0]) and np.array_equal(pi[0], ref[1]), (tx, tz)
+
+
+def test_full_ensemble_vs_oracle(orc):
+    """The benchmark's ensemble (256 periodic cubes of edge 24-96, each with
+    its own fields and step size, one level, default tiles and form), two RK4
+    steps: every instance within the bar of the oracle."""
+    insts = W.ensemble()
+    lev = make_level(insts)
+    _, u, pi = run_gpu(insts, 2, 1, 0, lev=lev)
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        for k, inst in enumerate(insts):
+            ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 2)
+            assert rel_err(u[k], ou) <= TOL, k
+            assert rel_err(pi[k], op) <= TOL, k
+    finally:
+        orc.set_threads(1)
