@@ -109,6 +109,8 @@ int upload(T** dst, const std::vector<T>& v) {
   return SC_OK;
 }
 
+int check_lists(const sc_hierarchy* H);
+
 int build_lists(sc_hierarchy* H) {
   const sc_level* C = H->coarse;
   const sc_level* F = H->fine;
@@ -222,6 +224,42 @@ int build_lists(sc_hierarchy* H) {
       }
     }
   }
+  return check_lists(H);
+}
+
+// Host check of the device lists before upload: every element an entry
+// reads or writes lies in its level's field (fields hold field_size
+// elements).  A list built wrong fails here, not on the device.
+bool span_in(int64_t e0, int64_t sx, int64_t sy, int64_t sz, int64_t ex, int64_t ey, int64_t ez,
+             int64_t n) {
+  if (ex <= 0 || ey <= 0 || ez <= 0) return true;
+  return e0 >= 0 && e0 + (ex - 1) * sx + (ey - 1) * sy + (ez - 1) * sz < n;
+}
+
+int check_lists(const sc_hierarchy* H) {
+  const int64_t nc = H->coarse->field_size, nf = H->fine->field_size;
+  for (const dev::DProl& p : H->prol) {
+    // the fine targets, two apart along each axis
+    if (!span_in(p.dst, 2, 2 * (int64_t)p.dpy, 2 * (int64_t)p.dpz, p.ex, p.ey, p.ez, nf))
+      return set_error(SC_EINVAL, "internal: a prolongation target lies outside the fine field");
+    // the coarse stencil points of the first and the last target
+    const int64_t f0[3] = {p.fx0, p.fy0, p.fz0};
+    const int64_t f1[3] = {p.fx0 + 2 * (int64_t)(p.ex - 1), p.fy0 + 2 * (int64_t)(p.ey - 1),
+                           p.fz0 + 2 * (int64_t)(p.ez - 1)};
+    const int64_t lo = p.cbase + stencil_lo(f0[0]) + stencil_lo(f0[1]) * p.cpy +
+                       stencil_lo(f0[2]) * p.cpz;
+    const int64_t hi = p.cbase + (stencil_hi(f1[0]) - 1) + (stencil_hi(f1[1]) - 1) * p.cpy +
+                       (stencil_hi(f1[2]) - 1) * p.cpz;
+    if (lo < 0 || hi >= nc)
+      return set_error(SC_EINVAL, "internal: a prolongation stencil lies outside the coarse field");
+  }
+  for (const dev::DRect& r : H->blend)
+    if (!span_in(r.src, 1, r.spy, r.spz, r.ex, r.ey, r.ez, nc))
+      return set_error(SC_EINVAL, "internal: a coarse footprint lies outside the coarse field");
+  for (const dev::DRestr& q : H->restr)
+    if (!span_in(q.dst, 1, q.dpy, q.dpz, q.ex, q.ey, q.ez, nc) ||
+        !span_in(q.src, 2, 2 * (int64_t)q.spy, 2 * (int64_t)q.spz, q.ex, q.ey, q.ez, nf))
+      return set_error(SC_EINVAL, "internal: a restriction entry lies outside its fields");
   return SC_OK;
 }
 

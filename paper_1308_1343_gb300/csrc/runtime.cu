@@ -40,6 +40,21 @@ int upload(T** dst, const std::vector<T>& v) {
   return SC_OK;
 }
 
+// Host check of a device list entry before upload: the elements of an
+// ex x ey x ez rectangle with first element e0 and pitches (1, py, pz) (all
+// non-negative) lie in a field of n elements.  A list built wrong fails
+// here, on the host, instead of as an out-of-bounds access on the device.
+bool rect_in_field(int64_t e0, int64_t py, int64_t pz, int64_t ex, int64_t ey, int64_t ez,
+                   int64_t n) {
+  if (ex <= 0 || ey <= 0 || ez <= 0) return true;
+  return e0 >= 0 && e0 + (ex - 1) + (ey - 1) * py + (ez - 1) * pz < n;
+}
+
+int list_error(const char* what) {
+  return set_error(SC_EINVAL, std::string("internal: a ") + what +
+                                  " entry lies outside its field (please report)");
+}
+
 void add_chunks(int rect, int64_t n, std::vector<DChunk>& out, int chunk = dev::kChunk) {
   for (int64_t f = 0; f < n; f += chunk) out.push_back(DChunk{rect, (int)f});
 }
@@ -209,6 +224,10 @@ int ensure_device(sc_level* L) {
     }
     D->box_gchunks[nb] = (int)gchunks.size();
   }
+  for (const DRect& r : grects)
+    if (!rect_in_field(r.src, r.spy, r.spz, r.ex, r.ey, r.ez, L->field_size) ||
+        !rect_in_field(r.dst, r.dpy, r.dpz, r.ex, r.ey, r.ez, L->field_size))
+      return list_error("ghost-copy");
   rc = upload(&D->grects, grects);
   if (!rc) rc = upload(&D->gchunks, gchunks);
   if (rc) return rc;
@@ -251,6 +270,11 @@ int ensure_device(sc_level* L) {
       e.dbase = (int)index_of(C.dst_box, C.dst_lo);
       e.dpy = (int)L->py[C.dst_box];
       e.dpz = (int)L->pz[C.dst_box];
+      // the kernels read sources inside the source box and write dbase onward
+      if (e.lo0 < 0 || e.lo1 < 0 || e.lo2 < 0 || e.hi0 > Bs.hi[0] - Bs.lo[0] ||
+          e.hi1 > Bs.hi[1] - Bs.lo[1] || e.hi2 > Bs.hi[2] - Bs.lo[2] ||
+          !rect_in_field(e.dbase, e.dpy, e.dpz, C.ext[0], C.ext[1], C.ext[2], L->field_size))
+        return list_error("ghost-push");
       groups[(size_t)C.src_box * 6 + 2 * d + side].push_back(e);
     }
     std::vector<DPush> entries;
@@ -300,6 +324,12 @@ int ensure_device(sc_level* L) {
         add_chunks((int)srects.size() - 1, (int64_t)e[0] * e[1] * e[2], schunks);
       }
   }
+  for (const DRect& r : irects)
+    if (!rect_in_field(r.src, r.spy, r.spz, r.ex, r.ey, r.ez, L->field_size))
+      return list_error("interior-rectangle");
+  for (const DRect& r : srects)
+    if (!rect_in_field(r.src, r.spy, r.spz, r.ex, r.ey, r.ez, L->field_size))
+      return list_error("star-rectangle");
   rc = upload(&D->irects, irects);
   if (!rc) rc = upload(&D->ichunks, ichunks);
   if (!rc) rc = upload(&D->srects, srects);
