@@ -185,6 +185,22 @@ int sc_level_get_tuning(const sc_level* level, int32_t size_class, sc_tile* tile
 int sc_level_set_fusion(sc_level* level, int32_t stages_per_pass);
 int sc_level_get_fusion(const sc_level* level, int32_t* stages_per_pass);
 
+/* Staging of the one-stage kernel's raw stencil inputs (the column value
+ * two planes ahead and the tile's halo pairs), the GPU form of the paper's
+ * compile-time tuning parameters (Sec. 3.3, prefetching as an option):
+ *  SC_STAGING_REGISTERS: loaded to registers one plane ahead (46 KB of
+ *    shared memory, 4 CTAs per SM);
+ *  SC_STAGING_SHARED: copied to shared memory by cp.async with the
+ *    pointwise fields (62 KB, 3 CTAs per SM).
+ * Results are identical.  The two-stage pass kernels always stage in shared
+ * memory (registers are their scarce resource).  Setting it fixes it; until
+ * then sc_level_autotune times both for the one-stage form and keeps the
+ * faster.  Errors: SC_EINVAL for other values. */
+#define SC_STAGING_REGISTERS 0
+#define SC_STAGING_SHARED 1
+int sc_level_set_staging(sc_level* level, int32_t staging);
+int sc_level_get_staging(const sc_level* level, int32_t* staging);
+
 /* Number of box-size classes and the class of each box (boxes are grouped
  * by interior extent rounded up to a multiple of 8 per axis). */
 int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
@@ -198,7 +214,9 @@ int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
  * x the best time, and keeps the best.  Unless sc_level_set_fusion fixed
  * the form, it does so for one and for two RK4 stages per pass and keeps
  * the form whose step is faster (selecting between sets of loop kernels,
- * Sec. 3.3).  budget_ms bounds the total tuning time.  Results are applied
+ * Sec. 3.3); for the one-stage form it also times both stagings of its raw
+ * inputs (sc_level_set_staging) with the tuned tiles, unless fixed.
+ * budget_ms bounds the total tuning time.  Results are applied
  * to the level and, if cache_path is not NULL, merged into that on-disk
  * cache (keyed by GPU name, SM count, arithmetic, form and class extent)
  * and reused from it.  Synchronises the stream. */

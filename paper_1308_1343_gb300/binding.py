@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libsc_level.so")
 
 SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_EDEVICE, SC_ENOTSUP = 0, -1, -2, -3, -4, -5
 SC_ARITH_FP64, SC_ARITH_FIXED = 0, 1
+SC_STAGING_REGISTERS, SC_STAGING_SHARED = 0, 1
 SC_MODE_GRAPH, SC_MODE_PER_BOX, SC_MODE_BATCHED, SC_MODE_TIMED = 0, 1, 2, 3
 SC_SET_UNION, SC_SET_INTERSECTION, SC_SET_DIFFERENCE, SC_SET_XOR = 0, 1, 2, 3
 (SC_KERNEL_STAGE, SC_KERNEL_GATHER, SC_KERNEL_STAGE_RECORD, SC_KERNEL_ADJ_A, SC_KERNEL_ADJ_B,
@@ -62,6 +63,8 @@ _SIGS = {
     "sc_level_get_tuning": (_i32, [_vp, _i32, ctypes.POINTER(ScTile)]),
     "sc_level_set_fusion": (_i32, [_vp, _i32]),
     "sc_level_get_fusion": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "sc_level_set_staging": (_i32, [_vp, _i32]),
+    "sc_level_get_staging": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "sc_level_autotune": (_i32, [_vp, _i32, _dbl, _dbl, ctypes.c_char_p, _vp]),
     "sc_level_fill_ghosts": (_i32, [_vp, _vp, _vp]),
     "sc_level_apply_laplacian": (_i32, [_vp, _vp, _vp, _vp]),

@@ -170,7 +170,7 @@ struct Timer {
       if (L->fuse == 2)
         launch_pairs(n);
       else
-        dev::launch_fwd_stage(L->arith, false, a, D->grid_stage, s);
+        dev::launch_fwd_stage(L->arith, false, L->staging, a, D->grid_stage_s[L->staging], s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
       float ms = 0;
@@ -291,8 +291,19 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
     cache[key] = {best, tbest};
   }
   // the whole level with every class at its tuned tile
-  const double t = T.time(-1, Cand{0, 0}, 1e30);
+  double t = T.time(-1, Cand{0, 0}, 1e30);
   if (t >= 1e30) return -1.0;
+  // one stage per pass: the staging of the raw column and halo values too
+  // (registers or cp.async), for the whole level with the tuned tiles
+  if (L->fuse == 1 && !L->staging_fixed) {
+    const int s0 = L->staging;
+    L->staging = 1 - s0;
+    const double t1 = T.time(-1, Cand{0, 0}, 1e30);
+    if (t1 < t)
+      t = t1;
+    else
+      L->staging = s0;
+  }
   return L->fuse == 2 ? t : 4.0 * t;
 }
 

@@ -254,9 +254,12 @@ struct FwdEpi {
   }
 };
 
-template <class A, bool RECORD>
-__global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
-  __shared__ Smem<NT, A, 4> smem;
+// ASYNC: raw column and halo values staged by cp.async (62 KB of shared
+// memory, 3 CTAs per SM) instead of in registers (46 KB, 4 CTAs per SM); the
+// tuner picks one per level (sc_level_set_staging)
+template <class A, bool RECORD, bool ASYNC>
+__global__ void __launch_bounds__(NT, ASYNC ? 3 : 4) fwd_stage_kernel(FwdArgs a) {
+  __shared__ Smem<NT, A, 4, 1, false, ASYNC> smem;
   __shared__ unsigned red[NT / 32];
   if (A::kFixed) clear_slot(a.emax_clear, a.ndom);
   unsigned err = 0;
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(NT, 4) fwd_stage_kernel(FwdArgs a) {
     FwdEpi<A, RECORD> epi{{a.wp_in, a.yu, a.yp, a.q}, a.wu_out, a.wp_out, a.lapw, arith,
                           a.qk, cf.gamma, cf.rec};
     epi.emax = 0;
-    run_item<NT>(it, bx, a.wu_in, arith, smem, err, epi);
+    run_item<NT, A, FwdEpi<A, RECORD>, ASYNC>(it, bx, a.wu_in, arith, smem, err, epi);
     // ghost copies of the new w.u, the next stage's stencil input
     push_item<NT>(PushTab{a.push, a.push_gofs}, it, bx, a.wu_out);
     if (A::kFixed) cta_max_to(epi.emax, a.emax_out + bx.dom, red);
@@ -879,10 +882,14 @@ static void set_carveouts() {
   static bool done = false;
   if (done) return;
   done = true;
-  prefer_shared(fwd_stage_kernel<Fixed, true>);
-  prefer_shared(fwd_stage_kernel<Fixed, false>);
-  prefer_shared(fwd_stage_kernel<Fp64, true>);
-  prefer_shared(fwd_stage_kernel<Fp64, false>);
+  prefer_shared(fwd_stage_kernel<Fixed, true, false>);
+  prefer_shared(fwd_stage_kernel<Fixed, false, false>);
+  prefer_shared(fwd_stage_kernel<Fp64, true, false>);
+  prefer_shared(fwd_stage_kernel<Fp64, false, false>);
+  prefer_shared(fwd_stage_kernel<Fixed, true, true>);
+  prefer_shared(fwd_stage_kernel<Fixed, false, true>);
+  prefer_shared(fwd_stage_kernel<Fp64, true, true>);
+  prefer_shared(fwd_stage_kernel<Fp64, false, true>);
   // pass B keeps three planes of pointwise fields: two 108 KB CTAs per SM
   prefer_shared(pair_kernel<FixedI, true, false>);
   prefer_shared(pair_kernel<FixedI, true, true>);
@@ -904,22 +911,31 @@ static void set_carveouts() {
   prefer_shared(adj2_kernel<Fp64, true>);
 }
 
-cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
+template <bool ASYNC>
+static void launch_fwd_stage_t(int arith, bool record, const FwdArgs& a, int grid,
+                               cudaStream_t s) {
+  if (arith == 1) {
+    if (record)
+      fwd_stage_kernel<Fixed, true, ASYNC><<<grid, NT, 0, s>>>(a);
+    else
+      fwd_stage_kernel<Fixed, false, ASYNC><<<grid, NT, 0, s>>>(a);
+  } else {
+    if (record)
+      fwd_stage_kernel<Fp64, true, ASYNC><<<grid, NT, 0, s>>>(a);
+    else
+      fwd_stage_kernel<Fp64, false, ASYNC><<<grid, NT, 0, s>>>(a);
+  }
+}
+
+cudaError_t launch_fwd_stage(int arith, bool record, int staging, const FwdArgs& a, int grid,
                              cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
   set_carveouts();
   grid = min(grid, a.nitems);
-  if (arith == 1) {
-    if (record)
-      fwd_stage_kernel<Fixed, true><<<grid, NT, 0, s>>>(a);
-    else
-      fwd_stage_kernel<Fixed, false><<<grid, NT, 0, s>>>(a);
-  } else {
-    if (record)
-      fwd_stage_kernel<Fp64, true><<<grid, NT, 0, s>>>(a);
-    else
-      fwd_stage_kernel<Fp64, false><<<grid, NT, 0, s>>>(a);
-  }
+  if (staging == 1)
+    launch_fwd_stage_t<true>(arith, record, a, grid, s);
+  else
+    launch_fwd_stage_t<false>(arith, record, a, grid, s);
   return cudaGetLastError();
 }
 
@@ -1023,13 +1039,17 @@ cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchun
 
 int stage_threads() { return NT; }
 
-cudaError_t stage_occupancy(int arith, int* blocks_per_sm) {
+cudaError_t stage_occupancy(int arith, int staging, int* blocks_per_sm) {
   set_carveouts();
-  if (arith == 1)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, fwd_stage_kernel<Fixed, false>, NT, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                       fwd_stage_kernel<Fp64, false>, NT, 0);
+  if (staging == 1)
+    return arith == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            blocks_per_sm, fwd_stage_kernel<Fixed, false, true>, NT, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            blocks_per_sm, fwd_stage_kernel<Fp64, false, true>, NT, 0);
+  return arith == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          blocks_per_sm, fwd_stage_kernel<Fixed, false, false>, NT, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          blocks_per_sm, fwd_stage_kernel<Fp64, false, false>, NT, 0);
 }
 
 }  // namespace dev

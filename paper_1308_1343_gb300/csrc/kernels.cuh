@@ -291,15 +291,16 @@ struct TileSmem {
 
 // NS stencil fields share the traversal (one pipeline, one barrier per
 // plane); field f uses tile buffers 2f and 2f+1.  A deferred epilogue (see
-// run_items) keeps three planes of pointwise fields instead of two.
-template <int NT, class A, int NF, int NS = 1, bool DEFER = false>
+// run_items) keeps three planes of pointwise fields instead of two.  ASYNC:
+// the raw column and halo values are staged in shared memory by cp.async
+// (the default with several stencil fields) instead of in registers.
+template <int NT, class A, int NF, int NS = 1, bool DEFER = false, bool ASYNC = (NS > 1)>
 struct Smem {
   typename A::T tile[2 * NS * TileSmem<NT>::kMaxElems];
   double2 pw[DEFER ? 3 : 2][NF > 0 ? NF : 1][NT];
-  // raw halo pairs and raw column pairs staged by cp.async (several stencil
-  // fields only)
-  double2 hraw[2][NS][NS > 1 ? NT : 1];
-  double2 craw[2][NS][NS > 1 ? NT : 1];
+  // raw halo pairs and raw column pairs staged by cp.async
+  double2 hraw[2][NS][ASYNC ? NT : 1];
+  double2 craw[2][NS][ASYNC ? NT : 1];
 };
 
 // Epi::kDefer if the epilogue declares it, else false
@@ -341,10 +342,11 @@ __device__ __forceinline__ int out_of(int c, int n) {
 // may be deferred (Epi::kDefer): plane k's runs after plane k+1's
 // conversions, before its barrier, which shortens the register lifetimes
 // around the stencil; the arithmetic and its results are unchanged.
-template <int NT, int NS, class A, class Epi>
+template <int NT, int NS, class A, class Epi, bool ASYNC = (NS > 1)>
 __device__ __forceinline__ void run_items(
     const DItem& it, const DBox& bx, const double* const (&F)[NS], const A (&arith)[NS],
-    Smem<NT, A, Epi::NF, NS, (NS > 1 && DeferOf<Epi>::value)>& sm, unsigned& err, Epi& epi) {
+    Smem<NT, A, Epi::NF, NS, (NS > 1 && DeferOf<Epi>::value), ASYNC>& sm, unsigned& err,
+    Epi& epi) {
   using T = typename A::T;
   using T2 = typename A::T2;
   constexpr int NF = Epi::NF;
@@ -417,11 +419,11 @@ __device__ __forceinline__ void run_items(
     return arith[f].conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
   };
 
-  // With several stencil fields the raw halo pairs of plane k and column
-  // pairs of plane k+2 travel by cp.async with the pointwise fields of plane
-  // k (registers are the scarce resource there); with one they are loaded to
-  // registers a plane ahead.
-  constexpr bool kAsyncHalo = NS > 1;
+  // The raw halo pairs of plane k and column pairs of plane k+2 travel by
+  // cp.async with the pointwise fields of plane k (ASYNC: the default with
+  // several stencil fields, where registers are the scarce resource), or
+  // are loaded to registers a plane ahead.
+  constexpr bool kAsyncHalo = ASYNC;
   constexpr bool kDefer = kAsyncHalo && DeferOf<Epi>::value;
 
   // running element offsets (advance by one plane per iteration)
@@ -592,14 +594,15 @@ struct OneField {
   }
 };
 
-template <int NT, class A, class Epi>
+template <int NT, class A, class Epi, bool ASYNC = false>
 __device__ __forceinline__ void run_item(const DItem& it, const DBox& bx,
                                          const double* __restrict__ F, A arith,
-                                         Smem<NT, A, Epi::NF>& sm, unsigned& err, Epi& epi) {
+                                         Smem<NT, A, Epi::NF, 1, false, ASYNC>& sm,
+                                         unsigned& err, Epi& epi) {
   const double* const Fs[1] = {F};
   const A as[1] = {arith};
   OneField<Epi> one{epi, epi.f};
-  run_items<NT, 1>(it, bx, Fs, as, sm, err, one);
+  run_items<NT, 1, A, OneField<Epi>, ASYNC>(it, bx, Fs, as, sm, err, one);
 }
 
 // Largest biased exponents of two fields over the CTA, one atomicMax per CTA

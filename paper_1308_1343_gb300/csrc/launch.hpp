@@ -145,7 +145,9 @@ cudaError_t launch_qprep(const DRect* rects, const DChunk* chunks, int nchunks,
 cudaError_t launch_misfit(const DRect* rects, const DChunk* chunks, int nchunks,
                           const double* u, const double* uo, double* seed, const double* h3,
                           double* partial, double* loss, int grid, cudaStream_t s);
-cudaError_t launch_fwd_stage(int arith, bool record, const FwdArgs& a, int grid,
+// staging: 0 raw column and halo values in registers, 1 in shared memory by
+// cp.async
+cudaError_t launch_fwd_stage(int arith, bool record, int staging, const FwdArgs& a, int grid,
                              cudaStream_t s);
 cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s);
@@ -171,7 +173,7 @@ cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchun
                             const double* fu, const double* fp, double* cu, double* cp,
                             unsigned* emax, cudaStream_t s);
 int stage_threads();
-cudaError_t stage_occupancy(int arith, int* blocks_per_sm);
+cudaError_t stage_occupancy(int arith, int staging, int* blocks_per_sm);
 
 }  // namespace dev
 }  // namespace sc

@@ -104,6 +104,7 @@ struct DeviceState {
   size_t ev_used = 0;
   std::vector<int> ev_kind;  // SC_KERNEL_* of each timed launch
   int grid_stage = 0;  // persistent grid of the stage kernels
+  int grid_stage_s[2] = {0, 0};  // of the one-stage kernel per staging
   int grid_pair = 0;   // persistent grid of the two-stage kernels
   int grid_small = 0;  // grid of the gather / reduction kernels
 };
@@ -121,6 +122,9 @@ struct sc_level {
   int arith = SC_ARITH_FIXED;
   int fuse = 2;             // RK4 stages per stencil pass of sc_level_rk4_step: 1 or 2
   bool fuse_fixed = false;  // set by sc_level_set_fusion; else the autotuner chooses
+  int staging = 0;             // one-stage kernel: raw values in registers (0) or
+                               // in shared memory by cp.async (1)
+  bool staging_fixed = false;  // set by sc_level_set_staging; else the autotuner chooses
   int ctas_per_sm = 0;
   int version = 0;  // bumps when items change (invalidates graphs)
   int64_t launches = 0;

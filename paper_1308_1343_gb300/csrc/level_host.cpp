@@ -302,6 +302,21 @@ int sc_level_get_fusion(const sc_level* L, int32_t* stages_per_pass) {
   return SC_OK;
 }
 
+int sc_level_set_staging(sc_level* L, int32_t staging) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (staging != SC_STAGING_REGISTERS && staging != SC_STAGING_SHARED)
+    return set_error(SC_EINVAL, "staging must be SC_STAGING_REGISTERS or SC_STAGING_SHARED");
+  L->staging = staging;  // the step graphs are keyed by it
+  L->staging_fixed = true;
+  return SC_OK;
+}
+
+int sc_level_get_staging(const sc_level* L, int32_t* staging) {
+  if (!L || !staging) return set_error(SC_EINVAL, "NULL argument");
+  *staging = L->staging;
+  return SC_OK;
+}
+
 int sc_level_get_tuning(const sc_level* L, int32_t size_class, sc_tile* tile) {
   if (!L || !tile) return set_error(SC_EINVAL, "NULL argument");
   if (size_class < 0 || size_class >= (int32_t)L->classes.size())

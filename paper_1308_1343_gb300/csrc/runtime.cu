@@ -90,10 +90,13 @@ void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, 
 
 int upload_items(sc_level* L) {
   DeviceState* D = L->dev;
-  int occ = 0;
-  SC_CUDA(dev::stage_occupancy(L->arith, &occ));
-  const int per_sm = L->ctas_per_sm > 0 ? L->ctas_per_sm : std::max(1, occ);
-  D->grid_stage = D->sms * per_sm;
+  for (int st = 0; st < 2; ++st) {
+    int occ = 0;
+    SC_CUDA(dev::stage_occupancy(L->arith, st, &occ));
+    D->grid_stage_s[st] = D->sms * (L->ctas_per_sm > 0 ? L->ctas_per_sm : std::max(1, occ));
+  }
+  // register staging: also the grid of the Laplacian kernel
+  D->grid_stage = D->grid_stage_s[0];
   int occ2 = 0;
   SC_CUDA(dev::pair_occupancy(L->arith, &occ2));
   D->grid_pair = D->sms * std::max(1, occ2);
@@ -512,14 +515,16 @@ static cudaError_t enq_fwd(const Enq& q, dev::FwdArgs a, bool record) {
     a.nitems = D->nitems;
     (*q.count)++;
     TimedLaunch t(q, record ? SC_KERNEL_STAGE_RECORD : SC_KERNEL_STAGE);
-    return dev::launch_fwd_stage(q.L->arith, record, a, D->grid_stage, q.s);
+    return dev::launch_fwd_stage(q.L->arith, record, q.L->staging, a,
+                                 D->grid_stage_s[q.L->staging], q.s);
   }
   for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
     a.items = D->items + D->box_items[b];
     a.nitems = D->box_items[b + 1] - D->box_items[b];
     (*q.count)++;
     TimedLaunch t(q, record ? SC_KERNEL_STAGE_RECORD : SC_KERNEL_STAGE);
-    cudaError_t e = dev::launch_fwd_stage(q.L->arith, record, a, D->grid_stage, q.s);
+    cudaError_t e = dev::launch_fwd_stage(q.L->arith, record, q.L->staging, a,
+                                          D->grid_stage_s[q.L->staging], q.s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -743,7 +748,7 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     return SC_OK;
   }
   auto key = std::make_tuple((const void*)u, (const void*)pi, (const void*)c2,
-                             L->arith + 2 * L->fuse, L->version);
+                             L->arith + 2 * L->fuse + 4 * L->staging, L->version);
   auto it = D->graphs.find(key);
   if (it == D->graphs.end()) {
     if (D->graphs.size() >= 16) {  // bounded cache: drop the oldest-keyed graphs

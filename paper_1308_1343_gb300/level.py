@@ -204,6 +204,16 @@ class Level:
         B.check(B.lib().sc_level_get_fusion(self._h, ctypes.byref(n)))
         return n.value
 
+    def set_staging(self, staging: int):
+        """Staging of the one-stage kernel's raw inputs: 0 registers, 1 shared
+        memory by cp.async (binding.SC_STAGING_*)."""
+        B.check(B.lib().sc_level_set_staging(self._h, int(staging)))
+
+    def get_staging(self) -> int:
+        n = ctypes.c_int32()
+        B.check(B.lib().sc_level_get_staging(self._h, ctypes.byref(n)))
+        return n.value
+
     def autotune(self, seed: int = 0, budget_ms: float = 2000.0, abort_factor: float = 2.0,
                  cache_path: Optional[str] = None, stream=None):
         cp = cache_path.encode() if cache_path else None

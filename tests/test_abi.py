@@ -313,6 +313,13 @@ def test_fusion_setting_and_tile_query(B):
         with pytest.raises(B.ScError, match="stages_per_pass"):
             lev.set_fusion(bad)
     assert lev.get_fusion() == 2
+    assert lev.get_staging() == B.SC_STAGING_REGISTERS
+    lev.set_staging(B.SC_STAGING_SHARED)
+    assert lev.get_staging() == B.SC_STAGING_SHARED
+    for bad in (2, -1):
+        with pytest.raises(B.ScError, match="staging"):
+            lev.set_staging(bad)
+    assert lev.get_staging() == B.SC_STAGING_SHARED
     tx, ty, tz = lev.get_tuning(0)
     assert tx in (16, 32, 64) and tx * ty == 512 and tz >= 1
     lev.set_tuning(0, 32, 12)

@@ -228,3 +228,33 @@ def test_full_ensemble_vs_oracle(orc):
             assert rel_err(pi[k], op) <= TOL, k
     finally:
         orc.set_threads(1)
+
+
+def test_stagings_change_no_bit(orc):
+    """One stage per pass with the raw stencil inputs staged in registers or
+    in shared memory by cp.async: the same bits, on a ragged multi-box level
+    and on a self-periodic box, in every launch mode; and the autotuner,
+    free to choose the staging, keeps the bits too."""
+    from paper_1308_1343_gb300 import binding as B
+    uneven = W.uneven_level(n=(96, 80, 64), h=1.0 / 64, levels=4, seed=3, box_seed=30)
+    single = W.bumpy_instance(W.Domain((44, 38, 30), 1.0 / 38), 6)
+    for inst in (uneven, single):
+        ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 3)
+        ref = None
+        for staging in (B.SC_STAGING_REGISTERS, B.SC_STAGING_SHARED):
+            for mode in (0, 1, 2):
+                lev = make_level([inst])
+                lev.set_fusion(1)
+                lev.set_staging(staging)
+                _, u, pi = run_gpu([inst], 3, 1, mode, lev=lev)
+                if ref is None:
+                    ref = (u[0], pi[0])
+                    assert rel_err(u[0], ou) <= TOL and rel_err(pi[0], op) <= TOL
+                assert np.array_equal(u[0], ref[0]) and np.array_equal(pi[0], ref[1]), \
+                    (staging, mode)
+        lev = make_level([inst])
+        lev.set_fusion(1)
+        lev.autotune(seed=3, budget_ms=200.0)
+        assert lev.get_staging() in (B.SC_STAGING_REGISTERS, B.SC_STAGING_SHARED)
+        _, u, pi = run_gpu([inst], 3, 1, 0, lev=lev)
+        assert np.array_equal(u[0], ref[0]) and np.array_equal(pi[0], ref[1])
