@@ -326,3 +326,22 @@ def test_fusion_setting_and_tile_query(B):
     assert lev.get_tuning(0) == (32, 16, 12)
     with pytest.raises(B.ScError, match="bad class"):
         lev.get_tuning(1)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the compiled library the Python API raises at the first call:
+    there is no CPU path to fall back to."""
+    import subprocess
+    import sys
+    code = (
+        "from paper_1308_1343_gb300 import binding as B\n"
+        "B.LIB_PATH = %r\n"
+        "from paper_1308_1343_gb300.level import Level\n"
+        "Level([((0, 0, 0), (8, 8, 8), 0)],\n"
+        "      [dict(lo=(0, 0, 0), hi=(8, 8, 8), h=1 / 8, periodic=7)])\n"
+    ) % str(tmp_path / "libsc_level.so")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode != 0
+    assert "libsc_level.so is missing" in r.stderr
+    assert "no CPU fallback" in r.stderr
