@@ -150,6 +150,8 @@ void release_device(sc_level* L) {
   L->dev = nullptr;
 }
 
+static int init_device(sc_level* L, int cur);
+
 int ensure_device(sc_level* L) {
   int cur = -1;
   SC_CUDA(cudaGetDevice(&cur));
@@ -158,6 +160,18 @@ int ensure_device(sc_level* L) {
       return set_error(SC_EINVAL, "level was set up on another device");
     return SC_OK;
   }
+  // a failed set-up leaves no partial device state behind: the next call
+  // starts again from nothing (the error message of this one is kept)
+  const int rc = init_device(L, cur);
+  if (rc) {
+    const std::string msg = sc_last_error();
+    release_device(L);
+    set_error(rc, msg);
+  }
+  return rc;
+}
+
+static int init_device(sc_level* L, int cur) {
   DeviceState* D = new DeviceState();
   L->dev = D;
   D->device = cur;
@@ -751,7 +765,7 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
                              L->arith + 2 * L->fuse + 4 * L->staging, L->version);
   auto it = D->graphs.find(key);
   if (it == D->graphs.end()) {
-    if (D->graphs.size() >= 16) {  // bounded cache: drop the oldest-keyed graphs
+    if (D->graphs.size() >= 16) {  // bounded cache: start it afresh
       SC_CUDA(cudaStreamSynchronize(s));
       for (auto& kv : D->graphs) cudaGraphExecDestroy(kv.second.first);
       D->graphs.clear();
@@ -762,7 +776,10 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     cudaError_t e = step(cq);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(D->capture, &g);
-    if (e != cudaSuccess) return cuda_fail(e, "capture of the RK4 step");
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e, "capture of the RK4 step");
+    }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
