@@ -116,12 +116,16 @@ int upload_items(sc_level* L) {
     if (!any) break;
     build_items(L, items, D->box_items);
   }
-  int rc = upload(&D->items, items);
-  if (rc) return rc;
-  D->nitems = (int)items.size();
+  // the captured graphs name the old list: drop them first, so that a failed
+  // upload leaves an empty list and no graph that reads freed memory
+  SC_CUDA(cudaDeviceSynchronize());
   for (auto& kv : D->graphs) cudaGraphExecDestroy(kv.second.first);
   D->graphs.clear();
   L->version++;
+  D->nitems = 0;
+  int rc = upload(&D->items, items);
+  if (rc) return rc;
+  D->nitems = (int)items.size();
   return SC_OK;
 }
 
@@ -396,8 +400,8 @@ int get_field(sc_level* L, const std::string& name, double** p) {
     cudaGetLastError();
     return set_error(SC_ENOMEM, "device allocation of scratch field '" + name + "' failed");
   }
+  D->fields[name] = q;  // owned by the level from here, freed with it
   SC_CUDA(cudaMemset(q, 0, sizeof(double) * L->field_size));
-  D->fields[name] = q;
   *p = q;
   return SC_OK;
 }
