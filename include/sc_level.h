@@ -25,7 +25,9 @@
  *    is available from sc_last_error() on the calling thread.  No function
  *    aborts the process, and no kernel traps: device-side problems set a
  *    device error word that the next synchronising call reports as
- *    SC_EDEVICE.
+ *    SC_EDEVICE.  The device state of a level (work lists, coefficients)
+ *    is built by its first device call; if that set-up fails, nothing of it
+ *    is kept and the next call builds it again.
  *  - Field buffers are caller-owned DEVICE pointers (e.g. torch tensors) of
  *    sc_level_field_size() doubles, 16-byte aligned, in the level layout
  *    below.  The library owns the level object and all of its scratch memory
