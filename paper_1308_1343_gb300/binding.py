@@ -10,7 +10,8 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsc_level.so")
+# SC_LEVEL_LIB selects another build of the library (the checked build)
+LIB_PATH = os.environ.get("SC_LEVEL_LIB") or os.path.join(HERE, "libsc_level.so")
 
 SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_EDEVICE, SC_ENOTSUP = 0, -1, -2, -3, -4, -5
 SC_ARITH_FP64, SC_ARITH_FIXED = 0, 1

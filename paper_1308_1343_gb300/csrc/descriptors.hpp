@@ -91,6 +91,7 @@ constexpr int kGatherChunk = 256;  // ghost gather: one point per thread
 // Error bits of the device error word.
 constexpr unsigned kErrNonFinite = 1u;   // Inf/NaN reached the fixed-point path
 constexpr unsigned kErrScale = 2u;       // an input exceeded its domain bound
+constexpr unsigned kErrBounds = 4u;      // checked build: an index left its box
 
 }  // namespace dev
 }  // namespace sc

@@ -33,6 +33,11 @@
 //    int64 and is rounded to FP64 once.  Each input is off by less than
 //    2^-S <= 2^-54 * max|x|.  This moves the sum from GB300's narrow FP64
 //    pipe to the integer pipes; the RK updates stay FP64 FMAs.
+//
+// Checked build (SC_BOUNDS_CHECK defined): the traversal verifies every
+// element index it loads from or hands to an epilogue against the item's
+// box (see run_items) and records a failure as kErrBounds in the error word
+// instead of making the access.  Release builds compile the checks out.
 #pragma once
 
 #include <cstdint>
@@ -373,6 +378,31 @@ __device__ __forceinline__ void run_items(
   // fewer than 2^31 doubles); columns outside the padded box read the box's
   // interior corner instead (in bounds, masked off below, never used)
   const int off0 = (int)bx.off, py = (int)bx.py;
+#ifdef SC_BOUNDS_CHECK
+  // a 16-byte pair at element i must lie in the box's padded block (x from
+  // -2 to the end of the row's padding, y and z from -2 to n+1); one that
+  // does not is replaced by the interior corner and flagged
+  const int blk0 = off0 - 2 - 2 * py - 2 * pz;
+  const int blk1 = off0 - 3 + py + (bx.ny + 1) * py + (bx.nz + 1) * pz;
+  auto ck = [&](int i) {
+    if (i < blk0 || i + 1 > blk1) {
+      err |= kErrBounds;
+      return off0;
+    }
+    return i;
+  };
+  // the point(s) handed to the epilogue: interior, at the element index the
+  // coordinates give; otherwise the call is skipped and flagged
+  auto ok_pt = [&](int i, int x, int y, int z, bool two) {
+    const bool ok = x >= 0 && x + (two ? 1 : 0) < bx.nx && y >= 0 && y < bx.ny && z >= 0 &&
+                    z < bx.nz && i == off0 + x + y * py + z * pz;
+    if (!ok) err |= kErrBounds;
+    return ok;
+  };
+#else
+  auto ck = [](int i) { return i; };
+  auto ok_pt = [](int, int, int, int, bool) { return true; };
+#endif
   const int colOff = colLoad ? off0 + wr(gx, bx.nx) + wr(gy, bx.ny) * py : off0;
   const int oy = out_of(gy, bx.ny);
   const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
@@ -435,15 +465,15 @@ __device__ __forceinline__ void run_items(
   auto stage_pw = [&](int buf, int pbuf) {
     if (actA) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async16(&sm.pw[pbuf][f][tid], epi.f[f] + op);
+      for (int f = 0; f < NF; ++f) cp_async16(&sm.pw[pbuf][f][tid], epi.f[f] + ck(op));
     }
     if (kAsyncHalo) {
       const int t = kAsyncHalo ? tid : 0;
 #pragma unroll
       for (int f = 0; f < NS; ++f)
-        if (mine(f)) cp_async16(&sm.hraw[buf][f][t], F[f] + oh);
+        if (mine(f)) cp_async16(&sm.hraw[buf][f][t], F[f] + ck(oh));
 #pragma unroll
-      for (int f = 0; f < NS; ++f) cp_async16(&sm.craw[buf][f][t], F[f] + oc);
+      for (int f = 0; f < NS; ++f) cp_async16(&sm.craw[buf][f][t], F[f] + ck(oc));
       oh += pz;
       oc += pz;
     }
@@ -455,13 +485,13 @@ __device__ __forceinline__ void run_items(
   double2 rc[NS], rh[NS];  // raw column of plane k+2, raw halo pair of plane k
 #pragma unroll
   for (int f = 0; f < NS; ++f) {
-    qa[f] = conv_at(f, ld2(F[f] + oc - 4 * pz), it.z0 - 2);
-    qb[f] = conv_at(f, ld2(F[f] + oc - 3 * pz), it.z0 - 1);
-    qc[f] = conv_at(f, ld2(F[f] + oc - 2 * pz), it.z0);
-    qd[f] = conv_at(f, ld2(F[f] + oc - pz), it.z0 + 1);
+    qa[f] = conv_at(f, ld2(F[f] + ck(oc - 4 * pz)), it.z0 - 2);
+    qb[f] = conv_at(f, ld2(F[f] + ck(oc - 3 * pz)), it.z0 - 1);
+    qc[f] = conv_at(f, ld2(F[f] + ck(oc - 2 * pz)), it.z0);
+    qd[f] = conv_at(f, ld2(F[f] + ck(oc - pz)), it.z0 + 1);
     if (!kAsyncHalo) {
-      rc[f] = ld2(F[f] + oc);
-      rh[f] = ld2(F[f] + oh);
+      rc[f] = ld2(F[f] + ck(oc));
+      rh[f] = ld2(F[f] + ck(oh));
     }
   }
   if (!kAsyncHalo) {
@@ -494,8 +524,8 @@ __device__ __forceinline__ void run_items(
       if (!kAsyncHalo) {
 #pragma unroll
         for (int f = 0; f < NS; ++f) {
-          rc[f] = ld2(F[f] + oc);
-          rh[f] = ld2(F[f] + oh);
+          rc[f] = ld2(F[f] + ck(oc));
+          rh[f] = ld2(F[f] + ck(oh));
         }
         oc += pz;
         oh += pz;
@@ -516,7 +546,7 @@ __device__ __forceinline__ void run_items(
         p2[f] = conv_at(f, sm.craw[kk & 1][f][t], k + 2);
       }
     }
-    if (kDefer && kk > 0 && actA) {
+    if (kDefer && kk > 0 && actA && ok_pt(oi - pz, gx, gy, k - 1, actB)) {
       const int pb = b3 == 0 ? 2 : b3 - 1;
       double2 pw[NF > 0 ? NF : 1];
 #pragma unroll
@@ -547,7 +577,7 @@ __device__ __forceinline__ void run_items(
           sA[f] = rA[f];
           sB[f] = rB[f];
         }
-      } else {
+      } else if (ok_pt(oi, gx, gy, k, actB)) {
         double2 pw[NF > 0 ? NF : 1];
 #pragma unroll
         for (int f = 0; f < NF; ++f) pw[f] = sm.pw[kk & 1][f][tid];
@@ -570,7 +600,7 @@ __device__ __forceinline__ void run_items(
     plane(kk, qe, qa, qb, qc, qd);
     if (++kk >= it.nzr) break;
   }
-  if (kDefer && actA) {
+  if (kDefer && actA && ok_pt(oi - pz, gx, gy, it.z0 + it.nzr - 1, actB)) {
     const int pb = b3 == 0 ? 2 : b3 - 1;
     double2 pw[NF > 0 ? NF : 1];
 #pragma unroll

@@ -916,6 +916,7 @@ int sc_level_sync(sc_level* L, void* stream) {
     std::string m = "device error word set:";
     if (e & dev::kErrNonFinite) m += " non-finite value in the fixed-point Laplacian;";
     if (e & dev::kErrScale) m += " input above its domain's exponent bound;";
+    if (e & dev::kErrBounds) m += " index outside its box (checked build);";
     return set_error(SC_EDEVICE, m);
   }
   return SC_OK;
