@@ -29,6 +29,41 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+def _field(t, n: int, name: str, optional: bool = False) -> Optional[int]:
+    """Device pointer of a field tensor after the checks the C ABI cannot
+    make (it sees only a pointer): a contiguous float64 CUDA tensor on the
+    current device holding at least n elements.  Raises ValueError or
+    TypeError otherwise, before any kernel could read or write past it."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError("%s: a field tensor is required" % name)
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s: expected a torch tensor, got %s" % (name, type(t).__name__))
+    if t.dtype != torch.float64:
+        raise ValueError("%s: dtype %s, fields are float64" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s: not contiguous" % name)
+    if t.numel() < n:
+        raise ValueError("%s: %d elements, the level's fields hold %d" % (name, t.numel(), n))
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError("%s: on %s, not on the current CUDA device" % (name, t.device))
+    return t.data_ptr()
+
+
+def _host_field(a, n: int, name: str) -> int:
+    """Address of a host field buffer: a C-contiguous float64 numpy array of
+    exactly n elements."""
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64:
+        raise ValueError("%s: expected a float64 numpy array" % name)
+    if not a.flags.c_contiguous or a.size != n:
+        raise ValueError("%s: expected a contiguous array of %d elements" % (name, n))
+    if name.endswith("_out") and not a.flags.writeable:
+        raise ValueError("%s: not writeable" % name)
+    return a.ctypes.data
+
+
 def _stream(stream) -> Optional[int]:
     torch = _torch()
     if stream is None:
@@ -226,59 +261,69 @@ class Level:
         a = np.atleast_1d(np.asarray(dt, dtype=np.float64))
         return (ctypes.c_double * len(a))(*a), len(a)
 
+    def _f(self, t, name, optional=False):
+        return _field(t, self.field_size, name, optional)
+
     def fill_ghosts(self, field, stream=None):
-        B.check(B.lib().sc_level_fill_ghosts(self._h, _ptr(field), _stream(stream)))
+        B.check(B.lib().sc_level_fill_ghosts(self._h, self._f(field, "field"), _stream(stream)))
 
     def apply_laplacian(self, u, out, stream=None):
-        B.check(B.lib().sc_level_apply_laplacian(self._h, _ptr(u), _ptr(out), _stream(stream)))
+        B.check(B.lib().sc_level_apply_laplacian(self._h, self._f(u, "u"), self._f(out, "out"),
+                                                 _stream(stream)))
 
     def rk4_step(self, u, pi, c2, dt, nsteps: int, mode: int = B.SC_MODE_GRAPH, stream=None):
         d, nd = self._dt(dt)
-        B.check(B.lib().sc_level_rk4_step(self._h, _ptr(u), _ptr(pi), _ptr(c2), d, nd,
-                                          int(nsteps), int(mode), _stream(stream)))
+        B.check(B.lib().sc_level_rk4_step(self._h, self._f(u, "u"), self._f(pi, "pi"),
+                                          self._f(c2, "c2"), d, nd, int(nsteps), int(mode),
+                                          _stream(stream)))
 
     def rk4_step_host(self, u: np.ndarray, pi: np.ndarray, c2: np.ndarray, dt, nsteps: int,
                       u_out: Optional[np.ndarray] = None, pi_out: Optional[np.ndarray] = None,
                       stream=None):
         """End to end from host buffers (ideally pinned); returns (u, pi)."""
-        for a in (u, pi, c2):
-            assert a.dtype == np.float64 and a.size == self.field_size
+        n = self.field_size
         u_out = np.empty_like(u) if u_out is None else u_out
         pi_out = np.empty_like(pi) if pi_out is None else pi_out
-        d, nd = self._dt(dt)
         vp = ctypes.c_void_p
-        B.check(B.lib().sc_level_rk4_step_host(
-            self._h, vp(u.ctypes.data), vp(pi.ctypes.data), vp(c2.ctypes.data),
-            vp(u_out.ctypes.data), vp(pi_out.ctypes.data), d, nd, int(nsteps), _stream(stream)))
+        ptrs = [vp(_host_field(a, n, name)) for a, name in
+                ((u, "u"), (pi, "pi"), (c2, "c2"), (u_out, "u_out"), (pi_out, "pi_out"))]
+        d, nd = self._dt(dt)
+        B.check(B.lib().sc_level_rk4_step_host(self._h, *ptrs, d, nd, int(nsteps),
+                                               _stream(stream)))
         return u_out, pi_out
 
     def misfit(self, u, u_obs, seed=None, stream=None):
         """(loss device scalar, seed) with seed = h^3 (u - u_obs)."""
         torch = _torch()
+        pu, po = self._f(u, "u"), self._f(u_obs, "u_obs")
+        ps = self._f(seed, "seed", optional=True)
         loss = torch.zeros(2, dtype=torch.float64, device=u.device)[:1]
-        B.check(B.lib().sc_level_misfit(self._h, _ptr(u), _ptr(u_obs), _ptr(loss), _ptr(seed),
-                                        _stream(stream)))
+        B.check(B.lib().sc_level_misfit(self._h, pu, po, _ptr(loss), ps, _stream(stream)))
         return loss[0], seed
 
     def forward_tape(self, u0, pi0, c2, dt, nsteps: int, ckpt_every: int, u_T=None, pi_T=None,
                      stream=None):
         d, nd = self._dt(dt)
-        B.check(B.lib().sc_level_forward_tape(self._h, _ptr(u0), _ptr(pi0), _ptr(c2), d, nd,
-                                              int(nsteps), int(ckpt_every), _ptr(u_T),
-                                              _ptr(pi_T), _stream(stream)))
+        f = self._f
+        B.check(B.lib().sc_level_forward_tape(
+            self._h, f(u0, "u0"), f(pi0, "pi0"), f(c2, "c2"), d, nd, int(nsteps),
+            int(ckpt_every), f(u_T, "u_T", True), f(pi_T, "pi_T", True), _stream(stream)))
 
     def backward_tape(self, c2, gu_T, gpi_T, g_u0, g_pi0, g_c2, stream=None):
-        B.check(B.lib().sc_level_backward_tape(self._h, _ptr(c2), _ptr(gu_T), _ptr(gpi_T),
-                                               _ptr(g_u0), _ptr(g_pi0), _ptr(g_c2),
-                                               _stream(stream)))
+        f = self._f
+        B.check(B.lib().sc_level_backward_tape(
+            self._h, f(c2, "c2"), f(gu_T, "gu_T", True), f(gpi_T, "gpi_T", True),
+            f(g_u0, "g_u0"), f(g_pi0, "g_pi0"), f(g_c2, "g_c2"), _stream(stream)))
 
     def grad(self, u0, pi0, c2, dt, nsteps, ckpt_every, gu_T, gpi_T, g_u0, g_pi0, g_c2,
              u_T=None, pi_T=None, stream=None):
         d, nd = self._dt(dt)
-        B.check(B.lib().sc_level_grad(self._h, _ptr(u0), _ptr(pi0), _ptr(c2), d, nd,
-                                      int(nsteps), int(ckpt_every), _ptr(gu_T), _ptr(gpi_T),
-                                      _ptr(g_u0), _ptr(g_pi0), _ptr(g_c2), _ptr(u_T),
-                                      _ptr(pi_T), _stream(stream)))
+        f = self._f
+        B.check(B.lib().sc_level_grad(
+            self._h, f(u0, "u0"), f(pi0, "pi0"), f(c2, "c2"), d, nd, int(nsteps),
+            int(ckpt_every), f(gu_T, "gu_T", True), f(gpi_T, "gpi_T", True),
+            f(g_u0, "g_u0"), f(g_pi0, "g_pi0"), f(g_c2, "g_c2"),
+            f(u_T, "u_T", True), f(pi_T, "pi_T", True), _stream(stream)))
 
     def kernel_times(self):
         """(stage_ms, stage_launches, gather_ms, gather_launches) of the last
@@ -375,17 +420,26 @@ class Hierarchy:
         """Coarse (x, y, z) points that restriction sets."""
         return self._points(B.lib().sc_hierarchy_restriction_points)
 
+    def _c(self, t, name):
+        return _field(t, self.coarse.field_size, name)
+
+    def _fn(self, t, name):
+        return _field(t, self.fine.field_size, name)
+
     def prolongate(self, u0, u1, p0, p1, alpha: float, fu, fpi, stream=None):
-        B.check(B.lib().sc_hierarchy_prolongate(self._h, _ptr(u0), _ptr(u1), _ptr(p0), _ptr(p1),
-                                                float(alpha), _ptr(fu), _ptr(fpi),
-                                                _stream(stream)))
+        c, f = self._c, self._fn
+        B.check(B.lib().sc_hierarchy_prolongate(self._h, c(u0, "u0"), c(u1, "u1"), c(p0, "p0"),
+                                                c(p1, "p1"), float(alpha), f(fu, "fu"),
+                                                f(fpi, "fpi"), _stream(stream)))
 
     def restrict(self, fu, fpi, cu, cpi, stream=None):
-        B.check(B.lib().sc_hierarchy_restrict(self._h, _ptr(fu), _ptr(fpi), _ptr(cu), _ptr(cpi),
-                                              _stream(stream)))
+        c, f = self._c, self._fn
+        B.check(B.lib().sc_hierarchy_restrict(self._h, f(fu, "fu"), f(fpi, "fpi"), c(cu, "cu"),
+                                              c(cpi, "cpi"), _stream(stream)))
 
     def step(self, cu, cpi, cc2, fu, fpi, fc2, dt: float, nsteps: int,
              mode: int = B.SC_MODE_GRAPH, stream=None):
-        B.check(B.lib().sc_hierarchy_step(self._h, _ptr(cu), _ptr(cpi), _ptr(cc2), _ptr(fu),
-                                          _ptr(fpi), _ptr(fc2), float(dt), int(nsteps), int(mode),
-                                          _stream(stream)))
+        c, f = self._c, self._fn
+        B.check(B.lib().sc_hierarchy_step(self._h, c(cu, "cu"), c(cpi, "cpi"), c(cc2, "cc2"),
+                                          f(fu, "fu"), f(fpi, "fpi"), f(fc2, "fc2"), float(dt),
+                                          int(nsteps), int(mode), _stream(stream)))

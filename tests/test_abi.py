@@ -345,3 +345,34 @@ def test_missing_library_fails_loudly(tmp_path):
     assert r.returncode != 0
     assert "libsc_level.so is missing" in r.stderr
     assert "no CPU fallback" in r.stderr
+
+
+def test_field_tensors_are_checked_before_any_call(B):
+    """The Python layer checks what the C ABI cannot see behind a pointer:
+    dtype, contiguity, element count and device of every field tensor, and
+    the host buffers of the end-to-end call.  Each wrong argument raises
+    before the library is called (no GPU is needed to see it)."""
+    import torch
+    from paper_1308_1343_gb300.level import Level
+    lev = Level([((0, 0, 0), (8, 8, 8), 0)], [dict(lo=(0, 0, 0), hi=(8, 8, 8), h=1 / 8,
+                                                  periodic=7)])
+    n = lev.field_size
+    good = torch.zeros(n, dtype=torch.float64)
+    cases = [
+        (torch.zeros(n, dtype=torch.float32), "dtype"),
+        (torch.zeros(n - 1, dtype=torch.float64), "elements"),
+        (torch.zeros(2 * n, dtype=torch.float64)[::2], "contiguous"),
+        (good, "CUDA device"),
+    ]
+    for bad, why in cases:
+        with pytest.raises(ValueError, match=why):
+            lev.rk4_step(bad, good, good, 0.01, 1)
+    with pytest.raises(TypeError):
+        lev.fill_ghosts(np.zeros(n))
+    with pytest.raises(ValueError, match="required"):
+        lev.apply_laplacian(None, good)
+    h = np.zeros(n)
+    with pytest.raises(ValueError, match="u_out"):
+        lev.rk4_step_host(h, h, h, 0.01, 1, u_out=np.zeros(n - 1), pi_out=np.zeros(n))
+    with pytest.raises(ValueError, match="c2"):
+        lev.rk4_step_host(h, h, h[::1].astype(np.float32), 0.01, 1)
