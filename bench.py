@@ -306,11 +306,20 @@ def _uneven(torch, W, B, Level, arith, stream):
         res[name] = n * 50 / t
     lev.rk4_step(u, pi, c2, inst.dt, 10, B.SC_MODE_TIMED, stream=stream)
     gbs, _, _, _, kname = _stencil_roofline(lev, B, n)
+    hbm = _peaks().get("hbm_gbs")
+    # whole-step view of both forms: the stencil kernels' algorithmic bytes per
+    # point and RK4 step (ghost copies not counted) times the step rate
+    per_pt = (sum(BYTES_PER_POINT_PASS.values()) if lev.get_fusion() == 2
+              else BYTES_PER_POINT_STEP)
+    frac = (lambda g: g / hbm if (g and hbm) else None)
     out = {
         "workload": "512x512x256 periodic domain, 64 bisected boxes, 50 RK4 steps",
         "boxes": len(inst.boxes), "points": n, "stages_per_pass": lev.get_fusion(),
         "graph_updates_per_s": res["graph"], "per_box_updates_per_s": res["per_box"],
         "stencil_kernel": kname, "stencil_kernel_gbs": gbs,
+        "stencil_kernel_frac_of_measured_hbm": frac(gbs),
+        "bytes_per_point_step": per_pt,
+        "step_frac_of_measured_hbm": {name: frac(per_pt * r / 1e9) for name, r in res.items()},
     }
     del lev, u, pi, c2
     torch.cuda.empty_cache()

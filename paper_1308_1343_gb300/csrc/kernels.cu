@@ -890,13 +890,9 @@ static void set_carveouts() {
   prefer_shared(fwd_stage_kernel<Fixed, false, true>);
   prefer_shared(fwd_stage_kernel<Fp64, true, true>);
   prefer_shared(fwd_stage_kernel<Fp64, false, true>);
-  // pass B keeps three planes of pointwise fields: two 108 KB CTAs per SM
-  prefer_shared(pair_kernel<FixedI, true, false>);
-  prefer_shared(pair_kernel<FixedI, true, true>);
-  prefer_shared(pair_kernel<Fp64, true, false>);
-  prefer_shared(pair_kernel<Fp64, true, true>);
   prefer_shared(lap_kernel<Fixed>);
   prefer_shared(lap_kernel<Fp64>);
+  // pass B keeps three planes of pointwise fields: two 108 KB CTAs per SM
   prefer_shared(pair_kernel<FixedI, false, false>);
   prefer_shared(pair_kernel<FixedI, true, false>);
   prefer_shared(pair_kernel<Fp64, false, false>);
