@@ -376,3 +376,15 @@ def test_field_tensors_are_checked_before_any_call(B):
         lev.rk4_step_host(h, h, h, 0.01, 1, u_out=np.zeros(n - 1), pi_out=np.zeros(n))
     with pytest.raises(ValueError, match="c2"):
         lev.rk4_step_host(h, h, h[::1].astype(np.float32), 0.01, 1)
+
+
+def test_checked_build_compiles_and_exports_every_symbol(B):
+    """The checked build (SC_BOUNDS_CHECK: traversal indices verified against
+    their box on the device) compiles from the same sources and exports the
+    same C ABI; the GPU test runs it."""
+    from paper_1308_1343_gb300 import build
+    path = build.build(checked=True)
+    assert path.endswith("libsc_level_checked.so") and os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
