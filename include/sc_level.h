@@ -221,7 +221,8 @@ int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
  * budget_ms bounds the total tuning time.  Results are applied
  * to the level and, if cache_path is not NULL, merged into that on-disk
  * cache (keyed by GPU name, SM count, arithmetic, form and class extent)
- * and reused from it.  Synchronises the stream. */
+ * and reused from it; a cache line whose tile sc_level_set_tuning would
+ * reject is ignored.  Synchronises the stream. */
 int sc_level_autotune(sc_level* level, int32_t seed, double budget_ms,
                       double abort_factor, const char* cache_path, void* stream);
 

@@ -12,6 +12,7 @@
 //  * results are saved to and restored from an on-disk cache (the paper's
 //    proposed future work on saving tuned parameters, Sec. 3.3).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <fstream>
 #include <map>
@@ -51,7 +52,12 @@ std::map<std::string, std::pair<Cand, double>> read_cache(const char* path) {
     std::string key;
     Cand c{};
     double us = 0;
-    if (std::getline(is, key, '\t') && (is >> c.tx >> c.tz >> us)) m[key] = {c, us};
+    // the file is outside the library's control: an entry is used only if
+    // its tile is one the kernels accept (the rules of sc_level_set_tuning)
+    if (std::getline(is, key, '\t') && (is >> c.tx >> c.tz >> us) &&
+        (c.tx == 16 || c.tx == 32 || c.tx == 64) && c.tz >= 1 && c.tz <= (1 << 20) &&
+        std::isfinite(us) && us >= 0.0)
+      m[key] = {c, us};
   }
   return m;
 }
