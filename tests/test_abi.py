@@ -388,3 +388,36 @@ def test_checked_build_compiles_and_exports_every_symbol(B):
     lib = ctypes.CDLL(path)
     for name in _declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_bad_calls_fail_with_einval_before_any_device_work(B):
+    """Host-side failure injection through the raw C ABI: a NULL level,
+    NULL or misaligned field pointers, a bad mode or step count, aliasing
+    fields and a missing tape all return SC_EINVAL with a message, without
+    touching a GPU (none is present here)."""
+    from paper_1308_1343_gb300.level import Level
+    lev = Level([((0, 0, 0), (8, 8, 8), 0)], [dict(lo=(0, 0, 0), hi=(8, 8, 8), h=1 / 8,
+                                                  periodic=7)])
+    lib, h = B.lib(), lev._h
+    ok = ctypes.c_void_p(1 << 20)    # aligned, never dereferenced here
+    mis = ctypes.c_void_p((1 << 20) + 8)
+    dt = (ctypes.c_double * 1)(0.01)
+
+    def einval(rc, text):
+        assert rc == B.SC_EINVAL
+        assert text in lib.sc_last_error().decode()
+
+    einval(lib.sc_level_rk4_step(None, ok, ok, ok, dt, 1, 1, 0, None), "NULL level")
+    einval(lib.sc_level_rk4_step(h, mis, ok, ok, dt, 1, 1, 0, None), "aligned")
+    einval(lib.sc_level_rk4_step(h, ok, None, ok, dt, 1, 1, 0, None), "aligned")
+    einval(lib.sc_level_rk4_step(h, ok, ok, ok, dt, 1, -1, 0, None), "nsteps")
+    einval(lib.sc_level_rk4_step(h, ok, ok, ok, dt, 1, 1, 9, None), "mode")
+    einval(lib.sc_level_fill_ghosts(h, mis, None), "aligned")
+    einval(lib.sc_level_apply_laplacian(h, ok, ok, None), "overlap")
+    einval(lib.sc_level_misfit(h, mis, ok, ok, None, None), "pointer")
+    einval(lib.sc_level_rk4_step_host(h, None, ok, ok, ok, ok, dt, 1, 1, None), "NULL")
+    einval(lib.sc_level_backward_tape(h, ok, None, None, ok, ok, ok, None), "tape")
+    bad = B.ScTile(24, 20, 8, 0)
+    einval(lib.sc_level_set_tuning(h, 0, ctypes.byref(bad), 0), "tile_x")
+    bad = B.ScTile(32, 16, 0, 0)
+    einval(lib.sc_level_set_tuning(h, 0, ctypes.byref(bad), 0), "tile_z")
