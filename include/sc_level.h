@@ -365,7 +365,14 @@ int sc_level_launch_count(const sc_level* level, int64_t* n);
  *    their ghosts are refreshed internally; c2 is read on interior points.
  *  - h: grid spacing; dt: step; nsteps >= 0.
  *  - Boxes whose padded size pz*(nz+4) exceeds 2^19 doubles are rejected
- *    with SC_EINVAL ("box too large"), as are bad pointers or sizes.
+ *    with SC_EINVAL ("box too large"; the size is formed in 64 bits, so no
+ *    extent can wrap it), as are bad pointers or sizes, before any CUDA
+ *    call.  A CUDA error already pending from earlier work is returned as
+ *    SC_ECUDA before anything is enqueued; a failed launch stops the call
+ *    at that launch (SC_ECUDA).
+ *  - There is no device error word: this FP64 path has no fixed-point
+ *    scale or non-finite check to report, so a non-finite input simply
+ *    propagates into the results, as FP64 arithmetic does.
  *  - The first call on a device resolves the static array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
  *    before any stream capture on the device.

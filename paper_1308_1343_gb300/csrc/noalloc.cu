@@ -134,8 +134,18 @@ extern "C" int sc_box_rk4_step_noalloc(double* u, double* pi, const double* c2, 
   if (!aligned16(u) || !aligned16(pi) || !aligned16(c2)) return set_error(SC_EINVAL, "bad pointer");
   if (nx < 2 || ny < 2 || nz < 2 || nsteps < 0 || !(h > 0.0) || !(dt >= 0.0))
     return set_error(SC_EINVAL, "bad argument");
-  const long long py = ((nx + 4 + 15) / 16) * 16, pz = py * (ny + 4);
-  if (pz * (nz + 4) > kNoAllocField) return set_error(SC_EINVAL, "box too large");
+  // every extent fits the scratch on its own before any product is formed,
+  // and the padded size is computed in 64 bits: no extent can wrap it
+  if ((long long)nx > kNoAllocField || (long long)ny > kNoAllocField ||
+      (long long)nz > kNoAllocField)
+    return set_error(SC_EINVAL, "box too large");
+  const long long py = ((long long)nx + 4 + 15) / 16 * 16;
+  const long long pz = py * ((long long)ny + 4);
+  if (pz > kNoAllocField || pz * ((long long)nz + 4) > kNoAllocField)
+    return set_error(SC_EINVAL, "box too large");
+  // an error left pending by earlier work belongs to that work: report it
+  // as such instead of enqueuing more launches behind it
+  if (cudaPeekAtLastError() != cudaSuccess) return set_error(SC_ECUDA, "earlier CUDA error pending");
   int device = -1;
   if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)
     return set_error(SC_ECUDA, "no device");
@@ -170,7 +180,8 @@ extern "C" int sc_box_rk4_step_noalloc(double* u, double* pi, const double* c2, 
       noalloc_stage_kernel<<<sms * 2, kNT, 0, s>>>(bx, txh, tz, in_u[st], in_p[st], u, pi, c2,
                                                     out_u[st], out_p[st], g,
                                                     g / (12.0 * h * h));
+      // stop at the first launch that fails
+      if (cudaGetLastError() != cudaSuccess) return set_error(SC_ECUDA, "launch failed");
     }
-  if (cudaGetLastError() != cudaSuccess) return set_error(SC_ECUDA, "launch failed");
   return SC_OK;
 }

@@ -421,3 +421,22 @@ def test_bad_calls_fail_with_einval_before_any_device_work(B):
     einval(lib.sc_level_set_tuning(h, 0, ctypes.byref(bad), 0), "tile_x")
     bad = B.ScTile(32, 16, 0, 0)
     einval(lib.sc_level_set_tuning(h, 0, ctypes.byref(bad), 0), "tile_z")
+
+
+def test_noalloc_rejects_huge_extents_before_any_device_work(B):
+    """The entry point without device allocation checks the box size in 64
+    bits: extents near INT32_MAX, whose padded size would wrap a 32-bit
+    product, and a padded box just over the static scratch return SC_EINVAL
+    ('too large') before any CUDA call (none can succeed here: no GPU)."""
+    lib = B.lib()
+    ok = ctypes.c_void_p(1 << 20)    # aligned, never dereferenced
+    big = 2147483644
+    for n in ((2, big, 2), (big, 2, 2), (2, 2, big), (big, big, big), (65536, 65536, 2)):
+        rc = lib.sc_box_rk4_step_noalloc(ok, ok, ok, n[0], n[1], n[2], 0.01, 0.0025, 1, None)
+        assert rc == B.SC_EINVAL, n
+        assert "too large" in lib.sc_last_error().decode(), n
+    # padded size 16 * 64 * 516 = 528384 > 2^19 doubles: one plane too many
+    rc = lib.sc_box_rk4_step_noalloc(ok, ok, ok, 12, 60, 512, 0.01, 0.0025, 1, None)
+    assert rc == B.SC_EINVAL and "too large" in lib.sc_last_error().decode()
+    rc = lib.sc_box_rk4_step_noalloc(ok, ok, ok, 1, 8, 8, 0.01, 0.0025, 1, None)
+    assert rc == B.SC_EINVAL and "bad argument" in lib.sc_last_error().decode()
