@@ -59,6 +59,13 @@ BYTES_PER_POINT_STEP_CLASSIC = 304
 CPU_SAMPLE_S = 12.0
 # RK4 steps of the oracle per step of the reference arm
 REF_RK4_STEPS = 10
+# what the line's dtype means in each arithmetic form of the Laplacian sum
+DTYPE_LABEL = {
+    "fixed": "f64 (fixed-point Laplacian sum: each input truncated to 2^-54 of its "
+             "field's domain maximum, the sum exact in int64 and rounded once; RK "
+             "updates in FP64)",
+    "fp64": "f64",
+}
 # run-time tuning results (tile per box-size class) are cached here between runs
 TUNE_CACHE = os.path.join(ROOT, "paper_1308_1343_gb300", "_build", "tune_cache.txt")
 
@@ -244,8 +251,14 @@ def run_reference(a, ws, rank):
         "ms_per_step": 1e3 * total_t / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points": inst.u.size,
-                   "rk4_steps_per_step": REF_RK4_STEPS, "arith": "fp64 (oracle)",
-                   "l2": "inputs larger than L2"},
+                   "rk4_steps_per_step": REF_RK4_STEPS,
+                   "workload_rk4_steps_per_step": RK4_STEPS_PER_BENCH_STEP,
+                   "rk4_steps_note": "the oracle advances %d of the workload's %d RK4 steps "
+                                     "per benchmark step, a bounded sample that keeps the "
+                                     "run within minutes; the metric counts updates per "
+                                     "second, so the two arms' rates compare"
+                                     % (REF_RK4_STEPS, RK4_STEPS_PER_BENCH_STEP),
+                   "arith": "fp64 (oracle)", "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -271,11 +284,33 @@ def _time_steps(torch, lev, u, pi, c2, dt, nsteps, mode, reps, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-EXTRAS = ("uneven", "ensemble", "two_level", "adjoint")
+EXTRAS = ("fp64", "uneven", "ensemble", "two_level", "adjoint")
+
+
+def _time_grad(torch, lev, u0, pi0, c2, dt, nsteps, ckpt, stream, reps=2):
+    """Wall time of a taped forward and of the backward of the misfit of u_T
+    against u0 (the second of `reps` repetitions)."""
+    uT = torch.empty_like(u0)
+    seed = torch.empty_like(u0)
+    g = [torch.empty_like(u0) for _ in range(3)]
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lev.forward_tape(u0, pi0, c2, dt, nsteps, ckpt, uT, None, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lev.misfit(uT, u0, seed, stream=stream)
+        lev.backward_tape(c2, seed, None, g[0], g[1], g[2], stream=stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    lev.sync(stream)
+    return t1 - t0, t2 - t1
 
 
 def _extras(torch, W, B, Level, arith, stream, which=EXTRAS):
     out = {}
+    if "fp64" in which and arith == B.SC_ARITH_FIXED:
+        out["fp64_arith"] = _fp64_rate(torch, W, B, Level, stream)
     if "uneven" in which:
         out["uneven_level"] = _uneven(torch, W, B, Level, arith, stream)
     if "ensemble" in which:
@@ -286,6 +321,30 @@ def _extras(torch, W, B, Level, arith, stream, which=EXTRAS):
         out["two_level"] = _two_level(torch, W, B, Level, arith, stream)
     if "adjoint" in which:
         out["adjoint"] = _adjoint(torch, W, B, Level, arith, stream)
+    return out
+
+
+def _fp64_rate(torch, W, B, Level, stream):
+    """The headline workload with FP64 adds and FMAs in the Laplacian sum
+    (SC_ARITH_FP64) instead of the fixed-point sum: the cost of IEEE
+    arithmetic throughout, same form choice, tuning and timing."""
+    inst = W.single_box(N_EDGE, seed=2)
+    lev = Level.from_instances([inst])
+    lev.set_arith(B.SC_ARITH_FP64)
+    lev.autotune(seed=2, budget_ms=2000.0, abort_factor=2.0, cache_path=TUNE_CACHE,
+                 stream=stream)
+    u, pi = lev.to_device([inst.u]), lev.to_device([inst.pi])
+    c2 = lev.to_device([inst.c2], fill=1.0)
+    nsub = RK4_STEPS_PER_BENCH_STEP
+    _time_steps(torch, lev, u, pi, c2, inst.dt, nsub, B.SC_MODE_GRAPH, 3, stream)
+    reps = 3
+    t = _time_steps(torch, lev, u, pi, c2, inst.dt, nsub, B.SC_MODE_GRAPH, reps, stream)
+    out = {"workload": WORKLOAD + ", FP64 Laplacian sums",
+           "arith": "fp64", "dtype": DTYPE_LABEL["fp64"], "stages_per_pass": lev.get_fusion(),
+           "updates_per_s": inst.u.size * nsub * reps / t,
+           "ms_per_step": 1e3 * t / reps, "rk4_steps_per_step": nsub}
+    del lev, u, pi, c2
+    torch.cuda.empty_cache()
     return out
 
 
@@ -321,7 +380,15 @@ def _uneven(torch, W, B, Level, arith, stream):
         "bytes_per_point_step": per_pt,
         "step_frac_of_measured_hbm": {name: frac(per_pt * r / 1e9) for name, r in res.items()},
     }
-    del lev, u, pi, c2
+    # the level's gradient: 50 steps, checkpoints every 10, misfit seed
+    u0, pi0 = lev.to_device([inst.u]), lev.to_device([inst.pi])
+    t_fwd = _time_steps(torch, lev, u, pi, c2, inst.dt, 50, B.SC_MODE_GRAPH, 1, stream)
+    t_tape, t_bwd = _time_grad(torch, lev, u0, pi0, c2, inst.dt, 50, 10, stream)
+    out["gradient"] = {"rk4_steps": 50, "ckpt_every": 10, "t_forward_s": t_fwd,
+                       "t_forward_tape_s": t_tape, "t_backward_s": t_bwd,
+                       "ratio_backward_over_forward": t_bwd / t_fwd,
+                       "ratio_total_over_forward": (t_tape + t_bwd) / t_fwd}
+    del lev, u, pi, c2, u0, pi0
     torch.cuda.empty_cache()
     return out
 
@@ -340,11 +407,20 @@ def _ensemble(torch, W, B, Level, arith, stream):
                  stream=stream)
     _time_steps(torch, lev, u, pi, c2, dts, 5, B.SC_MODE_GRAPH, 1, stream)
     t = _time_steps(torch, lev, u, pi, c2, dts, 100, B.SC_MODE_GRAPH, 1, stream)
+    # 100 RK4 steps plus the adjoint gradient of every instance (one misfit
+    # per instance, checkpoints every 20)
+    u0 = lev.to_device([i.u for i in insts])
+    pi0 = lev.to_device([i.pi for i in insts])
+    t_tape, t_bwd = _time_grad(torch, lev, u0, pi0, c2, dts, 100, 20, stream)
     out = {"workload": "256 periodic cubes, edges 24..96, own c2 and pulse, "
                        "100 RK4 steps, autotuned tiles",
            "points": n, "stages_per_pass": lev.get_fusion(),
-           "graph_updates_per_s": n * 100 / t}
-    del lev, u, pi, c2
+           "graph_updates_per_s": n * 100 / t,
+           "gradient": {"rk4_steps": 100, "ckpt_every": 20, "t_forward_s": t,
+                        "t_forward_tape_s": t_tape, "t_backward_s": t_bwd,
+                        "ratio_backward_over_forward": t_bwd / t,
+                        "ratio_total_over_forward": (t_tape + t_bwd) / t}}
+    del lev, u, pi, c2, u0, pi0
     torch.cuda.empty_cache()
     return out
 
@@ -555,7 +631,8 @@ def run_ours(a, ws, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL[a.arith],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "points": npts, "rk4_steps_per_step": nsub,
                        "arith": a.arith, "mode": "batched persistent launch, CUDA graph per "
                                                   "RK4 step",

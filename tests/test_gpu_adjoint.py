@@ -154,6 +154,42 @@ def test_autograd_function():
 
 
 @pytest.mark.parametrize("fuse", [1, 2])
+def test_autograd_function_vs_oracle(orc, fuse):
+    """wave_rk4 under torch autograd, with a loss built in torch on both
+    outputs -- the misfit of u_T against an oracle observation plus a
+    linear functional of pi_T, so that autograd hands the Function non-zero
+    seeds for both -- against the oracle's checkpointed adjoint seeded with
+    the same derivatives: u0.grad, pi0.grad and c2.grad within 1e-10, and
+    the loss itself within 1e-11."""
+    import torch
+    from paper_1308_1343_gb300.level import wave_rk4
+    inst = W.gradient_problem(20, 4)
+    nsteps, ckpt = 12, 5
+    h, dt = inst.dom.h, inst.dt
+    lev, t = _setup(inst, 1, fuse)
+    ouo, _ = orc.rk4_periodic(inst.u, inst.pi, inst.c2_obs, h, dt, nsteps)
+    b = W.random_direction(inst.dom.shape, 47)
+    interior = t(np.ones(inst.dom.shape)) != 0.0
+    u_obs, b_dev = t(ouo), t(b)
+    u0 = t(inst.u).requires_grad_(True)
+    pi0 = t(inst.pi).requires_grad_(True)
+    c2 = t(inst.c2, 1.0).requires_grad_(True)
+    uT, piT = wave_rk4(lev, u0, pi0, c2, dt, nsteps, ckpt_every=ckpt)
+    m = interior
+    loss = 0.5 * h ** 3 * ((uT[m] - u_obs[m]) ** 2).sum() + (b_dev[m] * piT[m]).sum()
+    loss.backward()
+    lev.sync()
+    ouT, opT = orc.rk4_periodic(inst.u, inst.pi, inst.c2, h, dt, nsteps)
+    want_loss = 0.5 * h ** 3 * float(np.sum((ouT - ouo) ** 2)) + float(np.sum(b * opT))
+    assert abs(loss.item() - want_loss) <= 1e-11 * abs(want_loss)
+    ou, op, oc = orc.grad_periodic(inst.u, inst.pi, inst.c2, h, dt, nsteps, ckpt,
+                                   orc.misfit_seed(ouT, ouo, h), b)
+    assert rel_err(lev.gather(u0.grad)[0], ou) <= 1e-10
+    assert rel_err(lev.gather(pi0.grad)[0], op) <= 1e-10
+    assert rel_err(lev.gather(c2.grad)[0], oc) <= 1e-10
+
+
+@pytest.mark.parametrize("fuse", [1, 2])
 @pytest.mark.parametrize("arith", [0, 1])
 def test_gradient_on_uneven_level(orc, arith, fuse):
     """Adjoint on an uneven multi-box level: equal to the one-box level's

@@ -69,6 +69,39 @@ def test_prolongation_bit_exact():
         assert np.array_equal(got_p, H.prolongate(b0, b1, alpha, pts))
 
 
+def test_prolongation_vs_order_free_tensor_sum():
+    """The GPU prolongation against the tensor-product sum rounded once
+    (exact_sums.tensor_sum_exact), which shares no evaluation order with
+    the kernel or the oracle: equal bit for bit on dyadic data (every
+    product and partial sum is then exact, in any order), and within 4 ulps
+    of the data's scale on random data, at alpha = 0, 1/2 and 0.3."""
+    import torch
+    from exact_sums import tensor_sum_exact
+    n, lo, hi = 24, (8, 6, 10), (38, 36, 36)
+    c, f, h = _setup(n, lo, hi)
+    rng = np.random.default_rng(8)
+    pts = h.prolongation_points()
+    sample = pts[::5]
+    fu = torch.zeros(f.field_size, dtype=torch.float64, device="cuda")
+    fp = torch.zeros_like(fu)
+    eps = np.finfo(float).eps
+    dyadic = [rng.integers(-2 ** 20, 2 ** 20, size=(n, n, n)).astype(np.float64)
+              for _ in range(2)]
+    normal = [rng.normal(size=(n, n, n)) for _ in range(2)]
+    for (a0, a1), alphas, exact in ((dyadic, (0.0, 0.5), True), (normal, (0.0, 0.3), False)):
+        d0, d1 = c.to_device([a0]), c.to_device([a1])
+        for alpha in alphas:
+            h.prolongate(d0, d1, d0, d1, alpha, fu, fp)
+            torch.cuda.synchronize()
+            got = _read_points(f, fu, sample, lo)
+            data = (1.0 - alpha) * a0 + alpha * a1
+            want = np.array([tensor_sum_exact(data, p) for p in sample])
+            if exact:
+                assert np.array_equal(got, want), alpha
+            else:
+                assert np.abs(got - want).max() <= 4 * eps * np.abs(data).max(), alpha
+
+
 def _read_points(lev, t, pts, lo):
     """Values of a level field at level points (interior or ghost shell)."""
     buf = t.cpu().numpy()

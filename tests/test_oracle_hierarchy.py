@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+from exact_sums import tensor_sum_exact
 from oracle import hierarchy as H
 from paper_1308_1343_gb300 import workloads as W
 
@@ -67,17 +68,6 @@ def test_time_interpolation_is_linear():
     assert np.abs(half - 0.5 * (pa + pb)).max() <= 1e-14 * np.abs(pa).max()
 
 
-def _flat_exact(data, p):
-    """The tensor-product value at fine point p from the 1-D stencils alone,
-    as one exactly rounded sum over all (z, y, x) terms (math.fsum): an
-    evaluation that shares no order or structure with the oracle's."""
-    nz, ny, nx = data.shape
-    (ix, wx), (iy, wy), (iz, wz) = (H.stencil_1d(int(p[d])) for d in range(3))
-    terms = [wz[a] * wy[b] * wx[c] * data[iz[a] % nz, iy[b] % ny, ix[c] % nx]
-             for a in range(len(iz)) for b in range(len(iy)) for c in range(len(ix))]
-    return math.fsum(terms)
-
-
 def test_prolongation_nested_equals_exact_tensor_sum():
     """The oracle's successive 1-D interpolations equal the tensor-product sum
     rounded once: exactly for dyadic data (every product and partial sum is
@@ -88,15 +78,15 @@ def test_prolongation_nested_equals_exact_tensor_sum():
     pts = H.shell_and_buffer((6, 6, 6), (18, 18, 18), 4)[::7]
     dyadic = rng.integers(-2 ** 20, 2 ** 20, size=(12, 12, 12)).astype(np.float64)
     got = H.prolongate(dyadic, dyadic, 0.0, pts)
-    want = np.array([_flat_exact(dyadic, p) for p in pts])
+    want = np.array([tensor_sum_exact(dyadic, p) for p in pts])
     assert np.array_equal(got, want)
     # x, y and z are not interchangeable: a transposed copy gives other values
     assert not np.array_equal(H.prolongate(dyadic.transpose(2, 1, 0).copy(),
                                            dyadic.transpose(2, 1, 0).copy(), 0.0, pts), want)
     data = rng.normal(size=(12, 12, 12))
     got = H.prolongate(data, data, 0.0, pts)
-    want = np.array([_flat_exact(data, p) for p in pts])
-    assert np.abs(got - want).max() <= 8 * np.finfo(float).eps * np.abs(data).max()
+    want = np.array([tensor_sum_exact(data, p) for p in pts])
+    assert np.abs(got - want).max() <= 4 * np.finfo(float).eps * np.abs(data).max()
 
 
 def test_prolongation_and_restriction_sets():
