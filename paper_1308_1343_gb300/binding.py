@@ -1,5 +1,5 @@
-"""ctypes binding of libsc_level.so (the C ABI of include/sc_level.h and
-include/sc_bboxset.h).  Argument marshalling only: every computation runs
+"""ctypes binding of libsc_level.so (the C ABI of include/sc_level.h,
+include/sc_bboxset.h, include/sc_hierarchy.h and include/sc_dist.h).  Argument marshalling only: every computation runs
 in the library.  There is no fallback -- if the library is missing or fails
 to load, ``lib()`` raises.
 """
@@ -18,6 +18,8 @@ SC_ARITH_FP64, SC_ARITH_FIXED = 0, 1
 SC_STAGING_REGISTERS, SC_STAGING_SHARED = 0, 1
 SC_MODE_GRAPH, SC_MODE_PER_BOX, SC_MODE_BATCHED, SC_MODE_TIMED = 0, 1, 2, 3
 SC_SET_UNION, SC_SET_INTERSECTION, SC_SET_DIFFERENCE, SC_SET_XOR = 0, 1, 2, 3
+SC_DIST_GREEDY, SC_DIST_BISECT = 0, 1
+SC_DIST_STATE, SC_DIST_STAGE = 0, 1
 (SC_KERNEL_STAGE, SC_KERNEL_GATHER, SC_KERNEL_STAGE_RECORD, SC_KERNEL_ADJ_A, SC_KERNEL_ADJ_B,
  SC_KERNEL_ADJ_C, SC_KERNEL_PAIR_A, SC_KERNEL_PAIR_B) = range(8)
 
@@ -100,6 +102,20 @@ _SIGS = {
     "sc_hierarchy_prolongate": (_i32, [_vp, _vp, _vp, _vp, _vp, _dbl, _vp, _vp, _vp]),
     "sc_hierarchy_restrict": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sc_hierarchy_step": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i32, _i32, _vp]),
+    "sc_dist_partition": (_i32, [ctypes.POINTER(ScBox), _i32, _i32, _i32,
+                                 ctypes.POINTER(_i32)]),
+    "sc_dist_create": (_i32, [ctypes.POINTER(ScBox), _i32, ctypes.POINTER(ScDomain), _i32, _i32,
+                              ctypes.POINTER(_i32), _i32, _i32, ctypes.POINTER(_vp)]),
+    "sc_dist_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                            ctypes.POINTER(_i32)]),
+    "sc_dist_global_box": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "sc_dist_buffer_sizes": (_i32, [_vp, _p64, _p64]),
+    "sc_dist_peer": (_i32, [_vp, _i32, ctypes.POINTER(_i32), _p64, _p64, _p64, _p64]),
+    "sc_dist_list": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ScCopy), _i64, _p64]),
+    "sc_dist_pack": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "sc_dist_unpack": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "sc_dist_rk4_begin": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl), _i32, _vp]),
+    "sc_dist_rk4_pass": (_i32, [_vp, _vp, _vp, _i32, _vp]),
 }
 
 _lock = threading.Lock()

@@ -79,6 +79,22 @@ struct DPush {
   int pad[3];
 };
 
+// One ghost copy that crosses ranks of a distributed level, seen from this
+// rank: a rectangle of the local field (interior points of a local source
+// box when packing, ghost points of a local destination box when unpacking)
+// and its place in the contiguous exchange buffer, where the rectangle's
+// points follow each other x fastest.  The buffer holds two fields: the
+// second one's copy of a point sits `second` doubles after the first's.
+struct DXfer {
+  long long fld;   // element index of the first point in the field
+  long long buf;   // index of the first point in the exchange buffer
+  long long fpy, fpz;  // field pitches of the rectangle's box
+  int ex, ey, ez;  // extent
+  int dom;         // domain of the points
+  int second;      // offset of the second field's block (the peer's points)
+  int pad;
+};
+
 // A chunk of up to CHUNK consecutive points of one rectangle.
 struct DChunk {
   int rect;

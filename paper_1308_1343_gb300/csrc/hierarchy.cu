@@ -313,6 +313,8 @@ int sc_hierarchy_create(sc_level* coarse, sc_level* fine, int32_t ratio, int32_t
                         sc_hierarchy** out) {
   if (!coarse || !fine || !out) return set_error(SC_EINVAL, "NULL argument");
   *out = nullptr;
+  if (coarse->partial || fine->partial)
+    return set_error(SC_EINVAL, "hierarchy: levels must not be distributed (sc_dist_create)");
   if (ratio != 2) return set_error(SC_EINVAL, "hierarchy: refinement ratio must be 2");
   if (buffer < 4) return set_error(SC_EINVAL, "hierarchy: buffer must be >= 4");
   if (coarse->doms.size() != 1 || fine->doms.size() != 1)

@@ -58,6 +58,45 @@ __global__ void __launch_bounds__(kGatherChunk) gather_kernel(
   }
 }
 
+// Exchange of a distributed level across ranks: PACK copies the points of
+// every DXfer rectangle of two fields into the contiguous buffer (the second
+// field `second` doubles after the first); otherwise the buffer is written
+// back into the rectangles (ghost points of local boxes) and, if emax is not
+// NULL, the largest biased exponent of what was written raises the exponent
+// bounds emax[dom] (first field) and emax[ndom + dom] (second field) that
+// the next pass reads.  One chunk of one rectangle per CTA iteration.
+template <bool PACK>
+__global__ void __launch_bounds__(kGatherChunk) xfer_kernel(
+    const DXfer* __restrict__ xs, const DChunk* __restrict__ chunks, int nchunks, double* f,
+    double* g, double* buf, unsigned* emax, int ndom) {
+  __shared__ unsigned red[2 * kGatherChunk / 32];
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const DChunk ch = chunks[c];
+    const DXfer r = xs[ch.rect];
+    const int p = ch.first + (int)threadIdx.x;
+    unsigned ea = 0u, eb = 0u;
+    if (p < r.ex * r.ey * r.ez) {
+      const int t = p / r.ex;
+      const int x = p - t * r.ex;
+      const int z = t / r.ey;
+      const int y = t - z * r.ey;
+      const long long fi = r.fld + x + y * r.fpy + z * r.fpz;
+      const long long bi = r.buf + p;
+      if (PACK) {
+        buf[bi] = f[fi];
+        buf[bi + r.second] = g[fi];
+      } else {
+        const double a = buf[bi], b = buf[bi + r.second];
+        f[fi] = a;
+        g[fi] = b;
+        ea = biased_exp(a);
+        eb = biased_exp(b);
+      }
+    }
+    if (!PACK && emax) cta_max2_to(ea, eb, emax + r.dom, emax + ndom + r.dom, red);
+  }
+}
+
 // Largest biased exponent of the field over the rectangles, per domain.
 __global__ void __launch_bounds__(256) maxexp_kernel(const DRect* __restrict__ rects,
                                                      const DChunk* __restrict__ chunks,
@@ -1005,6 +1044,18 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {
                                                          pair_kernel<FixedI, true, true>, NT, 0);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
                                                        pair_kernel<Fp64, true, true>, NT, 0);
+}
+
+cudaError_t launch_xfer(bool pack, const DXfer* xs, const DChunk* chunks, int nchunks,
+                        double* f, double* g, double* buf, unsigned* emax, int ndom, int grid,
+                        cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  grid = min(grid, nchunks);
+  if (pack)
+    xfer_kernel<true><<<grid, kGatherChunk, 0, s>>>(xs, chunks, nchunks, f, g, buf, nullptr, ndom);
+  else
+    xfer_kernel<false><<<grid, kGatherChunk, 0, s>>>(xs, chunks, nchunks, f, g, buf, emax, ndom);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(const DProl* rects, const DChunk* chunks, int nchunks,

@@ -10,6 +10,7 @@ struct DBox;
 struct DItem;
 struct DRect;
 struct DChunk;
+struct DXfer;
 struct DPush;
 struct DProl;
 struct DRestr;
@@ -172,6 +173,11 @@ cudaError_t launch_blend(const DRect* rects, const DChunk* chunks, int nchunks, 
 cudaError_t launch_restrict(const DRestr* rects, const DChunk* chunks, int nchunks,
                             const double* fu, const double* fp, double* cu, double* cp,
                             unsigned* emax, cudaStream_t s);
+// distributed level: pack the rectangles of f and g into buf (pack), or
+// write buf into them and raise emax[dom], emax[ndom + dom] (emax may be NULL)
+cudaError_t launch_xfer(bool pack, const DXfer* xs, const DChunk* chunks, int nchunks,
+                        double* f, double* g, double* buf, unsigned* emax, int ndom, int grid,
+                        cudaStream_t s);
 int stage_threads();
 cudaError_t stage_occupancy(int arith, int staging, int* blocks_per_sm);
 

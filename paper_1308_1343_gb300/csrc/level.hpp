@@ -37,6 +37,17 @@ void append_box_items(std::vector<dev::DItem>& items, int b, int nx, int ny, int
 int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt, int nsteps,
                 int mode, cudaStream_t s, bool qprep, bool bounds = false);
 
+// One peer of a rank-local part of a distributed level: the ghost copies
+// this rank sends to it (source boxes local) and receives from it
+// (destination boxes local), each in the order of the whole level's
+// exchange list, so that both ends of a pair agree on the buffer layout.
+struct PeerLists {
+  int peer = -1;
+  std::vector<sc_copy> send, recv;  // the local side's box index is local
+  int64_t send_points = 0, recv_points = 0;
+  int64_t send_offset = 0, recv_offset = 0;  // doubles into the 2-field buffers
+};
+
 struct SizeClass {
   std::array<int64_t, 3> ext;  // interior extent rounded up to a multiple of 8
   sc_tile tile;
@@ -95,6 +106,15 @@ struct DeviceState {
   std::map<std::string, double*> fields;
   std::map<std::string, size_t> field_count;
 
+  // distributed level: pack and unpack rectangles of every peer, in peer
+  // order (DXfer, one per ghost copy that crosses ranks) and their chunks
+  dev::DXfer* xsend = nullptr;
+  dev::DChunk* xsend_chunks = nullptr;
+  int nxsend_chunks = 0;
+  dev::DXfer* xrecv = nullptr;
+  dev::DChunk* xrecv_chunks = nullptr;
+  int nxrecv_chunks = 0;
+
   // captured RK4 step graphs keyed by (u, pi, c2, arith, version)
   std::map<std::tuple<const void*, const void*, const void*, int, int>,
            std::pair<cudaGraphExec_t, int>>
@@ -135,5 +155,17 @@ struct sc_level {
   int tape_nsteps = 0, tape_ckpt = 1;
   const double* tape_c2 = nullptr;
   std::vector<double> tape_dt;
+  // rank-local part of a distributed level (sc_dist_create): only this
+  // rank's boxes are stored; ghosts owned by other ranks' boxes arrive
+  // through sc_dist_unpack
+  bool partial = false;
+  int rank = 0, nranks = 1;
+  std::vector<int32_t> global_box;  // local box -> index in the whole level
+  std::vector<sc::PeerLists> peers;  // by increasing peer rank
+  int64_t send_doubles = 0, recv_doubles = 0;
+  bool dist_begun = false;  // sc_dist_rk4_begin has started a run
+  int dist_next_pass = 0;   // 0: pass A next, 1: pass B next
+  const double* dist_u = nullptr;  // the run's state buffers
+  const double* dist_pi = nullptr;
   sc::DeviceState* dev = nullptr;
 };

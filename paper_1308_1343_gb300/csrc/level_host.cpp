@@ -2,12 +2,15 @@
 // bboxset algebra, the level layout, the ghost-exchange list, size classes,
 // and the bboxset entry points.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "../../include/sc_bboxset.h"
+#include "../../include/sc_dist.h"
 #include "../../include/sc_level.h"
 #include "bboxset.hpp"
 #include "level.hpp"
@@ -182,6 +185,106 @@ static int validate(const sc_box* boxes, int32_t nboxes, const sc_domain* doms,
   return SC_OK;
 }
 
+// Layout, exchange list and size classes of a level whose boxes and domains
+// are set (every box stored, box-major; the exchange among those boxes).
+static int build_level(sc_level* L) {
+  L->all_periodic = true;
+  for (const auto& D : L->doms)
+    if (D.periodic != 7u) L->all_periodic = false;
+  // layout: interior corner of every box on a 16-double (128-byte) line
+  int64_t base = 14;
+  for (const auto& B : L->boxes) {
+    const int64_t nx = B.hi[0] - B.lo[0], ny = B.hi[1] - B.lo[1], nz = B.hi[2] - B.lo[2];
+    const int64_t py = roundup(nx + 4, 16), pz = py * (ny + 4), st = pz * (nz + 4);
+    L->py.push_back(py);
+    L->pz.push_back(pz);
+    L->storage.push_back(st);
+    L->off.push_back(base + 2 + 2 * py + 2 * pz);
+    base += st;
+  }
+  L->field_size = base + 2;
+  if (L->field_size >= (int64_t(1) << 31))
+    return set_error(SC_EINVAL, "level too large: a field must hold fewer than 2^31 doubles");
+  build_exchange(L);
+  build_classes(L);
+  return SC_OK;
+}
+
+static int64_t box_points(const sc_box& B) {
+  return (B.hi[0] - B.lo[0]) * (B.hi[1] - B.lo[1]) * (B.hi[2] - B.lo[2]);
+}
+
+// Greedy balance by point count: boxes in decreasing size (ties: lower
+// index first) each go to the rank with the fewest points so far (ties:
+// lower rank).  The largest load then exceeds the mean by less than the
+// largest box.
+static void partition_greedy(const sc_box* boxes, int nb, int nranks, int32_t* rank_of) {
+  std::vector<int> order(nb);
+  for (int b = 0; b < nb; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return box_points(boxes[a]) > box_points(boxes[b]);
+  });
+  std::vector<int64_t> load(nranks, 0);
+  for (int b : order) {
+    int r = 0;
+    for (int k = 1; k < nranks; ++k)
+      if (load[k] < load[r]) r = k;
+    rank_of[b] = r;
+    load[r] += box_points(boxes[b]);
+  }
+}
+
+// Recursive bisection in space: the boxes of a group of ranks are ordered
+// by their centres along the longest axis of the group's bounding box and
+// cut where the lower part's share of the points comes closest to its
+// share of the ranks (each part keeping at least as many boxes as ranks);
+// then each part is split again.  Boxes that are near each other share a
+// rank, so fewer ghost copies cross ranks than with the greedy split.
+static void partition_bisect(const sc_box* boxes, std::vector<int> group, int r0, int nr,
+                             int32_t* rank_of) {
+  if (nr == 1) {
+    for (int b : group) rank_of[b] = r0;
+    return;
+  }
+  int64_t lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = INT64_MAX;
+    hi[d] = INT64_MIN;
+  }
+  for (int b : group)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], boxes[b].lo[d]);
+      hi[d] = std::max(hi[d], boxes[b].hi[d]);
+    }
+  int axis = 0;
+  for (int d = 1; d < 3; ++d)
+    if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
+  std::stable_sort(group.begin(), group.end(), [&](int a, int b) {
+    return boxes[a].lo[axis] + boxes[a].hi[axis] < boxes[b].lo[axis] + boxes[b].hi[axis];
+  });
+  const int nl = nr / 2;
+  int64_t total = 0;
+  for (int b : group) total += box_points(boxes[b]);
+  // cut after k boxes, nl <= k <= size - (nr - nl)
+  int best = nl;
+  double best_gap = -1.0;
+  int64_t acc = 0;
+  const int n = (int)group.size();
+  for (int k = 1; k <= n - (nr - nl); ++k) {
+    acc += box_points(boxes[group[k - 1]]);
+    if (k < nl) continue;
+    const double gap = std::fabs((double)acc / (double)total - (double)nl / (double)nr);
+    if (best_gap < 0.0 || gap < best_gap) {
+      best_gap = gap;
+      best = k;
+    }
+  }
+  partition_bisect(boxes, std::vector<int>(group.begin(), group.begin() + best), r0, nl,
+                   rank_of);
+  partition_bisect(boxes, std::vector<int>(group.begin() + best, group.end()), r0 + nl,
+                   nr - nl, rank_of);
+}
+
 }  // namespace sc
 
 using namespace sc;
@@ -202,29 +305,13 @@ int sc_level_create(const sc_box* boxes, int32_t nboxes, const sc_domain* doms, 
   try {
     L->boxes.assign(boxes, boxes + nboxes);
     L->doms.assign(doms, doms + ndoms);
-    for (const auto& D : L->doms)
-      if (D.periodic != 7u) L->all_periodic = false;
-    // layout: interior corner of every box on a 16-double (128-byte) line
-    int64_t base = 14;
-    for (const auto& B : L->boxes) {
-      const int64_t nx = B.hi[0] - B.lo[0], ny = B.hi[1] - B.lo[1], nz = B.hi[2] - B.lo[2];
-      const int64_t py = roundup(nx + 4, 16), pz = py * (ny + 4), st = pz * (nz + 4);
-      L->py.push_back(py);
-      L->pz.push_back(pz);
-      L->storage.push_back(st);
-      L->off.push_back(base + 2 + 2 * py + 2 * pz);
-      base += st;
-    }
-    L->field_size = base + 2;
-    if (L->field_size >= (int64_t(1) << 31)) {
-      delete L;
-      return set_error(SC_EINVAL, "level too large: a field must hold fewer than 2^31 doubles");
-    }
-    build_exchange(L);
-    build_classes(L);
+    rc = build_level(L);
   } catch (const std::bad_alloc&) {
+    rc = set_error(SC_ENOMEM, "out of host memory");
+  }
+  if (rc) {
     delete L;
-    return set_error(SC_ENOMEM, "out of host memory");
+    return rc;
   }
   *out = L;
   return SC_OK;
@@ -418,6 +505,166 @@ int sc_bboxset_size(const int64_t* a, int64_t na, int64_t* npoints) {
   int rc = read_set(a, na, &A);
   if (rc) return rc;
   *npoints = A.size();
+  return SC_OK;
+}
+
+// ---- distributed level ---------------------------------------------------
+
+int sc_dist_partition(const sc_box* boxes, int32_t nboxes, int32_t nranks, int32_t method,
+                      int32_t* rank_of_box) {
+  if (!boxes || !rank_of_box) return set_error(SC_EINVAL, "NULL argument");
+  if (nranks < 1) return set_error(SC_EINVAL, "nranks must be >= 1");
+  if (nboxes < nranks) return set_error(SC_EINVAL, "fewer boxes than ranks");
+  try {
+    if (method == SC_DIST_GREEDY) {
+      partition_greedy(boxes, nboxes, nranks, rank_of_box);
+    } else if (method == SC_DIST_BISECT) {
+      std::vector<int> all(nboxes);
+      for (int b = 0; b < nboxes; ++b) all[b] = b;
+      partition_bisect(boxes, all, 0, nranks, rank_of_box);
+    } else {
+      return set_error(SC_EINVAL, "unknown partition method");
+    }
+  } catch (const std::bad_alloc&) {
+    return set_error(SC_ENOMEM, "out of host memory");
+  }
+  return SC_OK;
+}
+
+int sc_dist_create(const sc_box* boxes, int32_t nboxes, const sc_domain* doms, int32_t ndoms,
+                   int32_t ghost, const int32_t* rank_of_box, int32_t nranks, int32_t rank,
+                   sc_level** out) {
+  if (!out) return set_error(SC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (ghost != 2) return set_error(SC_EINVAL, "ghost width must be 2");
+  if (!rank_of_box) return set_error(SC_EINVAL, "rank_of_box is NULL");
+  if (nranks < 1 || rank < 0 || rank >= nranks) return set_error(SC_EINVAL, "bad rank");
+  int rc = validate(boxes, nboxes, doms, ndoms);
+  if (rc) return rc;
+  for (int32_t d = 0; d < ndoms; ++d)
+    if (doms[d].periodic != 7u)
+      return set_error(SC_EINVAL, "a distributed level needs domains periodic on every axis");
+  std::vector<int> owned(nranks, 0);
+  for (int32_t b = 0; b < nboxes; ++b) {
+    if (rank_of_box[b] < 0 || rank_of_box[b] >= nranks)
+      return set_error(SC_EINVAL, "box " + std::to_string(b) + ": rank out of range");
+    owned[rank_of_box[b]]++;
+  }
+  for (int r = 0; r < nranks; ++r)
+    if (!owned[r]) return set_error(SC_EINVAL, "rank " + std::to_string(r) + " owns no box");
+  sc_level* L = new (std::nothrow) sc_level();
+  if (!L) return set_error(SC_ENOMEM, "out of host memory");
+  try {
+    // the whole level's exchange list, in its deterministic order: every
+    // rank computes the same list, so the two ends of each peer pair filter
+    // the same copies in the same order
+    sc_level whole;
+    whole.boxes.assign(boxes, boxes + nboxes);
+    whole.doms.assign(doms, doms + ndoms);
+    build_exchange(&whole);
+    std::vector<int> local(nboxes, -1);
+    for (int32_t b = 0; b < nboxes; ++b)
+      if (rank_of_box[b] == rank) {
+        local[b] = (int)L->boxes.size();
+        L->boxes.push_back(boxes[b]);
+        L->global_box.push_back(b);
+      }
+    L->doms.assign(doms, doms + ndoms);
+    L->partial = true;
+    L->rank = rank;
+    L->nranks = nranks;
+    L->fuse = 2;  // the exchange sits between the two passes of a step
+    L->fuse_fixed = true;
+    rc = build_level(L);  // layout and the exchange among this rank's boxes
+    if (!rc) {
+      std::map<int, PeerLists> per;
+      for (const sc_copy& c : whole.copies) {
+        const int rs = rank_of_box[c.src_box], rd = rank_of_box[c.dst_box];
+        if (rs == rd) continue;
+        if (rd == rank) {
+          sc_copy e = c;
+          e.dst_box = local[c.dst_box];
+          PeerLists& P = per[rs];
+          P.recv.push_back(e);
+          P.recv_points += c.ext[0] * c.ext[1] * c.ext[2];
+        } else if (rs == rank) {
+          sc_copy e = c;
+          e.src_box = local[c.src_box];
+          PeerLists& P = per[rd];
+          P.send.push_back(e);
+          P.send_points += c.ext[0] * c.ext[1] * c.ext[2];
+        }
+      }
+      int64_t so = 0, ro = 0;
+      for (auto& kv : per) {
+        kv.second.peer = kv.first;
+        kv.second.send_offset = so;
+        kv.second.recv_offset = ro;
+        so += 2 * kv.second.send_points;
+        ro += 2 * kv.second.recv_points;
+        L->peers.push_back(kv.second);
+      }
+      L->send_doubles = so;
+      L->recv_doubles = ro;
+      if (so >= (int64_t(1) << 31) || ro >= (int64_t(1) << 31))
+        rc = set_error(SC_EINVAL, "exchange buffer too large");
+    }
+  } catch (const std::bad_alloc&) {
+    rc = set_error(SC_ENOMEM, "out of host memory");
+  }
+  if (rc) {
+    delete L;
+    return rc;
+  }
+  *out = L;
+  return SC_OK;
+}
+
+int sc_dist_info(const sc_level* L, int32_t* rank, int32_t* nranks, int32_t* npeers) {
+  if (!L || !rank || !nranks || !npeers) return set_error(SC_EINVAL, "NULL argument");
+  *rank = L->rank;
+  *nranks = L->nranks;
+  *npeers = (int32_t)L->peers.size();
+  return SC_OK;
+}
+
+int sc_dist_global_box(const sc_level* L, int32_t box, int32_t* global_box) {
+  if (!L || !global_box) return set_error(SC_EINVAL, "NULL argument");
+  if (box < 0 || box >= (int32_t)L->boxes.size()) return set_error(SC_EINVAL, "box out of range");
+  *global_box = L->partial ? L->global_box[box] : box;
+  return SC_OK;
+}
+
+int sc_dist_buffer_sizes(const sc_level* L, int64_t* send_doubles, int64_t* recv_doubles) {
+  if (!L || !send_doubles || !recv_doubles) return set_error(SC_EINVAL, "NULL argument");
+  *send_doubles = L->send_doubles;
+  *recv_doubles = L->recv_doubles;
+  return SC_OK;
+}
+
+int sc_dist_peer(const sc_level* L, int32_t i, int32_t* peer, int64_t* send_points,
+                 int64_t* recv_points, int64_t* send_offset, int64_t* recv_offset) {
+  if (!L || !peer || !send_points || !recv_points || !send_offset || !recv_offset)
+    return set_error(SC_EINVAL, "NULL argument");
+  if (i < 0 || i >= (int32_t)L->peers.size()) return set_error(SC_EINVAL, "peer out of range");
+  const PeerLists& P = L->peers[i];
+  *peer = P.peer;
+  *send_points = P.send_points;
+  *recv_points = P.recv_points;
+  *send_offset = P.send_offset;
+  *recv_offset = P.recv_offset;
+  return SC_OK;
+}
+
+int sc_dist_list(const sc_level* L, int32_t i, int32_t recv, sc_copy* out, int64_t cap,
+                 int64_t* n) {
+  if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
+  if (i < 0 || i >= (int32_t)L->peers.size()) return set_error(SC_EINVAL, "peer out of range");
+  if (cap > 0 && !out) return set_error(SC_EINVAL, "out is NULL");
+  const std::vector<sc_copy>& v = recv ? L->peers[i].recv : L->peers[i].send;
+  *n = (int64_t)v.size();
+  const int64_t m = std::min<int64_t>(cap, *n);
+  if (m > 0) std::memcpy(out, v.data(), (size_t)m * sizeof(sc_copy));
   return SC_OK;
 }
 

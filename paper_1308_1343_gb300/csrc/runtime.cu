@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/sc_dist.h"
 #include "level.hpp"
 
 namespace sc {
@@ -16,6 +17,7 @@ using dev::DChunk;
 using dev::DItem;
 using dev::DPush;
 using dev::DRect;
+using dev::DXfer;
 using dev::StageCoef;
 
 namespace {
@@ -144,7 +146,8 @@ void release_device(sc_level* L) {
   for (auto& kv : D->fields) cudaFree(kv.second);
   void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->gchunks_nw, D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
-                  D->emax_adj, D->err, D->partial};
+                  D->emax_adj, D->err, D->partial, D->xsend, D->xsend_chunks, D->xrecv,
+                  D->xrecv_chunks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D->pinned) cudaFreeHost(D->pinned);
@@ -173,6 +176,59 @@ int ensure_device(sc_level* L) {
     set_error(rc, msg);
   }
   return rc;
+}
+
+// Pack and unpack rectangles of a distributed level: one DXfer per ghost
+// copy that crosses ranks, peer by peer in increasing rank, each copy's
+// points at consecutive buffer positions from its peer's block offset (the
+// buffer layout of include/sc_dist.h), chunked for one point per thread.
+static int build_xfer_lists(sc_level* L) {
+  DeviceState* D = L->dev;
+  for (int dir = 0; dir < 2; ++dir) {  // 0: send (pack), 1: receive (unpack)
+    std::vector<DXfer> xs;
+    std::vector<DChunk> chunks;
+    const int64_t total = dir ? L->recv_doubles : L->send_doubles;
+    for (const PeerLists& P : L->peers) {
+      const std::vector<sc_copy>& v = dir ? P.recv : P.send;
+      const int64_t npts = dir ? P.recv_points : P.send_points;
+      const int64_t start = dir ? P.recv_offset : P.send_offset;
+      const int64_t end = start + npts;  // the first field's run of this peer
+      if (start < 0 || start + 2 * npts > total) return list_error("exchange-buffer");
+      int64_t pos = start;
+      for (const sc_copy& C : v) {
+        const int b = dir ? C.dst_box : C.src_box;
+        const int64_t* lo = dir ? C.dst_lo : C.src_lo;
+        const sc_box& B = L->boxes[b];
+        DXfer x{};
+        x.fld = L->off[b] + (lo[0] - B.lo[0]) + (lo[1] - B.lo[1]) * L->py[b] +
+                (lo[2] - B.lo[2]) * L->pz[b];
+        x.buf = pos;
+        x.fpy = L->py[b];
+        x.fpz = L->pz[b];
+        x.ex = (int)C.ext[0];
+        x.ey = (int)C.ext[1];
+        x.ez = (int)C.ext[2];
+        x.dom = B.domain;
+        x.second = (int)npts;
+        const int64_t n = C.ext[0] * C.ext[1] * C.ext[2];
+        // the field rectangle lies in the field; its first-field run
+        // [pos, pos + n) lies in the peer's first-field run [start, end),
+        // so its second-field run (npts later) lies in [end, end + npts)
+        if (!rect_in_field(x.fld, x.fpy, x.fpz, x.ex, x.ey, x.ez, L->field_size) ||
+            pos + n > end)
+          return list_error("exchange-buffer");
+        pos += n;
+        xs.push_back(x);
+        add_chunks((int)xs.size() - 1, n, chunks, dev::kGatherChunk);
+      }
+      if (pos != end) return list_error("exchange-buffer");
+    }
+    int rc = upload(dir ? &D->xrecv : &D->xsend, xs);
+    if (!rc) rc = upload(dir ? &D->xrecv_chunks : &D->xsend_chunks, chunks);
+    if (rc) return rc;
+    (dir ? D->nxrecv_chunks : D->nxsend_chunks) = (int)chunks.size();
+  }
+  return SC_OK;
 }
 
 static int init_device(sc_level* L, int cur) {
@@ -360,6 +416,8 @@ static int init_device(sc_level* L, int cur) {
   D->npchunks = (int)pchunks.size();
   D->nichunks = (int)ichunks.size();
   D->nschunks = (int)schunks.size();
+
+  if (L->partial && (rc = build_xfer_lists(L))) return rc;
 
   std::vector<double> inv(nd), h3(nd);
   for (int d = 0; d < nd; ++d) {
@@ -655,35 +713,38 @@ static cudaError_t enq_pair(const Enq& q, dev::PairArgs a, bool second) {
 // ndom) holds the bounds of (u, pi), Y = emax[2 ndom, 4 ndom) those of w_2;
 // each gather zeroes the slots that the pass after it accumulates into.  If
 // lapw is not NULL, lapw[s] receives C_{s+1} L w_s.u as enq_step records it.
-static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* const* W,
-                                  double* const* lapw = nullptr) {
+static cudaError_t enq_pass(const Enq& q, double* u, double* pi, double* const* W, int pass,
+                            double* const* lapw = nullptr) {
   DeviceState* D = q.L->dev;
   const int nd = (int)q.L->doms.size();
   const bool fixed = q.L->arith == SC_ARITH_FIXED;
   unsigned* X = D->emax;
   unsigned* Y = D->emax + 2 * nd;
-  cudaError_t e = enq_fill2(q, u, pi, fixed ? Y : nullptr);
-  if (e != cudaSuccess) return e;
   dev::PairArgs a{};
   a.ndom = nd;
   a.boxes = D->boxes;
-  a.s0 = u;
-  a.s1 = pi;
   a.yu = u;
   a.yp = pi;
   a.q = W[4];
-  a.x = W[5];
-  a.out_u = W[0];
-  a.out_p = W[1];
-  a.ly = W[2];
   a.coef = D->coef;
-  a.emax_in = X;
-  a.emax_out = Y;
   a.err = D->err;
-  a.rec0 = lapw ? lapw[0] : nullptr;
-  a.rec1 = lapw ? lapw[1] : nullptr;
-  if ((e = enq_pair(q, a, false)) != cudaSuccess) return e;
-  if ((e = enq_fill2(q, W[0], W[1], fixed ? X : nullptr)) != cudaSuccess) return e;
+  if (pass == 0) {
+    cudaError_t e = enq_fill2(q, u, pi, fixed ? Y : nullptr);
+    if (e != cudaSuccess) return e;
+    a.s0 = u;
+    a.s1 = pi;
+    a.x = W[5];
+    a.out_u = W[0];
+    a.out_p = W[1];
+    a.ly = W[2];
+    a.emax_in = X;
+    a.emax_out = Y;
+    a.rec0 = lapw ? lapw[0] : nullptr;
+    a.rec1 = lapw ? lapw[1] : nullptr;
+    return enq_pair(q, a, false);
+  }
+  cudaError_t e = enq_fill2(q, W[0], W[1], fixed ? X : nullptr);
+  if (e != cudaSuccess) return e;
   a.s0 = W[0];
   a.s1 = W[1];
   a.x = W[2];
@@ -695,6 +756,13 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
   a.rec0 = lapw ? lapw[2] : nullptr;
   a.rec1 = lapw ? lapw[3] : nullptr;
   return enq_pair(q, a, true);
+}
+
+static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* const* W,
+                                  double* const* lapw = nullptr) {
+  cudaError_t e = enq_pass(q, u, pi, W, 0, lapw);
+  if (e != cudaSuccess) return e;
+  return enq_pass(q, u, pi, W, 1, lapw);
 }
 
 // Prologue of a run of steps: the ghosts of u gathered (push exchange); the
@@ -856,6 +924,10 @@ int sc_level_rk4_step(sc_level* L, double* u, double* pi, const double* c2, cons
     return set_error(SC_EINVAL,
                      "a level with a non-periodic domain takes one step per call (its "
                      "boundary ghosts are refreshed between steps)");
+  if (L->partial)
+    return set_error(SC_EINVAL,
+                     "distributed level: step it with sc_dist_rk4_begin and sc_dist_rk4_pass, "
+                     "with the exchange of sc_dist_pack / sc_dist_unpack between passes");
   int rc = ensure_device(L);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -922,6 +994,102 @@ int sc_level_sync(sc_level* L, void* stream) {
   return SC_OK;
 }
 
+// ---- distributed level: exchange and split step ------------------------
+
+static int dist_fields(sc_level* L, int32_t which, const double* u, const double* pi,
+                       double** f, double** g) {
+  if (which == SC_DIST_STATE) {
+    if (!aligned16(u) || !aligned16(pi))
+      return set_error(SC_EINVAL, "u, pi must be 16-byte aligned device pointers");
+    *f = const_cast<double*>(u);
+    *g = const_cast<double*>(pi);
+    return SC_OK;
+  }
+  if (which != SC_DIST_STAGE) return set_error(SC_EINVAL, "which must be SC_DIST_STATE or SC_DIST_STAGE");
+  double* W[6];
+  const int rc = scratch4(L, W);
+  if (rc) return rc;
+  *f = W[0];
+  *g = W[1];
+  return SC_OK;
+}
+
+static int dist_xfer(sc_level* L, bool pack, int32_t which, const double* u, const double* pi,
+                     double* buf, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!L->partial) return set_error(SC_EINVAL, "not a distributed level (sc_dist_create)");
+  const int64_t need = pack ? L->send_doubles : L->recv_doubles;
+  if (need > 0 && (!buf || (reinterpret_cast<uintptr_t>(buf) & 7)))
+    return set_error(SC_EINVAL, "exchange buffer must be an 8-byte aligned device pointer");
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  double *f, *g;
+  if ((rc = dist_fields(L, which, u, pi, &f, &g))) return rc;
+  DeviceState* D = L->dev;
+  const int nd = (int)L->doms.size();
+  unsigned* emax = nullptr;
+  if (!pack && L->arith == SC_ARITH_FIXED)  // X: bounds of (u, pi); Y: of w_2
+    emax = which == SC_DIST_STATE ? D->emax : D->emax + 2 * nd;
+  const int n = pack ? D->nxsend_chunks : D->nxrecv_chunks;
+  if (n > 0) L->launches++;
+  SC_CUDA(dev::launch_xfer(pack, pack ? D->xsend : D->xrecv,
+                           pack ? D->xsend_chunks : D->xrecv_chunks, n, f, g, buf, emax, nd,
+                           D->grid_small, (cudaStream_t)stream));
+  return SC_OK;
+}
+
+int sc_dist_pack(sc_level* L, int32_t which, const double* u, const double* pi, double* send,
+                 void* stream) {
+  return dist_xfer(L, true, which, u, pi, send, stream);
+}
+
+int sc_dist_unpack(sc_level* L, int32_t which, const double* recv, double* u, double* pi,
+                   void* stream) {
+  return dist_xfer(L, false, which, u, pi, const_cast<double*>(recv), stream);
+}
+
+int sc_dist_rk4_begin(sc_level* L, double* u, double* pi, const double* c2, const double* dt,
+                      int32_t ndt, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!L->partial) return set_error(SC_EINVAL, "not a distributed level (sc_dist_create)");
+  if (!aligned16(u) || !aligned16(pi) || !aligned16(c2))
+    return set_error(SC_EINVAL, "u, pi, c2 must be 16-byte aligned device pointers");
+  if (u == pi) return set_error(SC_EINVAL, "u and pi must be different buffers");
+  L->dist_begun = false;
+  int rc = ensure_device(L);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = set_coef(L, dt, ndt, s))) return rc;
+  double* W[6];
+  if ((rc = scratch4(L, W))) return rc;
+  Enq q{L, s, &L->launches, false};
+  SC_CUDA(enq_prologue(q, u, pi, c2, W));
+  L->dist_begun = true;
+  L->dist_next_pass = 0;
+  L->dist_u = u;
+  L->dist_pi = pi;
+  return SC_OK;
+}
+
+int sc_dist_rk4_pass(sc_level* L, double* u, double* pi, int32_t pass, void* stream) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!L->partial) return set_error(SC_EINVAL, "not a distributed level (sc_dist_create)");
+  if (!L->dist_begun) return set_error(SC_EINVAL, "no run: call sc_dist_rk4_begin first");
+  if (pass != 0 && pass != 1) return set_error(SC_EINVAL, "pass must be 0 or 1");
+  if (pass != L->dist_next_pass)
+    return set_error(SC_EINVAL, pass ? "pass 1 needs pass 0 of the step first"
+                                     : "pass 0 needs the previous step's pass 1 first");
+  if (u != L->dist_u || pi != L->dist_pi)
+    return set_error(SC_EINVAL, "u, pi must be the buffers given to sc_dist_rk4_begin");
+  double* W[6];
+  int rc = scratch4(L, W);
+  if (rc) return rc;
+  Enq q{L, (cudaStream_t)stream, &L->launches, false};
+  SC_CUDA(enq_pass(q, u, pi, W, pass));
+  L->dist_next_pass = 1 - pass;
+  return SC_OK;
+}
+
 // Forward sweep keeping a checkpoint every K steps (the tape of the level).
 int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, const double* c2,
                           const double* dt, int32_t ndt, int32_t nsteps, int32_t ckpt_every,
@@ -932,6 +1100,7 @@ int sc_level_forward_tape(sc_level* L, const double* u0, const double* pi0, cons
     return set_error(SC_EINVAL, "fields must be 16-byte aligned device pointers");
   if (nsteps < 0 || ckpt_every < 1) return set_error(SC_EINVAL, "nsteps < 0 or ckpt_every < 1");
   if (!L->all_periodic) return set_error(SC_EINVAL, "needs domains periodic on every axis");
+  if (L->partial) return set_error(SC_EINVAL, "the adjoint of a distributed level is not built");
   int rc = ensure_device(L);
   if (rc) return rc;
   DeviceState* D = L->dev;

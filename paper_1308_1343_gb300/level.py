@@ -78,6 +78,15 @@ class Level:
                  domains: Sequence[dict], ghost: int = 2):
         lib = B.lib()
         nb, nd = len(boxes), len(domains)
+        cb, cd = self._c_arrays(boxes, domains)
+        h = ctypes.c_void_p()
+        B.check(lib.sc_level_create(cb, nb, cd, nd, int(ghost), ctypes.byref(h)))
+        self._adopt(h, boxes, domains)
+
+    @staticmethod
+    def _c_arrays(boxes, domains):
+        """ctypes arrays of sc_box and sc_domain."""
+        nb, nd = len(boxes), len(domains)
         cb = (B.ScBox * max(nb, 1))()
         for i, (lo, hi, d) in enumerate(boxes):
             cb[i].lo[:] = [int(v) for v in lo]
@@ -89,14 +98,18 @@ class Level:
             cd[i].hi[:] = [int(v) for v in D["hi"]]
             cd[i].h = float(D["h"])
             cd[i].periodic = int(D.get("periodic", 7))
-        h = ctypes.c_void_p()
-        B.check(lib.sc_level_create(cb, nb, cd, nd, int(ghost), ctypes.byref(h)))
+        return cb, cd
+
+    def _adopt(self, h, boxes, domains):
+        """Take ownership of level handle h whose stored boxes are `boxes`."""
+        lib = B.lib()
         self._h = h
         self.boxes = [(tuple(int(v) for v in lo), tuple(int(v) for v in hi), int(d))
                       for lo, hi, d in boxes]
         self.domains = [dict(lo=tuple(D.get("lo", (0, 0, 0))), hi=tuple(D["hi"]),
                              h=float(D["h"]), periodic=int(D.get("periodic", 7)))
                         for D in domains]
+        nb = len(self.boxes)
         n = ctypes.c_int64()
         B.check(lib.sc_level_field_size(h, ctypes.byref(n)))
         self.field_size = n.value

@@ -27,7 +27,7 @@ def B():
 
 def _declared_functions():
     names = []
-    for h in ("sc_level.h", "sc_bboxset.h", "sc_hierarchy.h"):
+    for h in ("sc_level.h", "sc_bboxset.h", "sc_hierarchy.h", "sc_dist.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names += re.findall(r"\b(sc_\w+)\s*\(", src)
