@@ -203,6 +203,33 @@ int sc_level_get_fusion(const sc_level* level, int32_t* stages_per_pass);
 int sc_level_set_staging(sc_level* level, int32_t staging);
 int sc_level_get_staging(const sc_level* level, int32_t* staging);
 
+/* Kernels of the two-stage passes (sc_level_set_fusion(2)):
+ *  SC_PASS_ONE_ROLE: every warp of a CTA converts, sums and runs the RK
+ *    epilogue of its points, one barrier per plane (256 threads, two CTAs
+ *    per SM);
+ *  SC_PASS_WARP_SPECIALISED: 8 producer warps convert and form the sums,
+ *    4 consumer warps run the epilogue, handing each plane's sums over
+ *    through a ring of shared-memory slots guarded by mbarriers, so the
+ *    FP64 epilogue runs beside the integer work of the next planes (384
+ *    threads, two CTAs per SM; the roles take 96 and 48 registers).  Every
+ *    wait inside it is bounded (1 s); a wait that gives up ends the kernel
+ *    and sets the device error word (SC_EDEVICE at sc_level_sync).
+ * Results are bit-identical.  Setting it fixes it; until then
+ * sc_level_autotune times both and keeps the faster.  Errors: SC_EINVAL. */
+#define SC_PASS_ONE_ROLE 0
+#define SC_PASS_WARP_SPECIALISED 1
+int sc_level_set_pass_kernel(sc_level* level, int32_t kind);
+int sc_level_get_pass_kernel(const sc_level* level, int32_t* kind);
+
+/* For tests of failure detection: the next launch of a warp-specialised
+ * pass kernel on this level (batched or per-box mode, not a graph captured
+ * earlier) withholds the consumers' release of its ring slots, so the
+ * producers' bounded wait runs out after 1 s; the kernel returns early and
+ * sc_level_sync reports SC_EDEVICE.  The fields it was writing are then
+ * undefined.  One shot.  SC_EINVAL unless the level runs the
+ * warp-specialised two-stage passes. */
+int sc_level_arm_wait_test(sc_level* level);
+
 /* Number of box-size classes and the class of each box (boxes are grouped
  * by interior extent rounded up to a multiple of 8 per axis). */
 int sc_level_size_classes(const sc_level* level, int32_t* nclasses,

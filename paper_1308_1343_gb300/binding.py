@@ -18,6 +18,7 @@ SC_ARITH_FP64, SC_ARITH_FIXED = 0, 1
 SC_STAGING_REGISTERS, SC_STAGING_SHARED = 0, 1
 SC_MODE_GRAPH, SC_MODE_PER_BOX, SC_MODE_BATCHED, SC_MODE_TIMED = 0, 1, 2, 3
 SC_SET_UNION, SC_SET_INTERSECTION, SC_SET_DIFFERENCE, SC_SET_XOR = 0, 1, 2, 3
+SC_PASS_ONE_ROLE, SC_PASS_WARP_SPECIALISED = 0, 1
 SC_DIST_GREEDY, SC_DIST_BISECT = 0, 1
 SC_DIST_STATE, SC_DIST_STAGE = 0, 1
 (SC_KERNEL_STAGE, SC_KERNEL_GATHER, SC_KERNEL_STAGE_RECORD, SC_KERNEL_ADJ_A, SC_KERNEL_ADJ_B,
@@ -69,6 +70,9 @@ _SIGS = {
     "sc_level_set_staging": (_i32, [_vp, _i32]),
     "sc_level_get_staging": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "sc_level_autotune": (_i32, [_vp, _i32, _dbl, _dbl, ctypes.c_char_p, _vp]),
+    "sc_level_set_pass_kernel": (_i32, [_vp, _i32]),
+    "sc_level_get_pass_kernel": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "sc_level_arm_wait_test": (_i32, [_vp]),
     "sc_level_fill_ghosts": (_i32, [_vp, _vp, _vp]),
     "sc_level_apply_laplacian": (_i32, [_vp, _vp, _vp, _vp]),
     "sc_level_rk4_step": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl), _i32, _i32, _i32,

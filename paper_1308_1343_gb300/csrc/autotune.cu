@@ -36,8 +36,9 @@ const int kTx[] = {16, 32, 64};
 
 std::string cache_key(const sc_level* L, const SizeClass& c) {
   std::ostringstream k;
-  k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|f" << L->fuse << "|"
-    << c.ext[0] << "," << c.ext[1] << "," << c.ext[2];
+  k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|f" << L->fuse
+    << (L->fuse == 2 && L->pass_ws ? "w" : "") << "|" << c.ext[0] << "," << c.ext[1] << ","
+    << c.ext[2];
   return k.str();
 }
 
@@ -129,7 +130,7 @@ struct Timer {
     p.emax_in = D->emax;
     p.emax_out = D->emax + 2 * nd;
     p.err = D->err;
-    dev::launch_pair(L->arith, false, p, D->grid_pair, s);
+    launch_pass(L, false, p, s);
     p.s0 = W[2];
     p.s1 = W[3];
     p.x = c2;
@@ -138,7 +139,7 @@ struct Timer {
     p.ly = nullptr;
     p.emax_in = D->emax + 2 * nd;
     p.emax_out = D->emax;
-    dev::launch_pair(L->arith, true, p, D->grid_pair, s);
+    launch_pass(L, true, p, s);
   }
 
   // Median time (microseconds) of what one stencil pass of the level's

@@ -108,6 +108,7 @@ constexpr int kGatherChunk = 256;  // ghost gather: one point per thread
 constexpr unsigned kErrNonFinite = 1u;   // Inf/NaN reached the fixed-point path
 constexpr unsigned kErrScale = 2u;       // an input exceeded its domain bound
 constexpr unsigned kErrBounds = 4u;      // checked build: an index left its box
+constexpr unsigned kErrTimeout = 8u;     // a bounded wait inside a kernel gave up
 
 }  // namespace dev
 }  // namespace sc

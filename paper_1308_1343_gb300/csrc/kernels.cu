@@ -15,6 +15,7 @@
 // L w_1.u and L w_3.u by linearity from the stencils of the pass's two
 // fields (15 doubles per point per step; see PairEpi).
 #include "kernels.cuh"
+#include "kernels_ws.cuh"
 #include "launch.hpp"
 
 namespace sc {
@@ -446,6 +447,64 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
     run_items<NT, 2>(it, bx, F, ar, smem, err, epi);
     if (A::kFixed)
       cta_max2_to(epi.eu, epi.ep, a.emax_out + bx.dom, a.emax_out + a.ndom + bx.dom, red);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+// The same passes with the warp-specialised traversal (kernels_ws.cuh):
+// producer warps form the sums, consumer warps run PairEpi on them.  Results
+// are bit-identical to pair_kernel.
+template <class A, bool SECOND, bool RECORD>
+__global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
+  __shared__ WsSmem<A> sm;
+  ws_init(sm);
+  unsigned err = 0, g = 0;
+  bool ok = true;
+  // registers: the CTA is launched with 80 per thread (two CTAs of 384
+  // threads per SM); producers take 96 and consumers give back to 48:
+  // 256 * 96 + 128 * 48 == 384 * 80, the launch allocation
+  if (threadIdx.x < kWsProducers) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 96;\n" ::: "memory");
+    const double* const F[2] = {a.s0, a.s1};
+    for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
+      const DItem it = a.items[i];
+      const DBox bx = a.boxes[it.box];
+      const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
+                       make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
+      ok = ws_produce(it, bx, F, ar, sm, err, g);
+    }
+  } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 48;\n" ::: "memory");
+    for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
+      const DItem it = a.items[i];
+      const DBox bx = a.boxes[it.box];
+      unsigned e2 = 0;  // a bad bound is reported by the producers
+      const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, e2),
+                       make_arith<A>(a.emax_in + a.ndom, bx.dom, e2)};
+      const int s0 = SECOND ? 2 : 0;
+      const StageCoef* ca = a.coef + s0 * a.ndom + bx.dom;
+      const StageCoef* cb = ca + a.ndom;
+      PairEpi<A, SECOND, RECORD> epi{{a.yu, a.yp, a.q, a.x}, a.out_u, a.out_p, a.ly, a.rec0,
+                                     a.rec1, ar[0], ar[1], ca->gamma, cb->gamma,
+                                     RECORD ? ca->rec : 0.0, RECORD ? cb->rec : 0.0, 0u, 0u};
+      ok = ws_consume(it, bx, sm, err, g, epi, a.stall);
+      // one verdict per warp before the warp-wide reduction (a lane whose
+      // wait gave up must not leave the others in a collective)
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok && A::kFixed) {
+        // exponent bounds of the item's outputs: one atomicMax per warp
+        const unsigned eu = __reduce_max_sync(0xffffffffu, epi.eu);
+        const unsigned ep = __reduce_max_sync(0xffffffffu, epi.ep);
+        if ((threadIdx.x & 31) == 0) {
+          if (eu) atomicMax(a.emax_out + bx.dom, eu);
+          if (ep) atomicMax(a.emax_out + a.ndom + bx.dom, ep);
+        }
+      }
+    }
+  }
+  if (!ok) {
+    reinterpret_cast<volatile int&>(sm.abort) = 1;
+    err |= kErrTimeout;
   }
   if (err) atomicOr(a.err, err);
 }
@@ -940,6 +999,14 @@ static void set_carveouts() {
   prefer_shared(pair_kernel<FixedI, true, true>);
   prefer_shared(pair_kernel<Fp64, false, true>);
   prefer_shared(pair_kernel<Fp64, true, true>);
+  prefer_shared(pair_ws_kernel<FixedI, false, false>);
+  prefer_shared(pair_ws_kernel<FixedI, true, false>);
+  prefer_shared(pair_ws_kernel<Fp64, false, false>);
+  prefer_shared(pair_ws_kernel<Fp64, true, false>);
+  prefer_shared(pair_ws_kernel<FixedI, false, true>);
+  prefer_shared(pair_ws_kernel<FixedI, true, true>);
+  prefer_shared(pair_ws_kernel<Fp64, false, true>);
+  prefer_shared(pair_ws_kernel<Fp64, true, true>);
   prefer_shared(adj2_kernel<FixedI, false>);
   prefer_shared(adj2_kernel<FixedI, true>);
   prefer_shared(adj2_kernel<Fp64, false>);
@@ -1035,6 +1102,38 @@ cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cud
           : pair_kernel<Fp64, false, false><<<grid, NT, 0, s>>>(a);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_pair_ws(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s) {
+  if (a.nitems <= 0) return cudaSuccess;
+  set_carveouts();
+  grid = min(grid, a.nitems);
+  const bool rec = a.rec0 != nullptr;
+  if (arith == 1) {
+    if (second)
+      rec ? pair_ws_kernel<FixedI, true, true><<<grid, kWsThreads, 0, s>>>(a)
+          : pair_ws_kernel<FixedI, true, false><<<grid, kWsThreads, 0, s>>>(a);
+    else
+      rec ? pair_ws_kernel<FixedI, false, true><<<grid, kWsThreads, 0, s>>>(a)
+          : pair_ws_kernel<FixedI, false, false><<<grid, kWsThreads, 0, s>>>(a);
+  } else {
+    if (second)
+      rec ? pair_ws_kernel<Fp64, true, true><<<grid, kWsThreads, 0, s>>>(a)
+          : pair_ws_kernel<Fp64, true, false><<<grid, kWsThreads, 0, s>>>(a);
+    else
+      rec ? pair_ws_kernel<Fp64, false, true><<<grid, kWsThreads, 0, s>>>(a)
+          : pair_ws_kernel<Fp64, false, false><<<grid, kWsThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pair_ws_occupancy(int arith, int* blocks_per_sm) {
+  set_carveouts();
+  if (arith == 1)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, pair_ws_kernel<FixedI, true, true>, kWsThreads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, pair_ws_kernel<Fp64, true, true>, kWsThreads, 0);
 }
 
 cudaError_t pair_occupancy(int arith, int* blocks_per_sm) {

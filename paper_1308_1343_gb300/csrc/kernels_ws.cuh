@@ -1,0 +1,386 @@
+// Warp-specialised traversal of the two-stage pass kernels (sm_103a).
+//
+// The one-role traversal (run_items in kernels.cuh) keeps every warp of a CTA
+// in the same phase -- one barrier per plane -- so the integer work of the
+// fixed-point sums and the FP64 work of the RK epilogue of one CTA do not run
+// at the same time, and the registers of both bound the warps per SM.  Here a
+// CTA of 384 threads splits the work of each plane between two roles:
+//
+//  * 8 producer warps (256 threads) own the tile as before: thread (lx, ly)
+//    holds the two x-adjacent points of its column, keeps the five z-values of
+//    both stencil fields in registers, stages the raw column and halo values
+//    of the coming planes by cp.async, converts them and forms the two 13-term
+//    sums of both fields.  They synchronise among themselves once per plane
+//    (the in-plane neighbours live in shared memory) and write the sums of
+//    each plane to a ring of shared-memory slots;
+//  * 4 consumer warps (128 threads, two point pairs each) take the sums of a
+//    plane from the ring, stream the pointwise fields of their pairs by
+//    cp.async one plane ahead, and run the epilogue (the int64 -> FP64
+//    conversion of the sums, the FP64 FMAs, the stores, the exponent bounds).
+//
+// Producers and consumers hand over through mbarriers ("full" slot: the
+// producers' 256 arrivals; "empty" slot: the consumers' 128 arrivals), so the
+// two roles drift by up to kWsRing planes and the FP64 pipe runs beside the
+// integer pipes.  The arithmetic of every point is that of run_items with the
+// same epilogue: results are bit-identical to the one-role kernels.
+//
+// Every wait is bounded: a wait that has not seen its phase complete within
+// kWsWaitNs (1 s) gives up, sets the CTA's abort flag and returns false; the
+// other threads of the CTA see the flag in their own waits and return as
+// well, and the kernel records kErrTimeout in the device error word, which
+// sc_level_sync reports as SC_EDEVICE.  There are no named barriers after the
+// start, so a thread that gives up cannot leave others blocked.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace sc {
+namespace dev {
+
+constexpr int kWsProducers = 256;  // 8 warps
+constexpr int kWsConsumers = 128;  // 4 warps: one per SM sub-partition
+constexpr int kWsThreads = kWsProducers + kWsConsumers;
+constexpr int kWsRing = 2;  // sum slots: producers run at most 2 planes ahead
+constexpr unsigned long long kWsWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+// arrive (release semantics: this thread's earlier shared-memory writes are
+// visible to a thread whose wait on the phase succeeds)
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+
+// true once the phase of parity `parity` has completed (acquire semantics)
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity`: false if kWsWaitNs pass
+// first or another thread of the CTA has given up (*abort != 0).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 31u) == 0u && (*abort != 0 || global_ns() - t0 > kWsWaitNs)) return false;
+  }
+}
+
+// Shared memory of one warp-specialised CTA (two stencil fields, four
+// pointwise fields): about 107 KB, two CTAs per SM.
+template <class A>
+struct WsSmem {
+  typename A::T tile[2 * 2 * TileSmem<kWsProducers>::kMaxElems];  // [field][plane parity]
+  double2 hraw[2][2][kWsProducers];   // [plane parity][field][producer]
+  double2 craw[2][2][kWsProducers];
+  typename A::T2 ring[kWsRing][2][kWsProducers];  // sums at (point A, point B)
+  double2 pw[2][4][kWsProducers];     // [plane parity][field][pair]
+  unsigned long long full[kWsRing];
+  unsigned long long empty[kWsRing];
+  unsigned long long tbar;            // producers: plane tile complete
+  int abort;
+};
+
+template <class A>
+__device__ __forceinline__ void ws_init(WsSmem<A>& sm) {
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < kWsRing; ++r) {
+      mbar_init(&sm.full[r], kWsProducers);
+      mbar_init(&sm.empty[r], kWsConsumers);
+    }
+    mbar_init(&sm.tbar, kWsProducers);
+    sm.abort = 0;
+  }
+  __syncthreads();
+}
+
+// Producer role for one work item (threads 0..255).  g counts the planes the
+// CTA has handed over since the launch (ring slot and barrier phases follow
+// it).  Returns false if a wait gave up.
+template <class A>
+__device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
+                                           const double* const (&F)[2], const A (&arith)[2],
+                                           WsSmem<A>& sm, unsigned& err, unsigned& g) {
+  using T = typename A::T;
+  using T2 = typename A::T2;
+  const int txh = it.txh;
+  const int TY = kWsProducers / txh;
+  const int TX = 2 * txh;
+  const int W = TX + 4;
+  const int bufElems = W * (TY + 4);
+  const int tid = threadIdx.x;
+  const int lx = tid % txh, ly = tid / txh;
+  const int gx = it.x0 + 2 * lx, gy = it.y0 + ly;
+  const bool colLoad = (gx < bx.nx + 2) && (gy < bx.ny + 2);
+  const bool actA = (gx < bx.nx) && (gy < bx.ny);
+  const int pz = (int)bx.pz;
+  const bool wrap = bx.wrap != 0;
+  auto wr = [wrap](int c, int n) { return !wrap ? c : (c < 0 ? c + n : (c >= n ? c - n : c)); };
+  const int off0 = (int)bx.off, py = (int)bx.py;
+#ifdef SC_BOUNDS_CHECK
+  const int blk0 = off0 - 2 - 2 * py - 2 * pz;
+  const int blk1 = off0 - 3 + py + (bx.ny + 1) * py + (bx.nz + 1) * pz;
+  auto ck = [&](int i) {
+    if (i < blk0 || i + 1 > blk1) {
+      err |= kErrBounds;
+      return off0;
+    }
+    return i;
+  };
+#else
+  auto ck = [](int i) { return i; };
+#endif
+  const int colOff = colLoad ? off0 + wr(gx, bx.nx) + wr(gy, bx.ny) * py : off0;
+  const int oy = out_of(gy, bx.ny);
+  const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
+  // this thread's halo pair of the plane tile, if any (at most one: the halo
+  // of a tile has 4 txh + 2 TY <= 256 pairs for every allowed shape)
+  const int nhalo = 4 * txh + 2 * TY;
+  const bool hasH = tid < nhalo;
+  int hs = 0, hg = off0, hx0 = 2, hx1 = 2;
+  if (hasH) {
+    int hx, hy;
+    if (tid < 4 * txh) {
+      const int r = tid / txh;
+      hx = 2 * (tid - r * txh);
+      hy = r < 2 ? r - 2 : TY + r - 2;
+    } else {
+      const int j = tid - 4 * txh;
+      const int side = j / TY;
+      hy = j - side * TY;
+      hx = side ? TX : -2;
+    }
+    const int ax = it.x0 + hx, ay = it.y0 + hy;
+    hs = (hy + 2) * W + hx + 2;
+    if (ax < bx.nx + 2 && ay < bx.ny + 2) {
+      hg = off0 + wr(ax, bx.nx) + wr(ay, bx.ny) * py;
+      const int o = out_of(ay, bx.ny);
+      hx0 = out_of(ax, bx.nx) + o;
+      hx1 = out_of(ax + 1, bx.nx) + o;
+    }
+  }
+  auto conv_at = [&](int f, double2 raw, int k) -> T2 {
+    const int oz = out_of(k, bx.nz);
+    return arith[f].conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
+  };
+  int oc = colOff + (it.z0 + 2) * pz;  // next column load (plane k+2)
+  int oh = hg + it.z0 * pz;            // next halo load (plane k)
+  // raw halo pairs of plane k and column pairs of plane k+2, by cp.async
+  auto stage_raw = [&](int buf) {
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      if (hasH) cp_async16(&sm.hraw[buf][f][tid], F[f] + ck(oh));
+#pragma unroll
+    for (int f = 0; f < 2; ++f) cp_async16(&sm.craw[buf][f][tid], F[f] + ck(oc));
+    oh += pz;
+    oc += pz;
+    cp_async_commit();
+  };
+  T2 qa[2], qb[2], qc[2], qd[2], qe[2];
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    qa[f] = conv_at(f, ld2(F[f] + ck(oc - 4 * pz)), it.z0 - 2);
+    qb[f] = conv_at(f, ld2(F[f] + ck(oc - 3 * pz)), it.z0 - 1);
+    qc[f] = conv_at(f, ld2(F[f] + ck(oc - 2 * pz)), it.z0);
+    qd[f] = conv_at(f, ld2(F[f] + ck(oc - pz)), it.z0 + 1);
+  }
+  stage_raw(g & 1);
+  const int rowSelf = (ly + 2) * W + 2 * lx + 2;
+  // one plane: m2..p1 hold planes k-2..k+1; p2 receives plane k+2
+  auto plane = [&](int kk, const T2 (&m2)[2], const T2 (&m1)[2], const T2 (&c0)[2],
+                   const T2 (&p1)[2], T2 (&p2)[2]) -> bool {
+    const int k = it.z0 + kk;
+    const int oz = out_of(k, bx.nz);
+    const int tb = (int)(g & 1u);
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      *reinterpret_cast<T2*>(sm.tile + (2 * f + tb) * bufElems + rowSelf) = c0[f];
+    if (kk + 1 < it.nzr)
+      stage_raw(tb ^ 1);
+    else
+      cp_async_commit();
+    cp_async_wait_one();  // this thread's raw values of plane k have landed
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      if (hasH)
+        *reinterpret_cast<T2*>(sm.tile + (2 * f + tb) * bufElems + hs) =
+            arith[f].conv(sm.hraw[tb][f][tid], hx0 + oz <= 1, hx1 + oz <= 1, err);
+      p2[f] = conv_at(f, sm.craw[tb][f][tid], k + 2);
+    }
+    // every producer has written plane k's tile
+    mbar_arrive(&sm.tbar);
+    if (!mbar_wait(&sm.tbar, g & 1u, &sm.abort)) return false;
+    T rA[2], rB[2];
+    if (actA) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        const T* row = sm.tile + (2 * f + tb) * bufElems + rowSelf;
+        const T2 xm = *reinterpret_cast<const T2*>(row - 2);
+        const T2 xp = *reinterpret_cast<const T2*>(row + 2);
+        const T2 ym1 = *reinterpret_cast<const T2*>(row - W);
+        const T2 ym2 = *reinterpret_cast<const T2*>(row - 2 * W);
+        const T2 yp1 = *reinterpret_cast<const T2*>(row + W);
+        const T2 yp2 = *reinterpret_cast<const T2*>(row + 2 * W);
+        rA[f] = A::lap(c0[f].x, xm.y, c0[f].y, ym1.x, yp1.x, m1[f].x, p1[f].x, xm.x, xp.x,
+                       ym2.x, yp2.x, m2[f].x, p2[f].x);
+        rB[f] = A::lap(c0[f].y, c0[f].x, xp.x, ym1.y, yp1.y, m1[f].y, p1[f].y, xm.y, xp.y,
+                       ym2.y, yp2.y, m2[f].y, p2[f].y);
+      }
+    }
+    // hand the sums over: the slot is free once the consumers released it
+    const unsigned slot = g % kWsRing;
+    if (!mbar_wait(&sm.empty[slot], ((g / kWsRing) & 1u) ^ 1u, &sm.abort)) return false;
+    if (actA) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        T2 s;
+        s.x = rA[f];
+        s.y = rB[f];
+        sm.ring[slot][f][tid] = s;
+      }
+    }
+    mbar_arrive(&sm.full[slot]);
+    ++g;
+    return true;
+  };
+  // unrolled by the queue length so the five z-values never move
+  bool ok = true;
+  for (int kk = 0;;) {
+    if (!(ok = plane(kk, qa, qb, qc, qd, qe))) break;
+    if (++kk >= it.nzr) break;
+    if (!(ok = plane(kk, qb, qc, qd, qe, qa))) break;
+    if (++kk >= it.nzr) break;
+    if (!(ok = plane(kk, qc, qd, qe, qa, qb))) break;
+    if (++kk >= it.nzr) break;
+    if (!(ok = plane(kk, qd, qe, qa, qb, qc))) break;
+    if (++kk >= it.nzr) break;
+    if (!(ok = plane(kk, qe, qa, qb, qc, qd))) break;
+    if (++kk >= it.nzr) break;
+  }
+  cp_async_wait_all();
+  return ok;
+}
+
+// Consumer role for one work item (threads 256..383): pairs ctid and
+// ctid + 128 of the tile.  For every plane it calls
+//   epi.point(idx, pw, rA, rB, actB, x, y, k)
+// exactly as run_items does.  stall != 0 (failure-detection tests only):
+// the consumers never release a slot, so the producers' wait for a free slot
+// runs out.  Returns false if a wait gave up.
+template <class A, class Epi>
+__device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, WsSmem<A>& sm,
+                                           unsigned& err, unsigned& g, Epi& epi, int stall) {
+  using T = typename A::T;
+  using T2 = typename A::T2;
+  const int ctid = threadIdx.x - kWsProducers;
+  const int txh = it.txh;
+  const int pz = (int)bx.pz, py = (int)bx.py, off0 = (int)bx.off;
+#ifdef SC_BOUNDS_CHECK
+  const int blk0 = off0 - 2 - 2 * py - 2 * pz;
+  const int blk1 = off0 - 3 + py + (bx.ny + 1) * py + (bx.nz + 1) * pz;
+  auto ck = [&](int i) {
+    if (i < blk0 || i + 1 > blk1) {
+      err |= kErrBounds;
+      return off0;
+    }
+    return i;
+  };
+  auto ok_pt = [&](int i, int x, int y, int z, bool two) {
+    const bool ok = x >= 0 && x + (two ? 1 : 0) < bx.nx && y >= 0 && y < bx.ny && z >= 0 &&
+                    z < bx.nz && i == off0 + x + y * py + z * pz;
+    if (!ok) err |= kErrBounds;
+    return ok;
+  };
+#else
+  auto ck = [](int i) { return i; };
+  auto ok_pt = [](int, int, int, int, bool) { return true; };
+#endif
+  int t[2], gxs[2], gys[2], op[2], oi[2];
+  bool actA[2], actB[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    t[j] = ctid + kWsConsumers * j;
+    const int lx = t[j] % txh, ly = t[j] / txh;
+    gxs[j] = it.x0 + 2 * lx;
+    gys[j] = it.y0 + ly;
+    actA[j] = gxs[j] < bx.nx && gys[j] < bx.ny;
+    actB[j] = gxs[j] + 1 < bx.nx && gys[j] < bx.ny;
+    op[j] = off0 + (actA[j] ? gxs[j] + gys[j] * py : 0) + it.z0 * pz;
+    oi[j] = op[j];
+  }
+  // the pointwise fields of the thread's pairs on the next plane, by cp.async
+  auto stage_pw = [&](int buf) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (actA[j]) {
+#pragma unroll
+        for (int f = 0; f < Epi::NF; ++f) cp_async16(&sm.pw[buf][f][t[j]], epi.f[f] + ck(op[j]));
+      }
+      op[j] += pz;
+    }
+    cp_async_commit();
+  };
+  stage_pw(g & 1);
+  bool ok = true;
+  for (int kk = 0; kk < it.nzr; ++kk) {
+    const int k = it.z0 + kk;
+    const int pb = (int)(g & 1u);
+    if (kk + 1 < it.nzr)
+      stage_pw(pb ^ 1);
+    else
+      cp_async_commit();
+    cp_async_wait_one();  // this thread's pointwise values of plane k have landed
+    const unsigned slot = g % kWsRing;
+    if (!(ok = mbar_wait(&sm.full[slot], (g / kWsRing) & 1u, &sm.abort))) break;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (actA[j] && ok_pt(oi[j], gxs[j], gys[j], k, actB[j])) {
+        T rA[2], rB[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const T2 s = sm.ring[slot][f][t[j]];
+          rA[f] = s.x;
+          rB[f] = s.y;
+        }
+        double2 pw[Epi::NF];
+#pragma unroll
+        for (int f = 0; f < Epi::NF; ++f) pw[f] = sm.pw[pb][f][t[j]];
+        epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k);
+      }
+      oi[j] += pz;
+    }
+    if (!stall) mbar_arrive(&sm.empty[slot]);
+    ++g;
+  }
+  cp_async_wait_all();
+  return ok;
+}
+
+}  // namespace dev
+}  // namespace sc

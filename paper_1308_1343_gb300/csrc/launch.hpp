@@ -74,6 +74,8 @@ struct PairArgs {
   const unsigned* emax_in;  // [2 ndom]: exponent bounds of s0, s1
   unsigned* emax_out;       // [2 ndom]: of out_u, out_p (zero on entry)
   unsigned* err;
+  int stall;                // warp-specialised kernels, failure-detection tests
+                            // only: consumers never release a ring slot
 };
 
 struct LapArgs {
@@ -153,6 +155,9 @@ cudaError_t launch_fwd_stage(int arith, bool record, int staging, const FwdArgs&
 cudaError_t launch_lap(int arith, const LapArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s);
 cudaError_t pair_occupancy(int arith, int* blocks_per_sm);
+// the warp-specialised pass kernels (384 threads: 8 producer, 4 consumer warps)
+cudaError_t launch_pair_ws(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s);
+cudaError_t pair_ws_occupancy(int arith, int* blocks_per_sm);
 // two fields over one exchange list; block 0 zeroes clear[0..nclear)
 cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
                            double* g, unsigned* clear, int nclear, cudaStream_t s);

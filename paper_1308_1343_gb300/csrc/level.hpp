@@ -126,6 +126,7 @@ struct DeviceState {
   int grid_stage = 0;  // persistent grid of the stage kernels
   int grid_stage_s[2] = {0, 0};  // of the one-stage kernel per staging
   int grid_pair = 0;   // persistent grid of the two-stage kernels
+  int grid_pair_ws = 0;  // ... of their warp-specialised form
   int grid_small = 0;  // grid of the gather / reduction kernels
 };
 
@@ -146,6 +147,10 @@ struct sc_level {
                                // in shared memory by cp.async (1)
   bool staging_fixed = false;  // set by sc_level_set_staging; else the autotuner chooses
   int ctas_per_sm = 0;
+  int pass_ws = 0;          // two-stage passes: one-role (0) or warp-specialised (1) kernels
+  bool pass_fixed = false;  // set by sc_level_set_pass_kernel; else the autotuner chooses
+  int wait_test = 0;        // failure-detection tests: the next warp-specialised pass
+                            // launch withholds its ring slots (one shot)
   int version = 0;  // bumps when items change (invalidates graphs)
   int64_t launches = 0;
   int profile = 0;  // time every launch of the taped forward/backward
@@ -169,3 +174,17 @@ struct sc_level {
   const double* dist_pi = nullptr;
   sc::DeviceState* dev = nullptr;
 };
+
+namespace sc {
+
+// Launch pass A (second == false) or B of the two-stage form with the level's
+// pass kernel (one-role or warp-specialised); an armed wait test goes to this
+// launch of the warp-specialised kernel and is then disarmed.
+inline cudaError_t launch_pass(sc_level* L, bool second, dev::PairArgs a, cudaStream_t s) {
+  if (!L->pass_ws) return dev::launch_pair(L->arith, second, a, L->dev->grid_pair, s);
+  a.stall = L->wait_test;
+  L->wait_test = 0;
+  return dev::launch_pair_ws(L->arith, second, a, L->dev->grid_pair_ws, s);
+}
+
+}  // namespace sc

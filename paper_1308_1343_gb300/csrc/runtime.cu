@@ -99,9 +99,11 @@ int upload_items(sc_level* L) {
   }
   // register staging: also the grid of the Laplacian kernel
   D->grid_stage = D->grid_stage_s[0];
-  int occ2 = 0;
+  int occ2 = 0, occ3 = 0;
   SC_CUDA(dev::pair_occupancy(L->arith, &occ2));
   D->grid_pair = D->sms * std::max(1, occ2);
+  SC_CUDA(dev::pair_ws_occupancy(L->arith, &occ3));
+  D->grid_pair_ws = D->sms * std::max(1, occ3);
   std::vector<DItem> items;
   build_items(L, items, D->box_items);
   // heuristic first choice (the paper's initial parameters, Sec. 3.2): while
@@ -695,14 +697,14 @@ static cudaError_t enq_pair(const Enq& q, dev::PairArgs a, bool second) {
     a.nitems = D->nitems;
     (*q.count)++;
     TimedLaunch t(q, kind);
-    return dev::launch_pair(q.L->arith, second, a, D->grid_pair, q.s);
+    return launch_pass(q.L, second, a, q.s);
   }
   for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
     a.items = D->items + D->box_items[b];
     a.nitems = D->box_items[b + 1] - D->box_items[b];
     (*q.count)++;
     TimedLaunch t(q, kind);
-    cudaError_t e = dev::launch_pair(q.L->arith, second, a, D->grid_pair, q.s);
+    cudaError_t e = launch_pass(q.L, second, a, q.s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -834,7 +836,8 @@ static int run_steps(sc_level* L, double* u, double* pi, const double* c2, int n
     return SC_OK;
   }
   auto key = std::make_tuple((const void*)u, (const void*)pi, (const void*)c2,
-                             L->arith + 2 * L->fuse + 4 * L->staging, L->version);
+                             L->arith + 2 * L->fuse + 4 * L->staging + 8 * L->pass_ws,
+                             L->version);
   auto it = D->graphs.find(key);
   if (it == D->graphs.end()) {
     if (D->graphs.size() >= 16) {  // bounded cache: start it afresh
@@ -989,6 +992,7 @@ int sc_level_sync(sc_level* L, void* stream) {
     if (e & dev::kErrNonFinite) m += " non-finite value in the fixed-point Laplacian;";
     if (e & dev::kErrScale) m += " input above its domain's exponent bound;";
     if (e & dev::kErrBounds) m += " index outside its box (checked build);";
+    if (e & dev::kErrTimeout) m += " a bounded wait inside a kernel gave up;";
     return set_error(SC_EDEVICE, m);
   }
   return SC_OK;
@@ -1320,6 +1324,29 @@ int sc_level_grad(sc_level* L, const double* u0, const double* pi0, const double
                                  stream);
   if (rc) return rc;
   return sc_level_backward_tape(L, c2, gu_T, gpi_T, g_u0, g_pi0, g_c2, stream);
+}
+
+int sc_level_set_pass_kernel(sc_level* L, int32_t kind) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (kind != SC_PASS_ONE_ROLE && kind != SC_PASS_WARP_SPECIALISED)
+    return set_error(SC_EINVAL, "kind must be SC_PASS_ONE_ROLE or SC_PASS_WARP_SPECIALISED");
+  L->pass_ws = kind;  // the step graphs are keyed by it
+  L->pass_fixed = true;
+  return SC_OK;
+}
+
+int sc_level_get_pass_kernel(const sc_level* L, int32_t* kind) {
+  if (!L || !kind) return set_error(SC_EINVAL, "NULL argument");
+  *kind = L->pass_ws;
+  return SC_OK;
+}
+
+int sc_level_arm_wait_test(sc_level* L) {
+  if (!L) return set_error(SC_EINVAL, "NULL level");
+  if (!L->pass_ws || L->fuse != 2)
+    return set_error(SC_EINVAL, "the wait test needs the warp-specialised two-stage passes");
+  L->wait_test = 1;
+  return SC_OK;
 }
 
 int sc_level_kernel_time(sc_level* L, int32_t kind, double* ms, int64_t* launches) {

@@ -252,6 +252,21 @@ class Level:
         B.check(B.lib().sc_level_get_fusion(self._h, ctypes.byref(n)))
         return n.value
 
+    def set_pass_kernel(self, kind: int):
+        """Kernels of the two-stage passes: binding.SC_PASS_ONE_ROLE or
+        binding.SC_PASS_WARP_SPECIALISED."""
+        B.check(B.lib().sc_level_set_pass_kernel(self._h, int(kind)))
+
+    def get_pass_kernel(self) -> int:
+        n = ctypes.c_int32()
+        B.check(B.lib().sc_level_get_pass_kernel(self._h, ctypes.byref(n)))
+        return n.value
+
+    def arm_wait_test(self):
+        """Failure-detection tests: the next warp-specialised pass launch
+        withholds its ring slots so that its bounded wait runs out."""
+        B.check(B.lib().sc_level_arm_wait_test(self._h))
+
     def set_staging(self, staging: int):
         """Staging of the one-stage kernel's raw inputs: 0 registers, 1 shared
         memory by cp.async (binding.SC_STAGING_*)."""

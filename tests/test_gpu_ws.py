@@ -1,0 +1,151 @@
+"""The warp-specialised pass kernels (sc_level_set_pass_kernel,
+SC_PASS_WARP_SPECIALISED) against the one-role pass kernels, through the C
+ABI: bit-identical states and gradients on every layout the one-role
+kernels are tested on (ragged, thin and odd boxes, an uneven level, an
+ensemble with per-domain step sizes, self-periodic boxes, every tile width
+and z-run, every launch mode, both arithmetic forms, the taped forward and
+the adjoint's recomputation), the oracle's values within the bar, and the
+bounded wait: a wait test makes the producers' wait for a free ring slot
+run out, the kernel returns, sc_level_sync reports SC_EDEVICE, and the
+level works again afterwards."""
+import numpy as np
+import pytest
+
+from paper_1308_1343_gb300 import workloads as W
+
+from gpu_helpers import make_level, rel_err, run_gpu, upload
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1308_1343_gb300 import build
+    build.build()
+
+
+def _both(inst_list, nsteps, arith, mode, tiles=None):
+    out = []
+    for kind in (0, 1):
+        lev = make_level(inst_list)
+        lev.set_fusion(2)
+        lev.set_pass_kernel(kind)
+        if tiles:
+            for cls, (tx, tz) in tiles.items():
+                lev.set_tuning(cls, tx, tz)
+        _, u, pi = run_gpu(inst_list, nsteps, arith, mode, lev=lev)
+        assert lev.get_pass_kernel() == kind
+        out.append((u, pi))
+        lev.close()
+    return out
+
+
+def _same(a, b):
+    return all(np.array_equal(x, y) for x, y in zip(a[0] + a[1], b[0] + b[1]))
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_ragged_box_every_mode(orc, arith, mode):
+    dom = W.Domain((40, 36, 28), 1.0 / 36)
+    inst = W.bumpy_instance(dom, 2)
+    one, ws = _both([inst], 6, arith, mode)
+    assert _same(one, ws)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, dom.h, inst.dt, 6)
+    assert rel_err(ws[0][0], ou) <= TOL and rel_err(ws[1][0], op) <= TOL
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_uneven_level_and_thin_boxes(orc, arith):
+    inst = W.uneven_level(n=(128, 128, 64), h=1.0 / 64, levels=6, seed=3, box_seed=30)
+    one, ws = _both([inst], 4, arith, 0)
+    assert _same(one, ws)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 4)
+    assert rel_err(ws[0][0], ou) <= TOL and rel_err(ws[1][0], op) <= TOL
+    n = (13, 11, 9)
+    thin = W.bumpy_instance(W.Domain(n, 1.0 / 11), 7)
+    thin.boxes = [((0, 0, 0), (2, 11, 9)), ((2, 0, 0), (5, 11, 9)), ((5, 0, 0), (13, 4, 9)),
+                  ((5, 4, 0), (13, 11, 2)), ((5, 4, 2), (13, 11, 9))]
+    one, ws = _both([thin], 4, arith, 0)
+    assert _same(one, ws)
+
+
+def test_ensemble_per_domain_dt_and_self_periodic_boxes():
+    insts = [W.bumpy_instance(W.Domain((n, n, n), 1.0 / n), 5000 + i)
+             for i, n in enumerate((24, 32, 40, 24, 56, 48))]
+    insts.append(W.bumpy_instance(W.Domain((3, 2, 5), 0.2), 9))   # odd x: gathered
+    insts.append(W.bumpy_instance(W.Domain((2, 2, 2), 0.5), 10))  # extent 2
+    one, ws = _both(insts, 5, 1, 0)
+    assert _same(one, ws)
+
+
+@pytest.mark.parametrize("tx,tz", [(16, 5), (32, 37), (64, 100), (64, 3), (16, 74)])
+def test_every_tile_and_z_run(tx, tz):
+    dom = W.Domain((44, 38, 75), 1.0 / 40)
+    inst = W.bumpy_instance(dom, 12)
+    one, ws = _both([inst], 3, 1, 0, tiles={0: (tx, tz)})
+    assert _same(one, ws)
+
+
+def test_256_box_bit_identical():
+    inst = W.single_box(256, seed=2)
+    one, ws = _both([inst], 3, 1, 0)
+    assert _same(one, ws)
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_taped_gradient_bit_identical(orc, arith):
+    import torch
+    inst = W.gradient_problem(20, 4)
+    res = []
+    for kind in (0, 1):
+        lev = make_level([inst])
+        lev.set_arith(arith)
+        lev.set_fusion(2)
+        lev.set_pass_kernel(kind)
+        t = lambda a, fill=0.0: upload(lev, [a], fill)
+        su = W.random_direction(inst.dom.shape, 43)
+        g = [torch.empty(lev.field_size, dtype=torch.float64, device="cuda") for _ in range(3)]
+        uT = torch.empty_like(g[0])
+        lev.grad(t(inst.u), t(inst.pi), t(inst.c2, 1.0), inst.dt, 11, 4, t(su), None, *g,
+                 u_T=uT)
+        lev.sync()
+        res.append([lev.gather(x)[0] for x in g + [uT]])
+        lev.close()
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+    ou, op, oc = orc.grad_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 11, 4, su,
+                                   np.zeros_like(su))
+    assert rel_err(res[1][0], ou) <= 1e-10 and rel_err(res[1][2], oc) <= 1e-10
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """A wait test withholds the consumers' release of the ring slots: the
+    producers' wait gives up after its limit, the kernel ends, sc_level_sync
+    reports SC_EDEVICE; the next steps run normally and match a fresh run."""
+    import torch
+    from paper_1308_1343_gb300 import binding as B
+    inst = W.bumpy_instance(W.Domain((48, 40, 36), 1.0 / 40), 3)
+    lev = make_level([inst])
+    lev.set_fusion(2)
+    lev.set_pass_kernel(1)
+    u, pi = upload(lev, [inst.u]), upload(lev, [inst.pi])
+    c2 = upload(lev, [inst.c2], fill=1.0)
+    lev.arm_wait_test()
+    lev.rk4_step(u, pi, c2, inst.dt, 1, B.SC_MODE_BATCHED)
+    with pytest.raises(B.ScError) as e:
+        lev.sync()
+    assert e.value.code == B.SC_EDEVICE and "bounded wait" in str(e.value)
+    # the context and the level are usable: a normal run from fresh inputs
+    u, pi = upload(lev, [inst.u]), upload(lev, [inst.pi])
+    lev.rk4_step(u, pi, c2, inst.dt, 3, B.SC_MODE_GRAPH)
+    lev.sync()
+    torch.cuda.synchronize()
+    _, u1, p1 = run_gpu([inst], 3, 1, 0, fuse=2)
+    assert np.array_equal(lev.gather(u)[0], u1[0]) and np.array_equal(lev.gather(pi)[0], p1[0])
+    lev.close()
