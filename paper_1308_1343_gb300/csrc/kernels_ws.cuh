@@ -133,7 +133,11 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
   const int TY = kWsProducers / txh;
   const int TX = 2 * txh;
   const int W = TX + 4;
-  const int bufElems = W * (TY + 4);
+  // buffers of (field, plane parity) at a fixed stride, whatever the item's
+  // tile shape: a fast producer starting the next item writes the other
+  // parity than the one slower producers may still be reading (there is no
+  // CTA-wide barrier between items)
+  constexpr int bufElems = TileSmem<kWsProducers>::kMaxElems;
   const int tid = threadIdx.x;
   const int lx = tid % txh, ly = tid / txh;
   const int gx = it.x0 + 2 * lx, gy = it.y0 + ly;
