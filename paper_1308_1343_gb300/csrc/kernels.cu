@@ -454,6 +454,10 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
 // The same passes with the warp-specialised traversal (kernels_ws.cuh):
 // producer warps form the sums, consumer warps run PairEpi on them.  Results
 // are bit-identical to pair_kernel.
+#ifndef SC_WS_PREGS
+#define SC_WS_PREGS "96"
+#define SC_WS_CREGS "48"
+#endif
 template <class A, bool SECOND, bool RECORD>
 __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
   __shared__ WsSmem<A> sm;
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
   // threads per SM); producers take 96 and consumers give back to 48:
   // 256 * 96 + 128 * 48 == 384 * 80, the launch allocation
   if (threadIdx.x < kWsProducers) {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 96;\n" ::: "memory");
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 " SC_WS_PREGS ";\n" ::: "memory");
     const double* const F[2] = {a.s0, a.s1};
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
       ok = ws_produce(it, bx, F, ar, sm, err, g);
     }
   } else {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 48;\n" ::: "memory");
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 " SC_WS_CREGS ";\n" ::: "memory");
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
       const DBox bx = a.boxes[it.box];

@@ -38,8 +38,12 @@ namespace sc {
 namespace dev {
 
 constexpr int kWsProducers = 256;  // 8 warps
-constexpr int kWsConsumers = 128;  // 4 warps: one per SM sub-partition
+#ifndef SC_WS_CONSUMERS
+#define SC_WS_CONSUMERS 128
+#endif
+constexpr int kWsConsumers = SC_WS_CONSUMERS;  // 4 warps: one per SM sub-partition
 constexpr int kWsThreads = kWsProducers + kWsConsumers;
+constexpr int kWsPairs = kWsProducers / kWsConsumers;  // point pairs per consumer thread
 constexpr int kWsRing = 2;  // sum slots: producers run at most 2 planes ahead
 constexpr unsigned long long kWsWaitNs = 1000000000ull;
 
@@ -240,7 +244,10 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
     // every producer has written plane k's tile
     mbar_arrive(&sm.tbar);
     if (!mbar_wait(&sm.tbar, g & 1u, &sm.abort)) return false;
-    T rA[2], rB[2];
+    // the slot is free once the consumers released it; each field's sums go
+    // to it as soon as they are formed
+    const unsigned slot = g % kWsRing;
+    if (!mbar_wait(&sm.empty[slot], ((g / kWsRing) & 1u) ^ 1u, &sm.abort)) return false;
     if (actA) {
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
@@ -251,22 +258,12 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
         const T2 ym2 = *reinterpret_cast<const T2*>(row - 2 * W);
         const T2 yp1 = *reinterpret_cast<const T2*>(row + W);
         const T2 yp2 = *reinterpret_cast<const T2*>(row + 2 * W);
-        rA[f] = A::lap(c0[f].x, xm.y, c0[f].y, ym1.x, yp1.x, m1[f].x, p1[f].x, xm.x, xp.x,
-                       ym2.x, yp2.x, m2[f].x, p2[f].x);
-        rB[f] = A::lap(c0[f].y, c0[f].x, xp.x, ym1.y, yp1.y, m1[f].y, p1[f].y, xm.y, xp.y,
-                       ym2.y, yp2.y, m2[f].y, p2[f].y);
-      }
-    }
-    // hand the sums over: the slot is free once the consumers released it
-    const unsigned slot = g % kWsRing;
-    if (!mbar_wait(&sm.empty[slot], ((g / kWsRing) & 1u) ^ 1u, &sm.abort)) return false;
-    if (actA) {
-#pragma unroll
-      for (int f = 0; f < 2; ++f) {
-        T2 s;
-        s.x = rA[f];
-        s.y = rB[f];
-        sm.ring[slot][f][tid] = s;
+        T2 r;
+        r.x = A::lap(c0[f].x, xm.y, c0[f].y, ym1.x, yp1.x, m1[f].x, p1[f].x, xm.x, xp.x,
+                     ym2.x, yp2.x, m2[f].x, p2[f].x);
+        r.y = A::lap(c0[f].y, c0[f].x, xp.x, ym1.y, yp1.y, m1[f].y, p1[f].y, xm.y, xp.y,
+                     ym2.y, yp2.y, m2[f].y, p2[f].y);
+        sm.ring[slot][f][tid] = r;
       }
     }
     mbar_arrive(&sm.full[slot]);
@@ -291,8 +288,8 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
   return ok;
 }
 
-// Consumer role for one work item (threads 256..383): pairs ctid and
-// ctid + 128 of the tile.  For every plane it calls
+// Consumer role for one work item (threads 256..): pairs ctid + j *
+// kWsConsumers (j < kWsPairs) of the tile.  For every plane it calls
 //   epi.point(idx, pw, rA, rB, actB, x, y, k)
 // exactly as run_items does.  stall != 0 (failure-detection tests only):
 // the consumers never release a slot, so the producers' wait for a free slot
@@ -325,10 +322,10 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, WsSm
   auto ck = [](int i) { return i; };
   auto ok_pt = [](int, int, int, int, bool) { return true; };
 #endif
-  int t[2], gxs[2], gys[2], op[2], oi[2];
-  bool actA[2], actB[2];
+  int t[kWsPairs], gxs[kWsPairs], gys[kWsPairs], op[kWsPairs], oi[kWsPairs];
+  bool actA[kWsPairs], actB[kWsPairs];
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < kWsPairs; ++j) {
     t[j] = ctid + kWsConsumers * j;
     const int lx = t[j] % txh, ly = t[j] / txh;
     gxs[j] = it.x0 + 2 * lx;
@@ -341,7 +338,7 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, WsSm
   // the pointwise fields of the thread's pairs on the next plane, by cp.async
   auto stage_pw = [&](int buf) {
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < kWsPairs; ++j) {
       if (actA[j]) {
 #pragma unroll
         for (int f = 0; f < Epi::NF; ++f) cp_async16(&sm.pw[buf][f][t[j]], epi.f[f] + ck(op[j]));
@@ -363,7 +360,7 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, WsSm
     const unsigned slot = g % kWsRing;
     if (!(ok = mbar_wait(&sm.full[slot], (g / kWsRing) & 1u, &sm.abort))) break;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < kWsPairs; ++j) {
       if (actA[j] && ok_pt(oi[j], gxs[j], gys[j], k, actB[j])) {
         T rA[2], rB[2];
 #pragma unroll
