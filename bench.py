@@ -174,7 +174,7 @@ class Clocks:
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "descriptors.hpp", "launch.hpp"):
+    for f in ("kernels.cu", "kernels.cuh", "kernels_ws.cuh", "descriptors.hpp", "launch.hpp"):
         with open(os.path.join(ROOT, "paper_1308_1343_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -185,13 +185,15 @@ def _stencil_roofline(lev, B, npts):
     from the per-launch CUDA events of the last SC_MODE_TIMED call:
     (achieved GB/s, mean launch ms, mean bytes per launch, launches, name)."""
     if lev.get_fusion() == 2:
+        name = "pair_ws_kernel" if lev.get_pass_kernel() == B.SC_PASS_WARP_SPECIALISED \
+            else "pair_kernel"
         ta, na = lev.kernel_time(B.SC_KERNEL_PAIR_A)
         tb, nb = lev.kernel_time(B.SC_KERNEL_PAIR_B)
         if not (na and nb):
-            return None, None, None, 0, "pair_kernel"
+            return None, None, None, 0, name
         nbytes = (BYTES_PER_POINT_PASS["A"] * na + BYTES_PER_POINT_PASS["B"] * nb) * npts
         return (nbytes / ((ta + tb) * 1e-3) / 1e9, (ta + tb) / (na + nb), nbytes / (na + nb),
-                na + nb, "pair_kernel (passes A and B)")
+                na + nb, name + " (passes A and B)")
     sm, sl, _, _ = lev.kernel_times()
     if not sl:
         return None, None, None, 0, "fwd_stage_kernel"
@@ -637,6 +639,9 @@ def run_ours(a, ws, rank, local):
                        "arith": a.arith, "mode": "batched persistent launch, CUDA graph per "
                                                   "RK4 step",
                        "stages_per_pass": form,
+                       "pass_kernel": ("warp-specialised" if lev.get_pass_kernel() ==
+                                       B.SC_PASS_WARP_SPECIALISED else "one-role")
+                       if form == 2 else None,
                        "tiles": [list(lev.get_tuning(c)) for c in range(lev.size_classes()[0])],
                        "l2": "inputs larger than L2 (fields 7 x %d MB)" % (fbytes >> 20),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -653,11 +658,12 @@ def run_ours(a, ws, rank, local):
                          "hbm_fraction_of_nominal_7900": achieved / 7900.0,
                          "kernel_hash": khash,
                          "note": ("two RK4 stages per pass halve the DRAM bytes of a step; "
-                                  "these kernels are then limited by the SM (latency of "
-                                  "shared-memory loads, FP64 results and integer chains at "
-                                  "15 warps per SM), not by HBM; classic_equivalent_gbs is "
-                                  "the rate times the 304 B per point and step of an unfused "
-                                  "stage form")
+                                  "in the warp-specialised kernels producer warps form the "
+                                  "fixed-point sums while consumer warps run the FP64 "
+                                  "epilogue, so the integer and FP64 pipes work at the same "
+                                  "time; what remains is memory latency and issue; "
+                                  "classic_equivalent_gbs is the rate times the 304 B per "
+                                  "point and step of an unfused stage form")
                          if form == 2 else "one stage per pass, HBM-bound"},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -214,8 +214,9 @@ int sc_level_get_staging(const sc_level* level, int32_t* staging);
  *    threads, two CTAs per SM; the roles take 96 and 48 registers).  Every
  *    wait inside it is bounded (1 s); a wait that gives up ends the kernel
  *    and sets the device error word (SC_EDEVICE at sc_level_sync).
- * Results are bit-identical.  Setting it fixes it; until then
- * sc_level_autotune times both and keeps the faster.  Errors: SC_EINVAL. */
+ * Results are bit-identical.  The default is SC_PASS_WARP_SPECIALISED.
+ * Setting it fixes it; until then sc_level_autotune tunes the tiles of both
+ * and keeps the faster kernel.  Errors: SC_EINVAL. */
 #define SC_PASS_ONE_ROLE 0
 #define SC_PASS_WARP_SPECIALISED 1
 int sc_level_set_pass_kernel(sc_level* level, int32_t kind);

@@ -314,6 +314,31 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
   return L->fuse == 2 ? t : 4.0 * t;
 }
 
+// The two-stage form: unless the caller fixed the pass kernels, tune the
+// tiles of the warp-specialised and of the one-role kernels and keep the
+// faster kernel with its tiles (another choice between sets of loop kernels).
+double tune_two_stage(sc_level* L, Timer& T,
+                      std::map<std::string, std::pair<Cand, double>>& cache,
+                      std::mt19937_64& rng, double per_class, double abort_factor) {
+  if (L->pass_fixed) return tune_form(L, T, cache, rng, per_class, abort_factor);
+  std::vector<sc_tile> start;
+  for (const auto& c : L->classes) start.push_back(c.tile);
+  L->pass_ws = 1;
+  const double tw = tune_form(L, T, cache, rng, per_class, abort_factor);
+  std::vector<sc_tile> tiles_ws;
+  for (const auto& c : L->classes) tiles_ws.push_back(c.tile);
+  for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = start[i];
+  L->pass_ws = 0;
+  const double to = tune_form(L, T, cache, rng, per_class, abort_factor);
+  if (tw < 0 || to < 0) return -1.0;
+  if (tw <= to) {
+    L->pass_ws = 1;
+    for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = tiles_ws[i];
+    return tw;
+  }
+  return to;
+}
+
 }  // namespace
 }  // namespace sc
 
@@ -337,11 +362,16 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
   // Unless the caller fixed the form, both are tuned and the faster kept:
   // choosing between sets of loop kernels (one or two RK4 stages per pass)
   // with the same optimiser, as the paper proposes for fission and fusion.
-  const int nforms = L->fuse_fixed ? 1 : 2;
+  // tunings: the one-stage form, and the two-stage form with each of its
+  // pass kernels
+  const int nforms = (L->fuse_fixed && L->fuse == 1 ? 1 : 0) +
+                     (L->fuse_fixed && L->fuse == 2 ? (L->pass_fixed ? 1 : 2) : 0) +
+                     (L->fuse_fixed ? 0 : (L->pass_fixed ? 2 : 3));
   const double per_class = budget_ms / (nforms * std::max<size_t>(1, L->classes.size()));
   bool ok = true;
   if (L->fuse_fixed) {
-    ok = tune_form(L, T, cache, rng, per_class, abort_factor) >= 0;
+    ok = (L->fuse == 2 ? tune_two_stage(L, T, cache, rng, per_class, abort_factor)
+                       : tune_form(L, T, cache, rng, per_class, abort_factor)) >= 0;
   } else {
     std::vector<sc_tile> start;
     for (const auto& c : L->classes) start.push_back(c.tile);
@@ -351,7 +381,7 @@ extern "C" int sc_level_autotune(sc_level* L, int32_t seed, double budget_ms,
     for (const auto& c : L->classes) tiles1.push_back(c.tile);
     for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = start[i];
     L->fuse = 2;
-    const double t2 = tune_form(L, T, cache, rng, per_class, abort_factor);
+    const double t2 = tune_two_stage(L, T, cache, rng, per_class, abort_factor);
     ok = t1 >= 0 && t2 >= 0;
     if (ok && t1 < t2) {
       L->fuse = 1;

@@ -71,15 +71,17 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
       : "memory");
 }
 
-// true once the phase of parity `parity` has completed (acquire semantics)
+// true once the phase of parity `parity` has completed (acquire semantics);
+// the thread may sleep up to kWsSuspendNs waiting for it instead of spinning
+constexpr unsigned kWsSuspendNs = 1000000u;
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kWsSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -90,9 +92,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
                                           volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
-  for (unsigned i = 1;; ++i) {
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 31u) == 0u && (*abort != 0 || global_ns() - t0 > kWsWaitNs)) return false;
+    if (*abort != 0 || global_ns() - t0 > kWsWaitNs) return false;
   }
 }
 

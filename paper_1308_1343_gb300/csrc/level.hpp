@@ -147,7 +147,7 @@ struct sc_level {
                                // in shared memory by cp.async (1)
   bool staging_fixed = false;  // set by sc_level_set_staging; else the autotuner chooses
   int ctas_per_sm = 0;
-  int pass_ws = 0;          // two-stage passes: one-role (0) or warp-specialised (1) kernels
+  int pass_ws = 1;          // two-stage passes: one-role (0) or warp-specialised (1) kernels
   bool pass_fixed = false;  // set by sc_level_set_pass_kernel; else the autotuner chooses
   int wait_test = 0;        // failure-detection tests: the next warp-specialised pass
                             // launch withholds its ring slots (one shot)
