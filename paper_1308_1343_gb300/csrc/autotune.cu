@@ -331,6 +331,11 @@ double tune_two_stage(sc_level* L, Timer& T,
   L->pass_ws = 0;
   const double to = tune_form(L, T, cache, rng, per_class, abort_factor);
   if (tw < 0 || to < 0) return -1.0;
+  // the one-role tiles stay with the classes for the adjoint's pass kernels
+  for (auto& c : L->classes) {
+    c.tile_one = c.tile;
+    c.has_one = true;
+  }
   if (tw <= to) {
     L->pass_ws = 1;
     for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = tiles_ws[i];

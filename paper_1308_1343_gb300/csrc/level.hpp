@@ -52,6 +52,11 @@ struct SizeClass {
   std::array<int64_t, 3> ext;  // interior extent rounded up to a multiple of 8
   sc_tile tile;
   bool fixed = false;          // tile set by sc_level_set_tuning / autotune
+  // the tile the autotuner found for the one-role two-stage kernels while the
+  // level runs the warp-specialised ones: the adjoint's pass kernels (one-role
+  // kernels over two stencil fields) use it
+  sc_tile tile_one{};
+  bool has_one = false;
 };
 
 // Device-side state, created lazily on the first call that takes a stream.
@@ -65,6 +70,10 @@ struct DeviceState {
   dev::DItem* items = nullptr;
   int nitems = 0;
   std::vector<int> box_items;  // per-box item ranges [b], [b+1]
+  // items of the adjoint's pass kernels: tiles tuned for one-role kernels
+  // (SizeClass::tile_one), or NULL to use `items`
+  dev::DItem* items_one = nullptr;
+  int nitems_one = 0;
 
   // ghost exchange as rectangles + chunks (sorted by destination box)
   dev::DRect* grects = nullptr;

@@ -62,14 +62,16 @@ void add_chunks(int rect, int64_t n, std::vector<DChunk>& out, int chunk = dev::
 }
 
 // Work items: every box cut into (tile_x, tile_y, tile_z) items of its class,
-// box-major, then z, y, x.
-void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>& box_items) {
+// box-major, then z, y, x (one_role: the classes' tile_one instead).
+void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>& box_items,
+                 bool one_role = false) {
   items.clear();
   box_items.assign(L->boxes.size() + 1, 0);
   for (size_t b = 0; b < L->boxes.size(); ++b) {
     box_items[b] = (int)items.size();
     const sc_box& B = L->boxes[b];
-    const sc_tile& t = L->classes[L->box_class[b]].tile;
+    const SizeClass& C = L->classes[L->box_class[b]];
+    const sc_tile& t = one_role && C.has_one ? C.tile_one : C.tile;
     append_box_items(items, (int)b, (int)(B.hi[0] - B.lo[0]), (int)(B.hi[1] - B.lo[1]),
                      (int)(B.hi[2] - B.lo[2]), t.tile_x, t.tile_y, t.tile_z);
   }
@@ -130,6 +132,22 @@ int upload_items(sc_level* L) {
   int rc = upload(&D->items, items);
   if (rc) return rc;
   D->nitems = (int)items.size();
+  // the adjoint's pass kernels: their own list where the tuner found other
+  // tiles for one-role kernels
+  bool other = false;
+  for (const auto& c : L->classes)
+    if (c.has_one && (c.tile_one.tile_x != c.tile.tile_x || c.tile_one.tile_z != c.tile.tile_z))
+      other = true;
+  D->nitems_one = 0;
+  if (D->items_one) cudaFree(D->items_one);
+  D->items_one = nullptr;
+  if (other) {
+    std::vector<DItem> one;
+    std::vector<int> box_one;
+    build_items(L, one, box_one, true);
+    if ((rc = upload(&D->items_one, one))) return rc;
+    D->nitems_one = (int)one.size();
+  }
   return SC_OK;
 }
 
@@ -146,7 +164,7 @@ void release_device(sc_level* L) {
     cudaEventDestroy(pr.second);
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
-  void* ptrs[] = {D->boxes, D->items, D->grects, D->gchunks, D->gchunks_nw, D->irects, D->ichunks,
+  void* ptrs[] = {D->boxes, D->items, D->items_one, D->grects, D->gchunks, D->gchunks_nw, D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial, D->xsend, D->xsend_chunks, D->xrecv,
                   D->xrecv_chunks};
@@ -1245,8 +1263,8 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
       const int p = (int)(n_adj & 1), pn = 1 - p;
       // (Phat4, Phat3) = L^ (c2 b, c2 a), (X', Y') = c2 (Phat4, Phat3)
       dev::Adj2Args a{};
-      a.items = D->items;
-      a.nitems = D->nitems;
+      a.items = D->items_one ? D->items_one : D->items;
+      a.nitems = D->items_one ? D->nitems_one : D->nitems;
       a.ndom = nd;
       a.boxes = D->boxes;
       a.c2 = c2;
@@ -1392,6 +1410,7 @@ int sc_level_set_tuning(sc_level* L, int32_t cls, const sc_tile* t, int32_t ctas
   L->classes[cls].tile = *t;
   L->classes[cls].tile.reserved = 0;
   L->classes[cls].fixed = true;
+  L->classes[cls].has_one = false;  // an explicit tile serves every kernel
   if (ctas_per_sm > 0) L->ctas_per_sm = ctas_per_sm;
   if (L->dev) return upload_items(L);
   return SC_OK;
