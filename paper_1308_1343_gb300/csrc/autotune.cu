@@ -86,14 +86,16 @@ struct Timer {
 
   // Items of the whole level with the current tiles, except class `cls`
   // which gets (tx, tz): the candidate is timed in the launch it will run in
-  // (coordinate descent over the classes).  Returns the item count.
+  // (coordinate descent over the classes); cls == kAll gives every class the
+  // candidate.  Returns the item count.
+  static constexpr int kAll = -2;
   int stage(int cls, const Cand& c) {
     std::vector<dev::DItem> items;
     for (size_t b = 0; b < L->boxes.size(); ++b) {
       const sc_box& B = L->boxes[b];
       const int nx = (int)(B.hi[0] - B.lo[0]), ny = (int)(B.hi[1] - B.lo[1]),
                 nz = (int)(B.hi[2] - B.lo[2]);
-      const bool mine = L->box_class[b] == cls;
+      const bool mine = cls == kAll || L->box_class[b] == cls;
       const int tx = mine ? c.tx : L->classes[L->box_class[b]].tile.tile_x;
       const int tz = mine ? c.tz : L->classes[L->box_class[b]].tile.tile_z;
       append_box_items(items, (int)b, nx, ny, nz, tx, 2 * dev_threads() / tx, tz);
@@ -221,6 +223,60 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
                  std::mt19937_64& rng, double per_class, double abort_factor) {
   cudaStream_t s = T.s;
   std::uniform_real_distribution<double> U(0.0, 1.0);
+  // Many size classes (a level of uneven boxes): first one tile for every
+  // class not in the cache, hill climbing over the whole level with half of
+  // the budget, so that each class starts its own search from it.
+  size_t uncached = 0;
+  int64_t nzmax = 1;
+  for (const auto& C : L->classes) {
+    if (!cache.count(cache_key(L, C))) ++uncached;
+    nzmax = std::max(nzmax, C.ext[2]);
+  }
+  if (uncached >= 4) {
+    std::map<Cand, double> seen;
+    auto eval = [&](const Cand& c, double limit) {
+      auto it = seen.find(c);
+      if (it != seen.end()) return it->second;
+      const double t = T.time(Timer::kAll, c, limit);
+      seen[c] = t;
+      return t;
+    };
+    Cand best{L->classes[0].tile.tile_x, L->classes[0].tile.tile_z};
+    double tbest = eval(best, 1e30);
+    const double budget = 0.5 * per_class * (double)L->classes.size();
+    cudaEvent_t w0, w1;
+    cudaEventCreate(&w0);
+    cudaEventCreate(&w1);
+    cudaEventRecord(w0, s);
+    for (double spent = 0; spent < budget;) {
+      Cand nb = best;
+      double tn = tbest;
+      for (const Cand& c : neighbours(best, nzmax)) {
+        const double t = eval(c, abort_factor * tbest);
+        if (t < tn) {
+          tn = t;
+          nb = c;
+        }
+      }
+      if (nb == best) break;  // local optimum of the shared tile
+      best = nb;
+      tbest = tn;
+      cudaEventRecord(w1, s);
+      cudaEventSynchronize(w1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, w0, w1);
+      spent = ms;
+    }
+    cudaEventDestroy(w0);
+    cudaEventDestroy(w1);
+    for (auto& C : L->classes)
+      if (!cache.count(cache_key(L, C))) {
+        C.tile.tile_x = best.tx;
+        C.tile.tile_y = 2 * dev::stage_threads() / best.tx;
+        C.tile.tile_z = (int)std::min<int64_t>(best.tz, C.ext[2]);
+      }
+    per_class *= 0.5;
+  }
   for (size_t ci = 0; ci < L->classes.size(); ++ci) {
     SizeClass& C = L->classes[ci];
     const std::string key = cache_key(L, C);

@@ -44,13 +44,7 @@ constexpr int kWsProducers = 256;  // 8 warps
 constexpr int kWsConsumers = SC_WS_CONSUMERS;  // 4 warps: one per SM sub-partition
 constexpr int kWsThreads = kWsProducers + kWsConsumers;
 constexpr int kWsPairs = kWsProducers / kWsConsumers;  // point pairs per consumer thread
-#ifndef SC_WS_RING
-#define SC_WS_RING 2
-#endif
-constexpr int kWsRing = SC_WS_RING;  // sum slots: producers run at most this many planes ahead
-// halo pairs of a plane tile (4 txh + 2 * 256 / txh: 96 for 32 x 16 and 16 x 32 tiles,
-// 144 for 64 x 8), for both fields
-constexpr int kWsHaloEntries = 2 * 144;
+constexpr int kWsRing = 2;  // sum slots: producers run at most 2 planes ahead
 constexpr unsigned long long kWsWaitNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -109,7 +103,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 template <class A>
 struct WsSmem {
   typename A::T tile[2 * 2 * TileSmem<kWsProducers>::kMaxElems];  // [field][plane parity]
-  double2 hraw[2][kWsHaloEntries];    // [plane parity][halo entry (pair, field)]
+  double2 hraw[2][2][kWsProducers];   // [plane parity][field][producer]
   double2 craw[2][2][kWsProducers];
   typename A::T2 ring[kWsRing][2][kWsProducers];  // sums at (point A, point B)
   double2 pw[2][4][kWsProducers];     // [plane parity][field][pair]
@@ -175,28 +169,19 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
   const int colOff = colLoad ? off0 + wr(gx, bx.nx) + wr(gy, bx.ny) * py : off0;
   const int oy = out_of(gy, bx.ny);
   const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
-  // this thread's halo entries of the plane tile.  Where both fields' halo
-  // pairs fit in one per thread (2 (4 txh + 2 TY) <= 256: the 32 x 16 and
-  // 16 x 32 tiles), thread t takes pair t mod nhalo of field t / nhalo, so no
-  // warp converts more than one halo pair per plane and the producers reach
-  // their plane barrier together; otherwise (64 x 8) thread t takes pair t of
-  // both fields.
+  // this thread's halo pair of the plane tile, if any (at most one: the halo
+  // of a tile has 4 txh + 2 TY <= 256 pairs for every allowed shape)
   const int nhalo = 4 * txh + 2 * TY;
-  const bool hsplit = 2 * nhalo <= kWsProducers;
-  const int hfield = hsplit ? tid / nhalo : 0;
-  const int hp = hsplit ? tid - hfield * nhalo : tid;  // the thread's halo pair
-  const bool hasH = hsplit ? tid < 2 * nhalo : tid < nhalo;
-  auto mine = [&](int f) { return hasH && (!hsplit || f == hfield); };
-  auto hent = [&](int f) { return f * nhalo + hp; };  // staging entry of field f
+  const bool hasH = tid < nhalo;
   int hs = 0, hg = off0, hx0 = 2, hx1 = 2;
   if (hasH) {
     int hx, hy;
-    if (hp < 4 * txh) {
-      const int r = hp / txh;
-      hx = 2 * (hp - r * txh);
+    if (tid < 4 * txh) {
+      const int r = tid / txh;
+      hx = 2 * (tid - r * txh);
       hy = r < 2 ? r - 2 : TY + r - 2;
     } else {
-      const int j = hp - 4 * txh;
+      const int j = tid - 4 * txh;
       const int side = j / TY;
       hy = j - side * TY;
       hx = side ? TX : -2;
@@ -220,7 +205,7 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
   auto stage_raw = [&](int buf) {
 #pragma unroll
     for (int f = 0; f < 2; ++f)
-      if (mine(f)) cp_async16(&sm.hraw[buf][hent(f)], F[f] + ck(oh));
+      if (hasH) cp_async16(&sm.hraw[buf][f][tid], F[f] + ck(oh));
 #pragma unroll
     for (int f = 0; f < 2; ++f) cp_async16(&sm.craw[buf][f][tid], F[f] + ck(oc));
     oh += pz;
@@ -253,9 +238,9 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
     cp_async_wait_one();  // this thread's raw values of plane k have landed
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-      if (mine(f))
+      if (hasH)
         *reinterpret_cast<T2*>(sm.tile + (2 * f + tb) * bufElems + hs) =
-            arith[f].conv(sm.hraw[tb][hent(f)], hx0 + oz <= 1, hx1 + oz <= 1, err);
+            arith[f].conv(sm.hraw[tb][f][tid], hx0 + oz <= 1, hx1 + oz <= 1, err);
       p2[f] = conv_at(f, sm.craw[tb][f][tid], k + 2);
     }
     // every producer has written plane k's tile
