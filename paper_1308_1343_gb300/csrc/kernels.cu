@@ -454,21 +454,16 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs a) {
 // The same passes with the warp-specialised traversal (kernels_ws.cuh):
 // producer warps form the sums, consumer warps run PairEpi on them.  Results
 // are bit-identical to pair_kernel.
-#ifndef SC_WS_PREGS
-#define SC_WS_PREGS "96"
-#define SC_WS_CREGS "48"
-#endif
 template <class A, bool SECOND, bool RECORD>
 __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
   __shared__ WsSmem<A> sm;
   ws_init(sm);
   unsigned err = 0, g = 0;
   bool ok = true;
-  // registers: the CTA is launched with 80 per thread (two CTAs of 384
-  // threads per SM); producers take 96 and consumers give back to 48:
-  // 256 * 96 + 128 * 48 == 384 * 80, the launch allocation
+  // registers: producers take 96 and consumers give back to 48 of the 80
+  // per thread the CTA was launched with
   if (threadIdx.x < kWsProducers) {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 " SC_WS_PREGS ";\n" ::: "memory");
+    ws_producer_regs<96, 48>();
     const double* const F[2] = {a.s0, a.s1};
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
@@ -478,7 +473,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
       ok = ws_produce(it, bx, F, ar, sm, err, g);
     }
   } else {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 " SC_WS_CREGS ";\n" ::: "memory");
+    ws_consumer_regs<96, 48>();
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
       const DBox bx = a.boxes[it.box];
@@ -642,6 +637,147 @@ __global__ void __launch_bounds__(NT, 2) adj2_kernel(Adj2Args a) {
       if (A::kFixed)
         cta_max2_to(epi.e0, epi.e1, a.emax_out + bx.dom, a.emax_out + a.ndom + bx.dom, red);
     }
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+// The adjoint step in two warp-specialised passes, without the pointwise
+// combination kernel: each output below is formed by the same FMAs in the
+// same nesting as adj_combine_kernel forms it (the first pass rounds the inner
+// part, the second adds the outer terms), and Phat4..Phat1, c2 Phat4, c2 Phat3
+// are those of adj2_kernel, so the gradients are bit-identical to the
+// one-role path.  The combination's FP64 work runs in the consumer warps,
+// beside the producers' integer work.
+template <class A, bool SECOND>
+struct AdjWsEpi {
+  // first: c2, a, b, c2bar, Q1..Q4 (one buffer, each pair's next plane as
+  // soon as its values are read); second: ybar.u part, ybar.pi part, c2
+  static constexpr int NF = SECOND ? 3 : 8;
+  const double* f[NF];
+  double* yu;
+  double* yp;
+  double* cb;
+  double* zo0;
+  double* zo1;
+  A a0, a1;
+  AdjCoef k;
+  unsigned e0, e1;
+  __device__ __forceinline__ void one(typename A::T s0, typename A::T s1, const double* v,
+                                      double& z0, double& z1, double& ou, double& op,
+                                      double& oc) const {
+    const double Pa = a0.scaled(s0, 0), Pb = a1.scaled(s1, 0);
+    if (!SECOND) {
+      // Pa = Phat4, Pb = Phat3; v = c2, a, b, c2bar, Q1, Q2, Q3, Q4
+      const double cc = v[0], av = v[1], bv = v[2];
+      z0 = cc * Pa;
+      z1 = cc * Pb;
+      ou = fma(k.cu[1], Pb, fma(k.cu[0], Pa, av));
+      op = fma(k.cp[2], Pb, fma(k.cp[1], Pa, fma(k.cp[0], av, bv)));
+      oc = fma(Pb, v[4], fma(Pa, v[5], fma(av, v[6], fma(bv, v[7], v[3]))));
+    } else {
+      // Pa = Phat2, Pb = Phat1; v = ybar.u part, ybar.pi part, c2
+      ou = fma(k.cu[3], Pb, fma(k.cu[2], Pa, v[0]));
+      op = fma(k.cp[3], Pa, v[1]);
+      z0 = v[2] * op;
+      z1 = v[2] * ou;
+      oc = 0.0;
+    }
+  }
+  __device__ __forceinline__ void point(int i, const double2* pw,
+                                        const typename A::T (&rA)[2],
+                                        const typename A::T (&rB)[2], bool actB, int, int,
+                                        int) {
+    double va[NF], vb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      va[f] = pw[f].x;
+      vb[f] = pw[f].y;
+    }
+    double2 z0, z1, ou, op, oc;
+    one(rA[0], rA[1], va, z0.x, z1.x, ou.x, op.x, oc.x);
+    one(rB[0], rB[1], vb, z0.y, z1.y, ou.y, op.y, oc.y);
+    if (actB) {
+      st2(zo0 + i, z0);
+      st2(zo1 + i, z1);
+      st2(yu + i, ou);
+      st2(yp + i, op);
+      if (!SECOND) st2(cb + i, oc);
+    } else {
+      zo0[i] = z0.x;
+      zo1[i] = z1.x;
+      yu[i] = ou.x;
+      yp[i] = op.x;
+      if (!SECOND) cb[i] = oc.x;
+    }
+    if (A::kFixed) {
+      e0 = max(e0, biased_exp(z0.x));
+      e1 = max(e1, biased_exp(z1.x));
+      if (actB) {
+        e0 = max(e0, biased_exp(z0.y));
+        e1 = max(e1, biased_exp(z1.y));
+      }
+    }
+  }
+};
+
+template <class A, bool SECOND>
+__global__ void __launch_bounds__(kWsThreads, 2) adj_ws_kernel(AdjWsArgs a) {
+  __shared__ WsSmem<A, SECOND ? 3 : 8, SECOND ? 2 : 1> sm;
+  ws_init(sm);
+  unsigned err = 0, g = 0;
+  bool ok = true;
+  // the first pass's consumers hold eight pointwise fields: 88 / 64 there
+  constexpr int kP = SECOND ? 96 : 88, kC = SECOND ? 48 : 64;
+  if (threadIdx.x < kWsProducers) {
+    ws_producer_regs<kP, kC>();
+    const double* const F[2] = {a.z0_in, a.z1_in};
+    for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
+      const DItem it = a.items[i];
+      const DBox bx = a.boxes[it.box];
+      const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
+                       make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
+      ok = ws_produce(it, bx, F, ar, sm, err, g);
+    }
+  } else {
+    ws_consumer_regs<kP, kC>();
+    for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
+      const DItem it = a.items[i];
+      const DBox bx = a.boxes[it.box];
+      unsigned e2 = 0;  // a bad bound is reported by the producers
+      AdjWsEpi<A, SECOND> epi;
+      if (SECOND) {
+        epi.f[0] = a.yu;
+        epi.f[1] = a.yp;
+        epi.f[2] = a.c2;
+      } else {
+        const double* fs[8] = {a.c2, a.yu, a.yp, a.c2bar, a.q1, a.q2, a.q3, a.q4};
+#pragma unroll
+        for (int f = 0; f < AdjWsEpi<A, SECOND>::NF; ++f) epi.f[f] = fs[f];
+      }
+      epi.yu = a.yu;
+      epi.yp = a.yp;
+      epi.cb = a.c2bar;
+      epi.zo0 = a.z0_out;
+      epi.zo1 = a.z1_out;
+      epi.a0 = make_arith<A>(a.emax_in, bx.dom, e2);
+      epi.a1 = make_arith<A>(a.emax_in + a.ndom, bx.dom, e2);
+      epi.k = a.coef[bx.dom];
+      epi.e0 = epi.e1 = 0u;
+      ok = ws_consume(it, bx, sm, err, g, epi, a.stall);
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok && A::kFixed) {
+        const unsigned e0 = __reduce_max_sync(0xffffffffu, epi.e0);
+        const unsigned e1 = __reduce_max_sync(0xffffffffu, epi.e1);
+        if ((threadIdx.x & 31) == 0) {
+          if (e0) atomicMax(a.emax_out + bx.dom, e0);
+          if (e1) atomicMax(a.emax_out + a.ndom + bx.dom, e1);
+        }
+      }
+    }
+  }
+  if (!ok) {
+    reinterpret_cast<volatile int&>(sm.abort) = 1;
+    err |= kErrTimeout;
   }
   if (err) atomicOr(a.err, err);
 }
@@ -1011,6 +1147,10 @@ static void set_carveouts() {
   prefer_shared(pair_ws_kernel<FixedI, true, true>);
   prefer_shared(pair_ws_kernel<Fp64, false, true>);
   prefer_shared(pair_ws_kernel<Fp64, true, true>);
+  prefer_shared(adj_ws_kernel<FixedI, false>);
+  prefer_shared(adj_ws_kernel<FixedI, true>);
+  prefer_shared(adj_ws_kernel<Fp64, false>);
+  prefer_shared(adj_ws_kernel<Fp64, true>);
   prefer_shared(adj2_kernel<FixedI, false>);
   prefer_shared(adj2_kernel<FixedI, true>);
   prefer_shared(adj2_kernel<Fp64, false>);
@@ -1108,8 +1248,31 @@ cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cud
   return cudaGetLastError();
 }
 
+// The warp-specialised kernels split the registers they were launched with
+// between the roles (setmaxnreg); a launch with another count would leave the
+// producers' increase waiting.  Checked once per kernel before its first launch.
+template <class K>
+static bool ws_regs_ok(K kernel) {
+  cudaFuncAttributes at{};
+  return cudaFuncGetAttributes(&at, kernel) == cudaSuccess && at.numRegs == 80 &&
+         at.maxThreadsPerBlock >= kWsThreads;
+}
+static bool ws_kernels_ok() {
+  static const bool ok =
+      ws_regs_ok(pair_ws_kernel<FixedI, false, false>) &&
+      ws_regs_ok(pair_ws_kernel<FixedI, true, false>) &&
+      ws_regs_ok(pair_ws_kernel<FixedI, false, true>) &&
+      ws_regs_ok(pair_ws_kernel<FixedI, true, true>) &&
+      ws_regs_ok(pair_ws_kernel<Fp64, false, false>) && ws_regs_ok(pair_ws_kernel<Fp64, true, false>) &&
+      ws_regs_ok(pair_ws_kernel<Fp64, false, true>) && ws_regs_ok(pair_ws_kernel<Fp64, true, true>) &&
+      ws_regs_ok(adj_ws_kernel<FixedI, false>) && ws_regs_ok(adj_ws_kernel<FixedI, true>) &&
+      ws_regs_ok(adj_ws_kernel<Fp64, false>) && ws_regs_ok(adj_ws_kernel<Fp64, true>);
+  return ok;
+}
+
 cudaError_t launch_pair_ws(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s) {
   if (a.nitems <= 0) return cudaSuccess;
+  if (!ws_kernels_ok()) return cudaErrorInvalidConfiguration;
   set_carveouts();
   grid = min(grid, a.nitems);
   const bool rec = a.rec0 != nullptr;
@@ -1127,6 +1290,25 @@ cudaError_t launch_pair_ws(int arith, bool second, const PairArgs& a, int grid, 
     else
       rec ? pair_ws_kernel<Fp64, false, true><<<grid, kWsThreads, 0, s>>>(a)
           : pair_ws_kernel<Fp64, false, false><<<grid, kWsThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_ws(bool second, int arith, const AdjWsArgs& a, int grid, cudaStream_t s) {
+  if (a.nitems <= 0) return cudaSuccess;
+  if (!ws_kernels_ok()) return cudaErrorInvalidConfiguration;
+  set_carveouts();
+  grid = min(grid, a.nitems);
+  if (arith == 1) {
+    if (second)
+      adj_ws_kernel<FixedI, true><<<grid, kWsThreads, 0, s>>>(a);
+    else
+      adj_ws_kernel<FixedI, false><<<grid, kWsThreads, 0, s>>>(a);
+  } else {
+    if (second)
+      adj_ws_kernel<Fp64, true><<<grid, kWsThreads, 0, s>>>(a);
+    else
+      adj_ws_kernel<Fp64, false><<<grid, kWsThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -83,6 +83,11 @@ __device__ __forceinline__ void cp_async_wait_one() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+// wait until at most N committed groups of this thread are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // 64-bit logical right shift whose amount saturates: >= 64 gives 0.
 __device__ __forceinline__ unsigned long long shr_sat(unsigned long long v, unsigned r) {

@@ -98,23 +98,42 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
 }
 
-// Shared memory of one warp-specialised CTA (two stencil fields, four
-// pointwise fields): about 107 KB, two CTAs per SM.
-template <class A>
+// Shared memory of one warp-specialised CTA with two stencil fields and NF
+// pointwise fields staged NB planes deep (NB = 2: one plane ahead; NB = 1:
+// each pair's next plane as soon as its values are read): 107 KB for the
+// forward passes (NF = 4, NB = 2), two CTAs per SM.
+template <class A, int NF = 4, int NB = 2>
 struct WsSmem {
+  using Arith = A;
+  static constexpr int kNF = NF;
+  static constexpr int kNB = NB;
   typename A::T tile[2 * 2 * TileSmem<kWsProducers>::kMaxElems];  // [field][plane parity]
   double2 hraw[2][2][kWsProducers];   // [plane parity][field][producer]
   double2 craw[2][2][kWsProducers];
   typename A::T2 ring[kWsRing][2][kWsProducers];  // sums at (point A, point B)
-  double2 pw[2][4][kWsProducers];     // [plane parity][field][pair]
+  double2 pw[NB][NF][kWsProducers];   // [plane parity][field][pair]
   unsigned long long full[kWsRing];
   unsigned long long empty[kWsRing];
   unsigned long long tbar;            // producers: plane tile complete
   int abort;
 };
 
-template <class A>
-__device__ __forceinline__ void ws_init(WsSmem<A>& sm) {
+// Register budgets of the two roles (setmaxnreg): the CTA is launched with 80
+// per thread (two CTAs of 384 threads per SM), so 256 P + 128 C must equal
+// 384 * 80 = 30720 (checked at compile time).
+template <int P, int C>
+__device__ __forceinline__ void ws_producer_regs() {
+  static_assert(kWsProducers * P + kWsConsumers * C == kWsThreads * 80, "register split");
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(P) : "memory");
+}
+template <int P, int C>
+__device__ __forceinline__ void ws_consumer_regs() {
+  static_assert(kWsProducers * P + kWsConsumers * C == kWsThreads * 80, "register split");
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(C) : "memory");
+}
+
+template <class S>
+__device__ __forceinline__ void ws_init(S& sm) {
   if (threadIdx.x == 0) {
     for (int r = 0; r < kWsRing; ++r) {
       mbar_init(&sm.full[r], kWsProducers);
@@ -129,10 +148,10 @@ __device__ __forceinline__ void ws_init(WsSmem<A>& sm) {
 // Producer role for one work item (threads 0..255).  g counts the planes the
 // CTA has handed over since the launch (ring slot and barrier phases follow
 // it).  Returns false if a wait gave up.
-template <class A>
+template <class A, class S>
 __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
                                            const double* const (&F)[2], const A (&arith)[2],
-                                           WsSmem<A>& sm, unsigned& err, unsigned& g) {
+                                           S& sm, unsigned& err, unsigned& g) {
   using T = typename A::T;
   using T2 = typename A::T2;
   const int txh = it.txh;
@@ -296,9 +315,11 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
 // exactly as run_items does.  stall != 0 (failure-detection tests only):
 // the consumers never release a slot, so the producers' wait for a free slot
 // runs out.  Returns false if a wait gave up.
-template <class A, class Epi>
-__device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, WsSmem<A>& sm,
+template <class Epi, class S>
+__device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, S& sm,
                                            unsigned& err, unsigned& g, Epi& epi, int stall) {
+  using A = typename S::Arith;
+  static_assert(S::kNF == Epi::NF, "staging and epilogue disagree on the pointwise fields");
   using T = typename A::T;
   using T2 = typename A::T2;
   const int ctid = threadIdx.x - kWsProducers;
@@ -337,49 +358,83 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, WsSm
     op[j] = off0 + (actA[j] ? gxs[j] + gys[j] * py : 0) + it.z0 * pz;
     oi[j] = op[j];
   }
-  // the pointwise fields of the thread's pairs on the next plane, by cp.async
-  auto stage_pw = [&](int buf) {
+  // the pointwise fields of pair j on the next plane, by cp.async
+  auto stage_one = [&](int buf, int j) {
+    if (actA[j]) {
 #pragma unroll
-    for (int j = 0; j < kWsPairs; ++j) {
-      if (actA[j]) {
-#pragma unroll
-        for (int f = 0; f < Epi::NF; ++f) cp_async16(&sm.pw[buf][f][t[j]], epi.f[f] + ck(op[j]));
-      }
-      op[j] += pz;
+      for (int f = 0; f < Epi::NF; ++f) cp_async16(&sm.pw[buf][f][t[j]], epi.f[f] + ck(op[j]));
     }
-    cp_async_commit();
+    op[j] += pz;
   };
-  stage_pw(g & 1);
+  auto hand = [&](int j, int k, const double2 (&pw)[Epi::NF], unsigned slot) {
+    T rA[2], rB[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const T2 s = sm.ring[slot][f][t[j]];
+      rA[f] = s.x;
+      rB[f] = s.y;
+    }
+    epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k);
+  };
   bool ok = true;
-  for (int kk = 0; kk < it.nzr; ++kk) {
-    const int k = it.z0 + kk;
-    const int pb = (int)(g & 1u);
-    if (kk + 1 < it.nzr)
-      stage_pw(pb ^ 1);
-    else
+  if (S::kNB == 2) {
+    // both pairs one plane ahead in one commit group per plane
+    auto stage_pw = [&](int buf) {
+#pragma unroll
+      for (int j = 0; j < kWsPairs; ++j) stage_one(buf, j);
       cp_async_commit();
-    cp_async_wait_one();  // this thread's pointwise values of plane k have landed
-    const unsigned slot = g % kWsRing;
-    if (!(ok = mbar_wait(&sm.full[slot], (g / kWsRing) & 1u, &sm.abort))) break;
+    };
+    stage_pw(g & 1);
+    for (int kk = 0; kk < it.nzr; ++kk) {
+      const int k = it.z0 + kk;
+      const int pb = (int)(g & 1u);
+      if (kk + 1 < it.nzr)
+        stage_pw(pb ^ 1);
+      else
+        cp_async_commit();
+      cp_async_wait_one();  // this thread's pointwise values of plane k have landed
+      const unsigned slot = g % kWsRing;
+      if (!(ok = mbar_wait(&sm.full[slot], (g / kWsRing) & 1u, &sm.abort))) break;
+#pragma unroll
+      for (int j = 0; j < kWsPairs; ++j) {
+        if (actA[j] && ok_pt(oi[j], gxs[j], gys[j], k, actB[j])) {
+          double2 pw[Epi::NF];
+#pragma unroll
+          for (int f = 0; f < Epi::NF; ++f) pw[f] = sm.pw[pb & (S::kNB - 1)][f][t[j]];
+          hand(j, k, pw, slot);
+        }
+        oi[j] += pz;
+      }
+      if (!stall) mbar_arrive(&sm.empty[slot]);
+      ++g;
+    }
+  } else {
+    // one buffer: one commit group per pair and plane; a pair's values are
+    // copied to registers, its next plane is requested, then its epilogue
+    // runs (the oldest pending group is always the next pair's)
 #pragma unroll
     for (int j = 0; j < kWsPairs; ++j) {
-      if (actA[j] && ok_pt(oi[j], gxs[j], gys[j], k, actB[j])) {
-        T rA[2], rB[2];
+      stage_one(0, j);
+      cp_async_commit();
+    }
+    for (int kk = 0; kk < it.nzr; ++kk) {
+      const int k = it.z0 + kk;
+      const unsigned slot = g % kWsRing;
+      if (!(ok = mbar_wait(&sm.full[slot], (g / kWsRing) & 1u, &sm.abort))) break;
 #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          const T2 s = sm.ring[slot][f][t[j]];
-          rA[f] = s.x;
-          rB[f] = s.y;
-        }
+      for (int j = 0; j < kWsPairs; ++j) {
+        cp_async_wait_n<kWsPairs - 1>();  // pair j's values of plane k have landed
         double2 pw[Epi::NF];
 #pragma unroll
-        for (int f = 0; f < Epi::NF; ++f) pw[f] = sm.pw[pb][f][t[j]];
-        epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k);
+        for (int f = 0; f < Epi::NF; ++f) pw[f] = sm.pw[0][f][t[j]];
+        if (kk + 1 < it.nzr) stage_one(0, j);
+        cp_async_commit();
+        if (actA[j] && ok_pt(oi[j], gxs[j], gys[j], k, actB[j])) hand(j, k, pw, slot);
+        oi[j] += pz;
       }
-      oi[j] += pz;
+      if (!stall) mbar_arrive(&sm.empty[slot]);
+      ++g;
     }
-    if (!stall) mbar_arrive(&sm.empty[slot]);
-    ++g;
   }
   cp_async_wait_all();
   return ok;

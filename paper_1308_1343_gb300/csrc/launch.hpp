@@ -111,6 +111,38 @@ struct Adj2Args {
   unsigned* err;
 };
 
+// The adjoint step in two warp-specialised passes (kernels.cu, adj_ws_kernel):
+//   first : (Phat4, Phat3) = L^ (z0_in, z1_in) = L^ (c2 b, c2 a); writes
+//           z0_out = c2 Phat4, z1_out = c2 Phat3 (stencil inputs of the second
+//           pass), the parts of ybar that need Phat4 and Phat3 into yu, yp
+//           (in place), and the whole c2bar update (in place);
+//   second: (Phat2, Phat1) = L^ (z0_in, z1_in); completes ybar in yu, yp and
+//           writes z0_out = c2 ybar.pi, z1_out = c2 ybar.u (the next adjoint
+//           step's stencil inputs).
+struct AdjWsArgs {
+  const DItem* items;
+  int nitems;
+  int ndom;
+  const DBox* boxes;
+  const double* z0_in;
+  const double* z1_in;
+  const double* c2;
+  double* yu;
+  double* yp;
+  double* c2bar;      // first pass
+  const double* q1;   // first pass: recorded C_1 Lw0 ... C_4 Lw3
+  const double* q2;
+  const double* q3;
+  const double* q4;
+  double* z0_out;
+  double* z1_out;
+  const AdjCoef* coef;      // [ndom]
+  const unsigned* emax_in;  // [2 ndom]: bounds of z0_in, z1_in
+  unsigned* emax_out;       // [2 ndom]: of z0_out, z1_out (zero on entry)
+  unsigned* err;
+  int stall;                // failure-detection tests only (as PairArgs)
+};
+
 struct AdjCombineArgs {
   double* yu;          // in: a (adjoint of the step output); out: of its input
   double* yp;          // in: b; out
@@ -158,6 +190,7 @@ cudaError_t pair_occupancy(int arith, int* blocks_per_sm);
 // the warp-specialised pass kernels (384 threads: 8 producer, 4 consumer warps)
 cudaError_t launch_pair_ws(int arith, bool second, const PairArgs& a, int grid, cudaStream_t s);
 cudaError_t pair_ws_occupancy(int arith, int* blocks_per_sm);
+cudaError_t launch_adj_ws(bool second, int arith, const AdjWsArgs& a, int grid, cudaStream_t s);
 // two fields over one exchange list; block 0 zeroes clear[0..nclear)
 cudaError_t launch_gather2(const DRect* rects, const DChunk* chunks, int nchunks, double* f,
                            double* g, unsigned* clear, int nclear, cudaStream_t s);

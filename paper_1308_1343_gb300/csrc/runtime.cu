@@ -1242,10 +1242,15 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
                           fixed ? slot(0) : nullptr, D->grid_small, s));
   SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yu, Y,
                           fixed ? slot(1) : nullptr, D->grid_small, s));
-  // the only gathers of the sweep: later stencil inputs have their ghosts
-  // pushed by the kernels that write them
-  SC_CUDA(enq_fill(q, X));
-  SC_CUDA(enq_fill(q, Y));
+  // warp-specialised adjoint passes (with the warp-specialised two-stage
+  // form): the stencil inputs of each pass are gathered before it; otherwise
+  // these are the only gathers of the sweep and later stencil inputs have
+  // their ghosts pushed by the kernels that write them
+  const bool ws = pairs && L->pass_ws;
+  if (!ws) {
+    SC_CUDA(enq_fill(q, X));
+    SC_CUDA(enq_fill(q, Y));
+  }
 
   long long n_adj = 0;
   for (int c = nck - 1; c >= 0; --c) {
@@ -1261,6 +1266,52 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     }
     for (int n = len - 1; n >= 0; --n, ++n_adj) {
       const int p = (int)(n_adj & 1), pn = 1 - p;
+      if (ws) {
+        // first pass: (Phat4, Phat3) = L^ (X, Y); X', Y' = c2 (Phat4, Phat3);
+        // the parts of ybar with Phat4, Phat3; the c2bar update.  Second pass:
+        // (Phat2, Phat1) = L^ (X', Y'); ybar; X, Y = c2 (ybar.pi, ybar.u).
+        // Each gather zeroes the exponent slots its pass accumulates into.
+        dev::AdjWsArgs w{};
+        w.items = D->items;
+        w.nitems = D->nitems;
+        w.ndom = nd;
+        w.boxes = D->boxes;
+        w.c2 = c2;
+        w.yu = Yu;
+        w.yp = Yp;
+        w.c2bar = g_c2;
+        w.q1 = lapw[4 * n + 0];
+        w.q2 = lapw[4 * n + 1];
+        w.q3 = lapw[4 * n + 2];
+        w.q4 = lapw[4 * n + 3];
+        w.coef = D->acoef;
+        w.err = D->err;
+        SC_CUDA(enq_fill2(q, X, Y, fixed ? slot(4 + 2 * p) : nullptr));
+        w.z0_in = X;
+        w.z1_in = Y;
+        w.z0_out = Xp;
+        w.z1_out = Yq;
+        w.emax_in = slot(2 * p);
+        w.emax_out = slot(4 + 2 * p);
+        L->launches++;
+        {
+          TimedLaunch t(q, SC_KERNEL_ADJ_A);
+          SC_CUDA(dev::launch_adj_ws(false, L->arith, w, D->grid_pair_ws, s));
+        }
+        SC_CUDA(enq_fill2(q, Xp, Yq, fixed ? slot(2 * pn) : nullptr));
+        w.z0_in = Xp;
+        w.z1_in = Yq;
+        w.z0_out = X;
+        w.z1_out = Y;
+        w.emax_in = slot(4 + 2 * p);
+        w.emax_out = slot(2 * pn);
+        L->launches++;
+        {
+          TimedLaunch t(q, SC_KERNEL_ADJ_B);
+          SC_CUDA(dev::launch_adj_ws(true, L->arith, w, D->grid_pair_ws, s));
+        }
+        continue;
+      }
       // (Phat4, Phat3) = L^ (c2 b, c2 a), (X', Y') = c2 (Phat4, Phat3)
       dev::Adj2Args a{};
       a.items = D->items_one ? D->items_one : D->items;

@@ -1,5 +1,6 @@
 """The warp-specialised pass kernels (sc_level_set_pass_kernel,
-SC_PASS_WARP_SPECIALISED) against the one-role pass kernels, through the C
+SC_PASS_WARP_SPECIALISED) and adjoint passes against the one-role pass
+kernels and adjoint passes with their combination kernel, through the C
 ABI: bit-identical states and gradients on every layout the one-role
 kernels are tested on (ragged, thin and odd boxes, an uneven level, an
 ensemble with per-domain step sizes, self-periodic boxes, every tile width
@@ -122,6 +123,46 @@ def test_taped_gradient_bit_identical(orc, arith):
     ou, op, oc = orc.grad_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 11, 4, su,
                                    np.zeros_like(su))
     assert rel_err(res[1][0], ou) <= 1e-10 and rel_err(res[1][2], oc) <= 1e-10
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_adjoint_passes_bit_identical_on_uneven_level_and_ensemble(orc, arith):
+    """The warp-specialised adjoint passes (which also form the adjoint
+    combination) against the one-role adjoint passes and combination kernel:
+    the same gradients bit for bit on an uneven 16-box level (ghosts of
+    every stencil input gathered) and on an ensemble with per-domain step
+    sizes; and the oracle's within 1e-10."""
+    import torch
+    uneven = W.uneven_level(n=(64, 48, 40), h=1.0 / 48, levels=4, seed=6, box_seed=31)
+    ens = [W.bumpy_instance(W.Domain((n, n, n), 1.0 / n), 5000 + i)
+           for i, n in enumerate((24, 32, 16))]
+    for insts, nsteps, ckpt in (([uneven], 7, 3), (ens, 5, 2)):
+        res = []
+        for kind in (0, 1):
+            lev = make_level(insts)
+            lev.set_arith(arith)
+            lev.set_fusion(2)
+            lev.set_pass_kernel(kind)
+            up = lambda arrs, fill=0.0: upload(lev, arrs, fill)
+            su = [W.random_direction(i.dom.shape, 60 + k) for k, i in enumerate(insts)]
+            sp = [W.random_direction(i.dom.shape, 70 + k) for k, i in enumerate(insts)]
+            g = [torch.empty(lev.field_size, dtype=torch.float64, device="cuda")
+                 for _ in range(3)]
+            lev.grad(up([i.u for i in insts]), up([i.pi for i in insts]),
+                     up([i.c2 for i in insts], 1.0), [i.dt for i in insts], nsteps, ckpt,
+                     up(su), up(sp), *g)
+            lev.sync()
+            res.append([lev.gather(x) for x in g])
+            lev.close()
+        for a, b in zip(res[0], res[1]):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+        for k, inst in enumerate(insts):
+            ou, op, oc = orc.grad_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt,
+                                           nsteps, ckpt, su[k], sp[k])
+            assert rel_err(res[1][0][k], ou) <= 1e-10
+            assert rel_err(res[1][1][k], op) <= 1e-10
+            assert rel_err(res[1][2][k], oc) <= 1e-10
 
 
 def test_bounded_wait_runs_out_and_is_reported():
