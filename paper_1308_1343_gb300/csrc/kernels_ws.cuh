@@ -311,8 +311,9 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
 
 // Consumer role for one work item (threads 256..): pairs ctid + j *
 // kWsConsumers (j < kWsPairs) of the tile.  For every plane it calls
-//   epi.point(idx, pw, rA, rB, actB, x, y, k)
-// exactly as run_items does.  stall != 0 (failure-detection tests only):
+//   epi.point(idx, pw, rA, rB, actB, x, y, k, zdup)
+// as run_items does, with zdup the offset of the point's periodic image in
+// the z ghosts of a self-periodic box (else 0).  stall != 0 (failure-detection tests only):
 // the consumers never release a slot, so the producers' wait for a free slot
 // runs out.  Returns false if a wait gave up.
 template <class Epi, class S>
@@ -366,6 +367,12 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, S& s
     }
     op[j] += pz;
   };
+  // a box that alone tiles its periodic domain (bx.wrap) has no other box to
+  // take its z ghosts from: the consumers write them, the outputs of planes
+  // 0, 1 again nz planes up and those of nz-2, nz-1 nz planes down (boxes of
+  // at least 4 planes; the host gathers the z faces of thinner ones)
+  const bool zpush = bx.wrap != 0 && bx.nz >= 4;
+  const int zper = bx.nz * pz;
   auto hand = [&](int j, int k, const double2 (&pw)[Epi::NF], unsigned slot) {
     T rA[2], rB[2];
 #pragma unroll
@@ -374,7 +381,8 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, S& s
       rA[f] = s.x;
       rB[f] = s.y;
     }
-    epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k);
+    const int zdup = !zpush ? 0 : (k < 2 ? zper : (k >= bx.nz - 2 ? -zper : 0));
+    epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k, zdup);
   };
   bool ok = true;
   if (S::kNB == 2) {

@@ -84,6 +84,14 @@ struct DeviceState {
   // self-periodic (DBox::wrap): the exchange that stencil inputs need
   dev::DChunk* gchunks_nw = nullptr;
   int ngchunks_nw = 0;
+  // the same without the z faces of self-periodic boxes of at least 4 planes,
+  // whose z ghosts the warp-specialised kernels write themselves
+  // (gchunks_ws), and those z faces alone (gchunks_wz: gathered once at the
+  // start of a run, whose inputs come from outside)
+  dev::DChunk* gchunks_ws = nullptr;
+  int ngchunks_ws = 0;
+  dev::DChunk* gchunks_wz = nullptr;
+  int ngchunks_wz = 0;
   std::vector<char> box_wrap;
   // interior rectangles (one per box) + chunks
   dev::DRect* irects = nullptr;

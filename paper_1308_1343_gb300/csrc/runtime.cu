@@ -164,7 +164,8 @@ void release_device(sc_level* L) {
     cudaEventDestroy(pr.second);
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
-  void* ptrs[] = {D->boxes, D->items, D->items_one, D->grects, D->gchunks, D->gchunks_nw, D->irects, D->ichunks,
+  void* ptrs[] = {D->boxes, D->items, D->items_one, D->grects, D->gchunks, D->gchunks_nw,
+                  D->gchunks_ws, D->gchunks_wz, D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial, D->xsend, D->xsend_chunks, D->xrecv,
                   D->xrecv_chunks};
@@ -338,6 +339,16 @@ static int init_device(sc_level* L, int cur) {
         if (!D->box_wrap[b] || zface[gchunks[c].rect]) nw.push_back(gchunks[c]);
     D->ngchunks_nw = (int)nw.size();
     if (!nw.empty() && (rc = upload(&D->gchunks_nw, nw))) return rc;
+    std::vector<DChunk> ws, wz;
+    for (int b = 0; b < nb; ++b) {
+      const bool pushed = D->box_wrap[b] && L->boxes[b].hi[2] - L->boxes[b].lo[2] >= 4;
+      for (int c = D->box_gchunks[b]; c < D->box_gchunks[b + 1]; ++c)
+        if (!D->box_wrap[b] || zface[gchunks[c].rect]) (pushed ? wz : ws).push_back(gchunks[c]);
+    }
+    D->ngchunks_ws = (int)ws.size();
+    D->ngchunks_wz = (int)wz.size();
+    if (!ws.empty() && (rc = upload(&D->gchunks_ws, ws))) return rc;
+    if (!wz.empty() && (rc = upload(&D->gchunks_wz, wz))) return rc;
   }
 
   // the same copies seen from their sources: a ghost on the low (high) side
@@ -677,17 +688,25 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
 
 // Ghost gather of two fields; the exponent slots `clear` (2 ndom, may be
 // NULL) are zeroed for the kernel that follows.
+// Whether the stencil inputs of the level's passes carry the z ghosts of its
+// self-periodic boxes, written by the warp-specialised kernels that produce
+// them (from a run's first pass on: enq_prologue gathers the first inputs').
+static bool ws_pushes(const Enq& q) {
+  return q.L->fuse == 2 && q.L->pass_ws && !q.per_box && !q.all_ghosts;
+}
+
 static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear) {
   DeviceState* D = q.L->dev;
   const int nclear = clear ? 2 * (int)q.L->doms.size() : 0;
   bool cleared = clear == nullptr;
   if (!q.per_box) {
-    const int n = q.all_ghosts ? D->ngchunks : D->ngchunks_nw;
+    const bool ws = ws_pushes(q);
+    const int n = q.all_ghosts ? D->ngchunks : (ws ? D->ngchunks_ws : D->ngchunks_nw);
+    const DChunk* list = q.all_ghosts ? D->gchunks : (ws ? D->gchunks_ws : D->gchunks_nw);
     if (n > 0) {
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
-      cudaError_t e = dev::launch_gather2(D->grects, q.all_ghosts ? D->gchunks : D->gchunks_nw,
-                                          n, f, g, clear, nclear, q.s);
+      cudaError_t e = dev::launch_gather2(D->grects, list, n, f, g, clear, nclear, q.s);
       if (e != cudaSuccess) return e;
       cleared = true;
     }
@@ -792,6 +811,15 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
 static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const double* c2,
                                 double* const* W) {
   DeviceState* D = q.L->dev;
+  if (pi && ws_pushes(q) && D->ngchunks_wz > 0) {
+    // the run's inputs come from outside: the z faces of self-periodic boxes,
+    // which the warp-specialised passes write for every later input
+    (*q.count)++;
+    TimedLaunch t(q, SC_KERNEL_GATHER);
+    cudaError_t e0 = dev::launch_gather2(D->grects, D->gchunks_wz, D->ngchunks_wz, u, pi,
+                                         nullptr, 0, q.s);
+    if (e0 != cudaSuccess) return e0;
+  }
   if (q.push) {
     cudaError_t e0 = enq_fill(q, u);  // ghosts of the run's first stencil input
     if (e0 != cudaSuccess) return e0;
@@ -1250,6 +1278,12 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
   if (!ws) {
     SC_CUDA(enq_fill(q, X));
     SC_CUDA(enq_fill(q, Y));
+  } else if (D->ngchunks_wz > 0) {
+    // the z faces of self-periodic boxes of the first stencil inputs; the
+    // warp-specialised adjoint passes write those of every later one
+    L->launches++;
+    TimedLaunch t(q, SC_KERNEL_GATHER);
+    SC_CUDA(dev::launch_gather2(D->grects, D->gchunks_wz, D->ngchunks_wz, X, Y, nullptr, 0, s));
   }
 
   long long n_adj = 0;
