@@ -277,11 +277,8 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
  * extent and x, y extents >= 2 (a self-periodic box), is an exception: the
  * kernels read the periodic images of its interior for its x and y ghosts,
  * which are not written, and only its z ghosts are gathered (in
- * SC_MODE_PER_BOX every ghost is gathered).  With the warp-specialised pass
- * kernels (sc_level_set_pass_kernel) the z ghosts of a self-periodic box of
- * at least 4 planes are gathered once per call and then written by the
- * kernels with every pass's outputs, so on return they hold the result.
- * sc_level_fill_ghosts always fills every ghost.
+ * SC_MODE_PER_BOX every ghost is gathered).  sc_level_fill_ghosts always
+ * fills every ghost.
  * mode is one of SC_MODE_*.  Scratch stage arrays are allocated on the first
  * call.
  * A level with a domain that is not periodic on every axis takes ONE step

@@ -384,26 +384,14 @@ struct PairEpi {
     }
   }
 
-  // zdup != 0 (the warp-specialised kernels, a self-periodic box's planes 0,
-  // 1, nz-2, nz-1): the stencil-input outputs are also stored zdup elements
-  // away, at the periodic image of the point in the box's z ghosts
   __device__ __forceinline__ void point(int i, const double2* pw,
                                         const typename A::T (&rA)[2],
                                         const typename A::T (&rB)[2], bool actB, int, int,
-                                        int, int zdup = 0) {
+                                        int, int = 0) {
     const double2 u0 = pw[0], p0 = pw[1], q = pw[2], x = pw[3];
     double2 un, pn, lv, q0, q1;
     one(rA[0], rA[1], u0.x, p0.x, q.x, x.x, un.x, pn.x, lv.x, q0.x, q1.x);
     one(rB[0], rB[1], u0.y, p0.y, q.y, x.y, un.y, pn.y, lv.y, q0.y, q1.y);
-    if (zdup) {
-      if (actB) {
-        st2(out_u + i + zdup, un);
-        st2(out_p + i + zdup, pn);
-      } else {
-        out_u[i + zdup] = un.x;
-        out_p[i + zdup] = pn.x;
-      }
-    }
     if (actB) {
       // pass A's outputs go out with an evict-first hint (measured: 4 %
       // faster; pass B was 3 % slower with it)
@@ -665,6 +653,10 @@ struct AdjWsEpi {
   // first: c2, a, b, c2bar, Q1..Q4 (one buffer, each pair's next plane as
   // soon as its values are read); second: ybar.u part, ybar.pi part, c2
   static constexpr int NF = SECOND ? 3 : 8;
+  // the z ghosts of a self-periodic box's stencil-input outputs are written
+  // here (zdup): its adjoint passes need no gathers (measured: the forward
+  // passes were 2 % slower with it, more than the gathers they saved)
+  static constexpr bool kZPush = true;
   const double* f[NF];
   double* yu;
   double* yp;
@@ -708,7 +700,7 @@ struct AdjWsEpi {
     double2 z0, z1, ou, op, oc;
     one(rA[0], rA[1], va, z0.x, z1.x, ou.x, op.x, oc.x);
     one(rB[0], rB[1], vb, z0.y, z1.y, ou.y, op.y, oc.y);
-    if (zdup) {  // the next pass's stencil inputs into the z ghosts (see PairEpi)
+    if (zdup) {  // the next pass's stencil inputs, at their z-ghost images too
       if (actB) {
         st2(zo0 + i + zdup, z0);
         st2(zo1 + i + zdup, z1);
@@ -744,6 +736,7 @@ struct AdjWsEpi {
 template <class A, bool SECOND>
 __global__ void __launch_bounds__(kWsThreads, 2) adj_ws_kernel(AdjWsArgs a) {
   __shared__ WsSmem<A, SECOND ? 3 : 8, SECOND ? 2 : 1> sm;
+  if (A::kFixed) clear_slot(a.emax_clear, 2 * a.ndom);
   ws_init(sm);
   unsigned err = 0, g = 0;
   bool ok = true;

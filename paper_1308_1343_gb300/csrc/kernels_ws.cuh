@@ -132,6 +132,18 @@ __device__ __forceinline__ void ws_consumer_regs() {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(C) : "memory");
 }
 
+// Epi::kZPush if the epilogue declares it (it then takes the z-ghost offset
+// of a self-periodic box's outer planes and stores its stencil-input outputs
+// there too), else false
+template <class E, class = void>
+struct ZPushOf {
+  static constexpr bool value = false;
+};
+template <class E>
+struct ZPushOf<E, std::void_t<decltype(E::kZPush)>> {
+  static constexpr bool value = E::kZPush;
+};
+
 template <class S>
 __device__ __forceinline__ void ws_init(S& sm) {
   if (threadIdx.x == 0) {
@@ -371,7 +383,7 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, S& s
   // take its z ghosts from: the consumers write them, the outputs of planes
   // 0, 1 again nz planes up and those of nz-2, nz-1 nz planes down (boxes of
   // at least 4 planes; the host gathers the z faces of thinner ones)
-  const bool zpush = bx.wrap != 0 && bx.nz >= 4;
+  const bool zpush = ZPushOf<Epi>::value && bx.wrap != 0 && bx.nz >= 4;
   const int zper = bx.nz * pz;
   auto hand = [&](int j, int k, const double2 (&pw)[Epi::NF], unsigned slot) {
     T rA[2], rB[2];

@@ -139,6 +139,7 @@ struct AdjWsArgs {
   const AdjCoef* coef;      // [ndom]
   const unsigned* emax_in;  // [2 ndom]: bounds of z0_in, z1_in
   unsigned* emax_out;       // [2 ndom]: of z0_out, z1_out (zero on entry)
+  unsigned* emax_clear;     // [2 ndom] zeroed by the kernel for a later launch
   unsigned* err;
   int stall;                // failure-detection tests only (as PairArgs)
 };

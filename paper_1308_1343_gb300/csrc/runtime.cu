@@ -688,21 +688,13 @@ static cudaError_t enq_step(const Enq& q, double* u, double* pi, const double* c
 
 // Ghost gather of two fields; the exponent slots `clear` (2 ndom, may be
 // NULL) are zeroed for the kernel that follows.
-// Whether the stencil inputs of the level's passes carry the z ghosts of its
-// self-periodic boxes, written by the warp-specialised kernels that produce
-// them (from a run's first pass on: enq_prologue gathers the first inputs').
-static bool ws_pushes(const Enq& q) {
-  return q.L->fuse == 2 && q.L->pass_ws && !q.per_box && !q.all_ghosts;
-}
-
 static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear) {
   DeviceState* D = q.L->dev;
   const int nclear = clear ? 2 * (int)q.L->doms.size() : 0;
   bool cleared = clear == nullptr;
   if (!q.per_box) {
-    const bool ws = ws_pushes(q);
-    const int n = q.all_ghosts ? D->ngchunks : (ws ? D->ngchunks_ws : D->ngchunks_nw);
-    const DChunk* list = q.all_ghosts ? D->gchunks : (ws ? D->gchunks_ws : D->gchunks_nw);
+    const int n = q.all_ghosts ? D->ngchunks : D->ngchunks_nw;
+    const DChunk* list = q.all_ghosts ? D->gchunks : D->gchunks_nw;
     if (n > 0) {
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
@@ -811,15 +803,6 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
 static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const double* c2,
                                 double* const* W) {
   DeviceState* D = q.L->dev;
-  if (pi && ws_pushes(q) && D->ngchunks_wz > 0) {
-    // the run's inputs come from outside: the z faces of self-periodic boxes,
-    // which the warp-specialised passes write for every later input
-    (*q.count)++;
-    TimedLaunch t(q, SC_KERNEL_GATHER);
-    cudaError_t e0 = dev::launch_gather2(D->grects, D->gchunks_wz, D->ngchunks_wz, u, pi,
-                                         nullptr, 0, q.s);
-    if (e0 != cudaSuccess) return e0;
-  }
   if (q.push) {
     cudaError_t e0 = enq_fill(q, u);  // ghosts of the run's first stencil input
     if (e0 != cudaSuccess) return e0;
@@ -1270,20 +1253,24 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
                           fixed ? slot(0) : nullptr, D->grid_small, s));
   SC_CUDA(dev::launch_mul(D->irects, D->ichunks, D->nichunks, c2, Yu, Y,
                           fixed ? slot(1) : nullptr, D->grid_small, s));
-  // warp-specialised adjoint passes (with the warp-specialised two-stage
-  // form): the stencil inputs of each pass are gathered before it; otherwise
-  // these are the only gathers of the sweep and later stencil inputs have
-  // their ghosts pushed by the kernels that write them
-  const bool ws = pairs && L->pass_ws;
+  // Warp-specialised adjoint passes with the two-stage form, unless the
+  // caller fixed the one-role kernels: the ghosts of each pass's stencil
+  // inputs are gathered before it, except the z ghosts of self-periodic boxes
+  // (the passes write them; those of the first inputs are gathered here).
+  // Otherwise these are the only gathers of the sweep and later stencil
+  // inputs have their ghosts pushed by the kernels that write them.
+  const bool ws = pairs && !(L->pass_fixed && !L->pass_ws);
+  auto gather_ws = [&](double* f, double* g, const DChunk* list, int n) -> cudaError_t {
+    if (n <= 0) return cudaSuccess;
+    L->launches++;
+    TimedLaunch t(q, SC_KERNEL_GATHER);
+    return dev::launch_gather2(D->grects, list, n, f, g, nullptr, 0, s);
+  };
   if (!ws) {
     SC_CUDA(enq_fill(q, X));
     SC_CUDA(enq_fill(q, Y));
-  } else if (D->ngchunks_wz > 0) {
-    // the z faces of self-periodic boxes of the first stencil inputs; the
-    // warp-specialised adjoint passes write those of every later one
-    L->launches++;
-    TimedLaunch t(q, SC_KERNEL_GATHER);
-    SC_CUDA(dev::launch_gather2(D->grects, D->gchunks_wz, D->ngchunks_wz, X, Y, nullptr, 0, s));
+  } else {
+    SC_CUDA(gather_ws(X, Y, D->gchunks_wz, D->ngchunks_wz));
   }
 
   long long n_adj = 0;
@@ -1320,25 +1307,31 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
         w.q4 = lapw[4 * n + 3];
         w.coef = D->acoef;
         w.err = D->err;
-        SC_CUDA(enq_fill2(q, X, Y, fixed ? slot(4 + 2 * p) : nullptr));
+        // exponent slots: the first pass writes slot 4+2p (zeroed by the
+        // previous step's first pass) and zeroes 4+2pn for the next one; the
+        // second writes 2pn (zeroed by the previous step's second pass) and
+        // zeroes 2p, which this step's first pass has read
+        SC_CUDA(gather_ws(X, Y, D->gchunks_ws, D->ngchunks_ws));
         w.z0_in = X;
         w.z1_in = Y;
         w.z0_out = Xp;
         w.z1_out = Yq;
         w.emax_in = slot(2 * p);
         w.emax_out = slot(4 + 2 * p);
+        w.emax_clear = slot(4 + 2 * pn);
         L->launches++;
         {
           TimedLaunch t(q, SC_KERNEL_ADJ_A);
           SC_CUDA(dev::launch_adj_ws(false, L->arith, w, D->grid_pair_ws, s));
         }
-        SC_CUDA(enq_fill2(q, Xp, Yq, fixed ? slot(2 * pn) : nullptr));
+        SC_CUDA(gather_ws(Xp, Yq, D->gchunks_ws, D->ngchunks_ws));
         w.z0_in = Xp;
         w.z1_in = Yq;
         w.z0_out = X;
         w.z1_out = Y;
         w.emax_in = slot(4 + 2 * p);
         w.emax_out = slot(2 * pn);
+        w.emax_clear = slot(2 * p);
         L->launches++;
         {
           TimedLaunch t(q, SC_KERNEL_ADJ_B);
