@@ -558,6 +558,10 @@ struct Enq {
   // the exponent bounds of the run's input are already in place (see
   // level_steps)
   bool bounds = false;
+  // the passes are the warp-specialised recording kernels, which write the z
+  // ghosts of self-periodic boxes (of at least 4 planes) with their outputs:
+  // the prologue gathers those of the run's inputs, later gathers skip them
+  bool zpushed = false;
 };
 
 // Event pair around one launch when timing is on.
@@ -693,8 +697,9 @@ static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear
   const int nclear = clear ? 2 * (int)q.L->doms.size() : 0;
   bool cleared = clear == nullptr;
   if (!q.per_box) {
-    const int n = q.all_ghosts ? D->ngchunks : D->ngchunks_nw;
-    const DChunk* list = q.all_ghosts ? D->gchunks : D->gchunks_nw;
+    const bool ws = q.zpushed && !q.all_ghosts;
+    const int n = q.all_ghosts ? D->ngchunks : (ws ? D->ngchunks_ws : D->ngchunks_nw);
+    const DChunk* list = q.all_ghosts ? D->gchunks : (ws ? D->gchunks_ws : D->gchunks_nw);
     if (n > 0) {
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
@@ -803,6 +808,15 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
 static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const double* c2,
                                 double* const* W) {
   DeviceState* D = q.L->dev;
+  if (q.zpushed && pi && !q.per_box && D->ngchunks_wz > 0) {
+    // the z faces of self-periodic boxes of the run's inputs (the passes
+    // write those of every later input)
+    (*q.count)++;
+    TimedLaunch t(q, SC_KERNEL_GATHER);
+    cudaError_t e0 = dev::launch_gather2(D->grects, D->gchunks_wz, D->ngchunks_wz, u, pi,
+                                         nullptr, 0, q.s);
+    if (e0 != cudaSuccess) return e0;
+  }
   if (q.push) {
     cudaError_t e0 = enq_fill(q, u);  // ghosts of the run's first stencil input
     if (e0 != cudaSuccess) return e0;
@@ -1278,12 +1292,23 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     const int len = std::min(K, nsteps - c * K);
     SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
-    SC_CUDA(enq_prologue(q, Su, pairs ? Sp : nullptr, c2, W));
-    for (int n = 0; n < len; ++n) {
-      Enq qf = q;
-      qf.push = !pairs;
-      SC_CUDA(pairs ? enq_step_pairs(qf, Su, Sp, W, lapw.data() + 4 * n)
-                    : enq_step(qf, Su, Sp, c2, W, lapw.data() + 4 * n));
+    {
+      // with the warp-specialised adjoint, the recomputation runs the
+      // warp-specialised recording passes too (they write the z ghosts of
+      // self-periodic boxes); the level's own choice is restored after
+      const int pass_ws = L->pass_ws;
+      if (ws) L->pass_ws = 1;
+      Enq qr = q;
+      qr.zpushed = ws;
+      cudaError_t e = enq_prologue(qr, Su, pairs ? Sp : nullptr, c2, W);
+      for (int n = 0; n < len && e == cudaSuccess; ++n) {
+        Enq qf = qr;
+        qf.push = !pairs;
+        e = pairs ? enq_step_pairs(qf, Su, Sp, W, lapw.data() + 4 * n)
+                  : enq_step(qf, Su, Sp, c2, W, lapw.data() + 4 * n);
+      }
+      L->pass_ws = pass_ws;
+      SC_CUDA(e);
     }
     for (int n = len - 1; n >= 0; --n, ++n_adj) {
       const int p = (int)(n_adj & 1), pn = 1 - p;
