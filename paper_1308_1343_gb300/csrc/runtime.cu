@@ -1293,13 +1293,15 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     SC_CUDA(cudaMemcpyAsync(Su, cku[c], bytes, cudaMemcpyDeviceToDevice, s));
     SC_CUDA(cudaMemcpyAsync(Sp, ckp[c], bytes, cudaMemcpyDeviceToDevice, s));
     {
-      // with the warp-specialised adjoint, the recomputation runs the
-      // warp-specialised recording passes too (they write the z ghosts of
-      // self-periodic boxes); the level's own choice is restored after
+      // with the warp-specialised adjoint on a level with self-periodic boxes
+      // the recomputation runs the warp-specialised recording passes, which
+      // write those boxes' z ghosts (no gathers after the first pass); else
+      // the level's own pass kernels.  The level's choice is restored after
+      const bool rec_ws = ws && (L->pass_ws || D->ngchunks_wz > 0);
       const int pass_ws = L->pass_ws;
-      if (ws) L->pass_ws = 1;
+      if (rec_ws) L->pass_ws = 1;
       Enq qr = q;
-      qr.zpushed = ws;
+      qr.zpushed = rec_ws;
       cudaError_t e = enq_prologue(qr, Su, pairs ? Sp : nullptr, c2, W);
       for (int n = 0; n < len && e == cudaSuccess; ++n) {
         Enq qf = qr;
