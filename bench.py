@@ -286,7 +286,7 @@ def _time_steps(torch, lev, u, pi, c2, dt, nsteps, mode, reps, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-EXTRAS = ("fp64", "uneven", "ensemble", "two_level", "adjoint")
+EXTRAS = ("fp64", "uneven", "ensemble", "two_level", "adjoint", "dist")
 
 
 def _time_grad(torch, lev, u0, pi0, c2, dt, nsteps, ckpt, stream, reps=2):
@@ -323,6 +323,52 @@ def _extras(torch, W, B, Level, arith, stream, which=EXTRAS):
         out["two_level"] = _two_level(torch, W, B, Level, arith, stream)
     if "adjoint" in which:
         out["adjoint"] = _adjoint(torch, W, B, Level, arith, stream)
+    if "dist" in which:
+        out["dist_emulated"] = _dist_emulated(torch, W, B, Level, arith, stream)
+    return out
+
+
+def _dist_emulated(torch, W, B, Level, arith, stream):
+    """The distributed level's kernels on one GPU: the 64-box level split over
+    two ranks (spatial bisection), both ranks' parts in this process, their
+    exchange blocks copied device to device between the passes (no NCCL, no
+    second GPU): what the partition, the pack and unpack kernels and the split
+    step cost against the one-level graph run of the same level."""
+    from paper_1308_1343_gb300.dist import DistLevel, partition, step_ranks
+    inst = W.uneven_level()
+    boxes = [(lo, hi, 0) for lo, hi in inst.boxes]
+    doms = [dict(hi=inst.dom.n, h=inst.dom.h, periodic=7)]
+    nranks = 2
+    owner = partition(boxes, nranks, B.SC_DIST_BISECT)
+    levs = [DistLevel(boxes, doms, nranks, r, owner) for r in range(nranks)]
+    for L in levs:
+        L.set_arith(arith)
+    us = [L.to_device([inst.u]) for L in levs]
+    ps = [L.to_device([inst.pi]) for L in levs]
+    cs = [L.to_device([inst.c2], fill=1.0) for L in levs]
+    step_ranks(levs, us, ps, cs, inst.dt, 2, stream=stream)
+    torch.cuda.synchronize()
+    nsteps = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step_ranks(levs, us, ps, cs, inst.dt, nsteps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    for L in levs:
+        L.sync(stream)
+    t = e0.elapsed_time(e1) / 1e3
+    sent = sum(L.send_doubles for L in levs) * 8 * 2  # two exchanges per step
+    out = {"workload": "512x512x256 periodic domain, 64 bisected boxes, over 2 ranks "
+                       "(spatial bisection) held in one process on one GPU; exchange blocks "
+                       "copied device to device between the passes (no NCCL)",
+           "ranks": nranks, "boxes_per_rank": [len(L.boxes) for L in levs],
+           "rk4_steps": nsteps, "updates_per_s": inst.u.size * nsteps / t,
+           "ms_per_step": 1e3 * t / nsteps, "exchanged_bytes_per_step": sent}
+    for L in levs:
+        L.close()
+    del us, ps, cs
+    torch.cuda.empty_cache()
     return out
 
 
