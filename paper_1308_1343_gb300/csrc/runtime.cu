@@ -733,14 +733,12 @@ static cudaError_t enq_pair(const Enq& q, dev::PairArgs a, bool second) {
     TimedLaunch t(q, kind);
     return launch_pass(q.L, second, a, q.s);
   }
-  // one launch per box: the one-role kernels (bit-identical), whose smaller
-  // CTAs fill the GPU better with one box's items than the 384-thread ones
   for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
     a.items = D->items + D->box_items[b];
     a.nitems = D->box_items[b + 1] - D->box_items[b];
     (*q.count)++;
     TimedLaunch t(q, kind);
-    cudaError_t e = dev::launch_pair(q.L->arith, second, a, D->grid_pair, q.s);
+    cudaError_t e = launch_pass(q.L, second, a, q.s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
