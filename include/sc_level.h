@@ -276,8 +276,10 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
  * A box that alone tiles a domain periodic on every axis, with an even x
  * extent and x, y extents >= 2 (a self-periodic box), is an exception: the
  * kernels read the periodic images of its interior for its x and y ghosts,
- * which are not written, and only its z ghosts are gathered (in
- * SC_MODE_PER_BOX every ghost is gathered).  sc_level_fill_ghosts always
+ * which are not written, and only its z ghosts are gathered; the
+ * warp-specialised two-stage passes (SC_PASS_WARP_SPECIALISED) read its z
+ * ghosts the same way when its z extent is >= 2, and gather nothing for it
+ * (in SC_MODE_PER_BOX every ghost is gathered).  sc_level_fill_ghosts always
  * fills every ghost.
  * mode is one of SC_MODE_*.  Scratch stage arrays are allocated on the first
  * call.

@@ -14,10 +14,12 @@ struct DBox {
   long long pz;   // plane pitch (elements)
   int nx, ny, nz; // interior extent
   int dom;        // domain index
-  int wrap;       // 1: the box alone tiles a domain periodic on every axis
-                  // (nx even, nx and ny >= 2), so the stencil kernels read
-                  // the periodic images of its interior in x and y directly,
-                  // and only its z ghosts are gathered
+  int wrap;       // bit 0: the box alone tiles a domain periodic on every
+                  // axis (nx even, nx and ny >= 2), so the stencil kernels read
+                  // the periodic images of its interior in x and y directly;
+                  // bit 1: also nz >= 2, and the warp-specialised kernels read
+                  // its z ghosts the same way (the one-role kernels have them
+                  // gathered)
 };
 
 struct DItem {

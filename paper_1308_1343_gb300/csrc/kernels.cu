@@ -342,11 +342,6 @@ template <class A, bool SECOND, bool RECORD>
 struct PairEpi {
   static constexpr int NF = 4;  // y.u, y.pi, q = c2 dt/(12 h^2), then A: q/3, B: L y.u
   static constexpr bool kDefer = SECOND;  // measured: faster for pass B only
-  // The recording passes (the adjoint's recomputation) write the z ghosts of
-  // a self-periodic box's outputs themselves in the warp-specialised kernels
-  // (zdup), so the recomputation needs no gathers after its first pass; the
-  // plain forward passes gather them (measured 2 % faster at 256^3)
-  static constexpr bool kZPush = RECORD;
   const double* f[NF];
   double* out_u;
   double* out_p;
@@ -392,20 +387,11 @@ struct PairEpi {
   __device__ __forceinline__ void point(int i, const double2* pw,
                                         const typename A::T (&rA)[2],
                                         const typename A::T (&rB)[2], bool actB, int, int,
-                                        int, int zdup = 0) {
+                                        int) {
     const double2 u0 = pw[0], p0 = pw[1], q = pw[2], x = pw[3];
     double2 un, pn, lv, q0, q1;
     one(rA[0], rA[1], u0.x, p0.x, q.x, x.x, un.x, pn.x, lv.x, q0.x, q1.x);
     one(rB[0], rB[1], u0.y, p0.y, q.y, x.y, un.y, pn.y, lv.y, q0.y, q1.y);
-    if (kZPush && zdup) {  // the stencil-input outputs at their z-ghost images too
-      if (actB) {
-        st2(out_u + i + zdup, un);
-        st2(out_p + i + zdup, pn);
-      } else {
-        out_u[i + zdup] = un.x;
-        out_p[i + zdup] = pn.x;
-      }
-    }
     if (actB) {
       // pass A's outputs go out with an evict-first hint (measured: 4 %
       // faster; pass B was 3 % slower with it)
@@ -667,10 +653,6 @@ struct AdjWsEpi {
   // first: c2, a, b, c2bar, Q1..Q4 (one buffer, each pair's next plane as
   // soon as its values are read); second: ybar.u part, ybar.pi part, c2
   static constexpr int NF = SECOND ? 3 : 8;
-  // the z ghosts of a self-periodic box's stencil-input outputs are written
-  // here (zdup): its adjoint passes need no gathers (measured: the forward
-  // passes were 2 % slower with it, more than the gathers they saved)
-  static constexpr bool kZPush = true;
   const double* f[NF];
   double* yu;
   double* yp;
@@ -704,7 +686,7 @@ struct AdjWsEpi {
   __device__ __forceinline__ void point(int i, const double2* pw,
                                         const typename A::T (&rA)[2],
                                         const typename A::T (&rB)[2], bool actB, int, int,
-                                        int, int zdup = 0) {
+                                        int) {
     double va[NF], vb[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -714,15 +696,6 @@ struct AdjWsEpi {
     double2 z0, z1, ou, op, oc;
     one(rA[0], rA[1], va, z0.x, z1.x, ou.x, op.x, oc.x);
     one(rB[0], rB[1], vb, z0.y, z1.y, ou.y, op.y, oc.y);
-    if (zdup) {  // the next pass's stencil inputs, at their z-ghost images too
-      if (actB) {
-        st2(zo0 + i + zdup, z0);
-        st2(zo1 + i + zdup, z1);
-      } else {
-        zo0[i + zdup] = z0.x;
-        zo1[i + zdup] = z1.x;
-      }
-    }
     if (actB) {
       st2(zo0 + i, z0);
       st2(zo1 + i, z1);

@@ -132,18 +132,6 @@ __device__ __forceinline__ void ws_consumer_regs() {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(C) : "memory");
 }
 
-// Epi::kZPush if the epilogue declares it (it then takes the z-ghost offset
-// of a self-periodic box's outer planes and stores its stencil-input outputs
-// there too), else false
-template <class E, class = void>
-struct ZPushOf {
-  static constexpr bool value = false;
-};
-template <class E>
-struct ZPushOf<E, std::void_t<decltype(E::kZPush)>> {
-  static constexpr bool value = E::kZPush;
-};
-
 template <class S>
 __device__ __forceinline__ void ws_init(S& sm) {
   if (threadIdx.x == 0) {
@@ -230,8 +218,17 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
     const int oz = out_of(k, bx.nz);
     return arith[f].conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
   };
-  int oc = colOff + (it.z0 + 2) * pz;  // next column load (plane k+2)
-  int oh = hg + it.z0 * pz;            // next halo load (plane k)
+  // a self-periodic box of at least two planes (bx.wrap & 2) reads its z
+  // ghosts from their periodic images too -- planes -2, -1 are nz-2, nz-1 and
+  // planes nz, nz+1 are 0, 1 -- so that it needs no gather at all: the column
+  // pointer goes back to plane 0 after plane nz-1 (halo loads stay inside)
+  const bool zwrap = (bx.wrap & 2) != 0;
+  auto wz = [&](int k) {
+    return !zwrap ? k : (k < 0 ? k + bx.nz : (k >= bx.nz ? k - bx.nz : k));
+  };
+  const int ocLast = zwrap ? colOff + (bx.nz - 1) * pz : -1;
+  int oc = colOff + wz(it.z0 + 2) * pz;  // next column load (plane k+2)
+  int oh = hg + it.z0 * pz;              // next halo load (plane k)
   // raw halo pairs of plane k and column pairs of plane k+2, by cp.async
   auto stage_raw = [&](int buf) {
 #pragma unroll
@@ -240,16 +237,16 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
 #pragma unroll
     for (int f = 0; f < 2; ++f) cp_async16(&sm.craw[buf][f][tid], F[f] + ck(oc));
     oh += pz;
-    oc += pz;
+    oc = oc == ocLast ? colOff : oc + pz;
     cp_async_commit();
   };
   T2 qa[2], qb[2], qc[2], qd[2], qe[2];
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
-    qa[f] = conv_at(f, ld2(F[f] + ck(oc - 4 * pz)), it.z0 - 2);
-    qb[f] = conv_at(f, ld2(F[f] + ck(oc - 3 * pz)), it.z0 - 1);
-    qc[f] = conv_at(f, ld2(F[f] + ck(oc - 2 * pz)), it.z0);
-    qd[f] = conv_at(f, ld2(F[f] + ck(oc - pz)), it.z0 + 1);
+    qa[f] = conv_at(f, ld2(F[f] + ck(colOff + wz(it.z0 - 2) * pz)), it.z0 - 2);
+    qb[f] = conv_at(f, ld2(F[f] + ck(colOff + wz(it.z0 - 1) * pz)), it.z0 - 1);
+    qc[f] = conv_at(f, ld2(F[f] + ck(colOff + it.z0 * pz)), it.z0);
+    qd[f] = conv_at(f, ld2(F[f] + ck(colOff + wz(it.z0 + 1) * pz)), it.z0 + 1);
   }
   stage_raw(g & 1);
   const int rowSelf = (ly + 2) * W + 2 * lx + 2;
@@ -323,9 +320,8 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
 
 // Consumer role for one work item (threads 256..): pairs ctid + j *
 // kWsConsumers (j < kWsPairs) of the tile.  For every plane it calls
-//   epi.point(idx, pw, rA, rB, actB, x, y, k, zdup)
-// as run_items does, with zdup the offset of the point's periodic image in
-// the z ghosts of a self-periodic box (else 0).  stall != 0 (failure-detection tests only):
+//   epi.point(idx, pw, rA, rB, actB, x, y, k)
+// as run_items does.  stall != 0 (failure-detection tests only):
 // the consumers never release a slot, so the producers' wait for a free slot
 // runs out.  Returns false if a wait gave up.
 template <class Epi, class S>
@@ -379,12 +375,6 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, S& s
     }
     op[j] += pz;
   };
-  // a box that alone tiles its periodic domain (bx.wrap) has no other box to
-  // take its z ghosts from: the consumers write them, the outputs of planes
-  // 0, 1 again nz planes up and those of nz-2, nz-1 nz planes down (boxes of
-  // at least 4 planes; the host gathers the z faces of thinner ones)
-  const bool zpush = ZPushOf<Epi>::value && bx.wrap != 0 && bx.nz >= 4;
-  const int zper = bx.nz * pz;
   auto hand = [&](int j, int k, const double2 (&pw)[Epi::NF], unsigned slot) {
     T rA[2], rB[2];
 #pragma unroll
@@ -393,8 +383,7 @@ __device__ __forceinline__ bool ws_consume(const DItem& it, const DBox& bx, S& s
       rA[f] = s.x;
       rB[f] = s.y;
     }
-    const int zdup = !zpush ? 0 : (k < 2 ? zper : (k >= bx.nz - 2 ? -zper : 0));
-    epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k, zdup);
+    epi.point(oi[j], pw, rA, rB, actB[j], gxs[j], gys[j], k);
   };
   bool ok = true;
   if (S::kNB == 2) {

@@ -80,18 +80,16 @@ struct DeviceState {
   dev::DChunk* gchunks = nullptr;
   int ngchunks = 0;
   std::vector<int> box_gchunks;
-  // the chunks of the gather list whose destination box is not
-  // self-periodic (DBox::wrap): the exchange that stencil inputs need
+  // the chunks of the gather list that the one-role stencil kernels need:
+  // every ghost of a box that is not self-periodic (DBox::wrap), the z ghosts
+  // of one that is
   dev::DChunk* gchunks_nw = nullptr;
   int ngchunks_nw = 0;
-  // the same without the z faces of self-periodic boxes of at least 4 planes,
-  // whose z ghosts the warp-specialised kernels write themselves
-  // (gchunks_ws), and those z faces alone (gchunks_wz: gathered once at the
-  // start of a run, whose inputs come from outside)
-  dev::DChunk* gchunks_ws = nullptr;
-  int ngchunks_ws = 0;
-  dev::DChunk* gchunks_wz = nullptr;
-  int ngchunks_wz = 0;
+  // those the warp-specialised kernels need: the same without the z ghosts
+  // of self-periodic boxes of two planes or more, which they read from the
+  // periodic images
+  dev::DChunk* gchunks_nz = nullptr;
+  int ngchunks_nz = 0;
   std::vector<char> box_wrap;
   // interior rectangles (one per box) + chunks
   dev::DRect* irects = nullptr;

@@ -165,7 +165,8 @@ void release_device(sc_level* L) {
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
   void* ptrs[] = {D->boxes, D->items, D->items_one, D->grects, D->gchunks, D->gchunks_nw,
-                  D->gchunks_ws, D->gchunks_wz, D->irects, D->ichunks,
+                  D->gchunks_nz,
+                  D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial, D->xsend, D->xsend_chunks, D->xrecv,
                   D->xrecv_chunks};
@@ -272,14 +273,17 @@ static int init_device(sc_level* L, int cur) {
     // self-periodic: the box is its domain, periodic on every axis; the
     // kernels then read the owners of its x and y ghosts by wrapping the
     // coordinates (pairs of x-points stay 16-byte aligned for an even x
-    // extent), and only its z ghosts are gathered
+    // extent), the warp-specialised ones those of its z ghosts too (two
+    // planes or more); the one-role kernels have its z ghosts gathered
     bool self = Dm.periodic == 7u;
     for (int d = 0; d < 3; ++d) self = self && B.lo[d] == Dm.lo[d] && B.hi[d] == Dm.hi[d];
     self = self && B.hi[0] - B.lo[0] >= 2 && B.hi[1] - B.lo[1] >= 2 &&
            (B.hi[0] - B.lo[0]) % 2 == 0;
-    D->box_wrap[b] = self ? 1 : 0;
+    const int zw = self && B.hi[2] - B.lo[2] >= 2 ? 2 : 0;
+    D->box_wrap[b] = self ? 1 | zw : 0;
     boxes[b] = DBox{L->off[b], L->py[b], L->pz[b], (int)(B.hi[0] - B.lo[0]),
-                    (int)(B.hi[1] - B.lo[1]), (int)(B.hi[2] - B.lo[2]), B.domain, self ? 1 : 0};
+                    (int)(B.hi[1] - B.lo[1]), (int)(B.hi[2] - B.lo[2]), B.domain,
+                    D->box_wrap[b]};
   }
   int rc = upload(&D->boxes, boxes);
   if (rc) return rc;
@@ -339,16 +343,16 @@ static int init_device(sc_level* L, int cur) {
         if (!D->box_wrap[b] || zface[gchunks[c].rect]) nw.push_back(gchunks[c]);
     D->ngchunks_nw = (int)nw.size();
     if (!nw.empty() && (rc = upload(&D->gchunks_nw, nw))) return rc;
-    std::vector<DChunk> ws, wz;
-    for (int b = 0; b < nb; ++b) {
-      const bool pushed = D->box_wrap[b] && L->boxes[b].hi[2] - L->boxes[b].lo[2] >= 4;
+    // the exchange the warp-specialised kernels need: every ghost of an
+    // ordinary box, none of a self-periodic one (but the z ghosts of one of
+    // a single plane)
+    std::vector<DChunk> nzl;
+    for (int b = 0; b < nb; ++b)
       for (int c = D->box_gchunks[b]; c < D->box_gchunks[b + 1]; ++c)
-        if (!D->box_wrap[b] || zface[gchunks[c].rect]) (pushed ? wz : ws).push_back(gchunks[c]);
-    }
-    D->ngchunks_ws = (int)ws.size();
-    D->ngchunks_wz = (int)wz.size();
-    if (!ws.empty() && (rc = upload(&D->gchunks_ws, ws))) return rc;
-    if (!wz.empty() && (rc = upload(&D->gchunks_wz, wz))) return rc;
+        if (!D->box_wrap[b] || (zface[gchunks[c].rect] && !(D->box_wrap[b] & 2)))
+          nzl.push_back(gchunks[c]);
+    D->ngchunks_nz = (int)nzl.size();
+    if (!nzl.empty() && (rc = upload(&D->gchunks_nz, nzl))) return rc;
   }
 
   // the same copies seen from their sources: a ghost on the low (high) side
@@ -558,10 +562,6 @@ struct Enq {
   // the exponent bounds of the run's input are already in place (see
   // level_steps)
   bool bounds = false;
-  // the passes are the warp-specialised recording kernels, which write the z
-  // ghosts of self-periodic boxes (of at least 4 planes) with their outputs:
-  // the prologue gathers those of the run's inputs, later gathers skip them
-  bool zpushed = false;
 };
 
 // Event pair around one launch when timing is on.
@@ -697,9 +697,10 @@ static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear
   const int nclear = clear ? 2 * (int)q.L->doms.size() : 0;
   bool cleared = clear == nullptr;
   if (!q.per_box) {
-    const bool ws = q.zpushed && !q.all_ghosts;
-    const int n = q.all_ghosts ? D->ngchunks : (ws ? D->ngchunks_ws : D->ngchunks_nw);
-    const DChunk* list = q.all_ghosts ? D->gchunks : (ws ? D->gchunks_ws : D->gchunks_nw);
+    // the pass kernels that follow read what is gathered here
+    const bool ws = q.L->pass_ws && !q.all_ghosts;
+    const int n = q.all_ghosts ? D->ngchunks : (ws ? D->ngchunks_nz : D->ngchunks_nw);
+    const DChunk* list = q.all_ghosts ? D->gchunks : (ws ? D->gchunks_nz : D->gchunks_nw);
     if (n > 0) {
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
@@ -808,15 +809,6 @@ static cudaError_t enq_step_pairs(const Enq& q, double* u, double* pi, double* c
 static cudaError_t enq_prologue(const Enq& q, double* u, double* pi, const double* c2,
                                 double* const* W) {
   DeviceState* D = q.L->dev;
-  if (q.zpushed && pi && !q.per_box && D->ngchunks_wz > 0) {
-    // the z faces of self-periodic boxes of the run's inputs (the passes
-    // write those of every later input)
-    (*q.count)++;
-    TimedLaunch t(q, SC_KERNEL_GATHER);
-    cudaError_t e0 = dev::launch_gather2(D->grects, D->gchunks_wz, D->ngchunks_wz, u, pi,
-                                         nullptr, 0, q.s);
-    if (e0 != cudaSuccess) return e0;
-  }
   if (q.push) {
     cudaError_t e0 = enq_fill(q, u);  // ghosts of the run's first stencil input
     if (e0 != cudaSuccess) return e0;
@@ -1269,10 +1261,10 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
                           fixed ? slot(1) : nullptr, D->grid_small, s));
   // Warp-specialised adjoint passes with the two-stage form, unless the
   // caller fixed the one-role kernels: the ghosts of each pass's stencil
-  // inputs are gathered before it, except the z ghosts of self-periodic boxes
-  // (the passes write them; those of the first inputs are gathered here).
-  // Otherwise these are the only gathers of the sweep and later stencil
-  // inputs have their ghosts pushed by the kernels that write them.
+  // inputs are gathered before it, except those of self-periodic boxes (the
+  // passes read their periodic images).  Otherwise these are the only
+  // gathers of the sweep and later stencil inputs have their ghosts pushed by
+  // the kernels that write them.
   const bool ws = pairs && !(L->pass_fixed && !L->pass_ws);
   auto gather_ws = [&](double* f, double* g, const DChunk* list, int n) -> cudaError_t {
     if (n <= 0) return cudaSuccess;
@@ -1283,8 +1275,6 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
   if (!ws) {
     SC_CUDA(enq_fill(q, X));
     SC_CUDA(enq_fill(q, Y));
-  } else {
-    SC_CUDA(gather_ws(X, Y, D->gchunks_wz, D->ngchunks_wz));
   }
 
   long long n_adj = 0;
@@ -1295,13 +1285,12 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
     {
       // with the warp-specialised adjoint on a level with self-periodic boxes
       // the recomputation runs the warp-specialised recording passes, which
-      // write those boxes' z ghosts (no gathers after the first pass); else
-      // the level's own pass kernels.  The level's choice is restored after
-      const bool rec_ws = ws && (L->pass_ws || D->ngchunks_wz > 0);
+      // need no gathers for those boxes; else the level's own pass kernels.
+      // The level's choice is restored after
+      const bool rec_ws = ws && (L->pass_ws || D->ngchunks_nz < D->ngchunks_nw);
       const int pass_ws = L->pass_ws;
       if (rec_ws) L->pass_ws = 1;
       Enq qr = q;
-      qr.zpushed = rec_ws;
       cudaError_t e = enq_prologue(qr, Su, pairs ? Sp : nullptr, c2, W);
       for (int n = 0; n < len && e == cudaSuccess; ++n) {
         Enq qf = qr;
@@ -1338,7 +1327,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
         // previous step's first pass) and zeroes 4+2pn for the next one; the
         // second writes 2pn (zeroed by the previous step's second pass) and
         // zeroes 2p, which this step's first pass has read
-        SC_CUDA(gather_ws(X, Y, D->gchunks_ws, D->ngchunks_ws));
+        SC_CUDA(gather_ws(X, Y, D->gchunks_nz, D->ngchunks_nz));
         w.z0_in = X;
         w.z1_in = Y;
         w.z0_out = Xp;
@@ -1351,7 +1340,7 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
           TimedLaunch t(q, SC_KERNEL_ADJ_A);
           SC_CUDA(dev::launch_adj_ws(false, L->arith, w, D->grid_pair_ws, s));
         }
-        SC_CUDA(gather_ws(Xp, Yq, D->gchunks_ws, D->ngchunks_ws));
+        SC_CUDA(gather_ws(Xp, Yq, D->gchunks_nz, D->ngchunks_nz));
         w.z0_in = Xp;
         w.z1_in = Yq;
         w.z0_out = X;
