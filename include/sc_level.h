@@ -273,6 +273,10 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
  * ghosts of every stencil input are gathered before the pass that reads it
  * (one batched launch, inside the step's CUDA graph in SC_MODE_GRAPH), so on
  * return the ghosts of u hold the input of the last pass, not the result.
+ * The warp-specialised two-stage passes read the two-point-wide x-face
+ * ghosts that another box of the level owns (even x extents, 16-byte
+ * aligned rows) from that box directly; those ghosts are not gathered and
+ * keep older values.
  * A box that alone tiles a domain periodic on every axis, with an even x
  * extent and x, y extents >= 2 (a self-periodic box), is an exception: the
  * kernels read the periodic images of its interior for its x and y ghosts,

@@ -98,7 +98,10 @@ struct Timer {
       const bool mine = cls == kAll || L->box_class[b] == cls;
       const int tx = mine ? c.tx : L->classes[L->box_class[b]].tile.tile_x;
       const int tz = mine ? c.tz : L->classes[L->box_class[b]].tile.tile_z;
-      append_box_items(items, (int)b, nx, ny, nz, tx, 2 * dev_threads() / tx, tz);
+      const auto& cuts = L->dev->xg_cuts;
+      const bool cut = cuts.size() == 2 * L->boxes.size();
+      append_box_items(items, (int)b, nx, ny, nz, tx, 2 * dev_threads() / tx, tz,
+                       cut ? &cuts[2 * b] : nullptr, cut ? &cuts[2 * b + 1] : nullptr);
     }
     if (items.size() > cap) {
       if (ditems) cudaFree(ditems);
@@ -132,6 +135,8 @@ struct Timer {
     p.emax_in = D->emax;
     p.emax_out = D->emax + 2 * nd;
     p.err = D->err;
+    p.xg = D->xg;
+    p.xg_ofs = D->xg_ofs;
     launch_pass(L, false, p, s);
     p.s0 = W[2];
     p.s1 = W[3];

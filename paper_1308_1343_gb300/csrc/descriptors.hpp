@@ -81,6 +81,18 @@ struct DPush {
   int pad[3];
 };
 
+// One ghost copy into an x face of a box, read by the warp-specialised
+// kernels from its owner directly instead of being gathered (the copy's rows
+// are two points, 16 bytes, wide: half of every DRAM sector at both ends of
+// a gather).  In the destination box's interior coordinates it fills the
+// ghost pair of rows y in [y0, y1) of planes z in [z0, z1); the source of
+// row y0 of plane z0 is element src, and the source pitches are spy, spz.
+// sbox names the source box (bounds checks of the checked build).
+struct DXGhost {
+  int y0, y1, z0, z1;
+  int src, spy, spz, sbox;
+};
+
 // One ghost copy that crosses ranks of a distributed level, seen from this
 // rank: a rectangle of the local field (interior points of a local source
 // box when packing, ghost points of a local destination box when unpacking)

@@ -465,12 +465,13 @@ __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
   if (threadIdx.x < kWsProducers) {
     ws_producer_regs<96, 48>();
     const double* const F[2] = {a.s0, a.s1};
+    const XgTab xt{a.xg, a.xg_ofs, a.boxes};
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
       const DBox bx = a.boxes[it.box];
       const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
                        make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
-      ok = ws_produce(it, bx, F, ar, sm, err, g);
+      ok = ws_produce(it, bx, F, ar, sm, err, g, xt);
     }
   } else {
     ws_consumer_regs<96, 48>();
@@ -732,12 +733,13 @@ __global__ void __launch_bounds__(kWsThreads, 2) adj_ws_kernel(AdjWsArgs a) {
   if (threadIdx.x < kWsProducers) {
     ws_producer_regs<kP, kC>();
     const double* const F[2] = {a.z0_in, a.z1_in};
+    const XgTab xt{a.xg, a.xg_ofs, a.boxes};
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
       const DBox bx = a.boxes[it.box];
       const A ar[2] = {make_arith<A>(a.emax_in, bx.dom, err),
                        make_arith<A>(a.emax_in + a.ndom, bx.dom, err)};
-      ok = ws_produce(it, bx, F, ar, sm, err, g);
+      ok = ws_produce(it, bx, F, ar, sm, err, g, xt);
     }
   } else {
     ws_consumer_regs<kP, kC>();

@@ -132,6 +132,26 @@ __device__ __forceinline__ void ws_consumer_regs() {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(C) : "memory");
 }
 
+// x-face ghost copies read from their owners (DXGhost): per box b, entries
+// [ofs[2 b + side], ofs[2 b + side + 1]) of its low (side 0) and high (side
+// 1) x face; ofs == NULL: none (every ghost the kernels read is gathered)
+struct XgTab {
+  const DXGhost* e;
+  const int* ofs;
+  const DBox* boxes;
+};
+
+// The copy that holds ghost row y of planes [z, z + n) of face g (2 b +
+// side), or NULL (the row is gathered; work items at an x face end their
+// z-run where such a copy starts or ends, so no item has a row in two)
+__device__ __forceinline__ const DXGhost* xg_find(const XgTab& t, int g, int y, int z, int n) {
+  for (int j = t.ofs[g], j1 = t.ofs[g + 1]; j < j1; ++j) {
+    const DXGhost* e = t.e + j;
+    if (y >= e->y0 && y < e->y1 && z >= e->z0 && z + n <= e->z1) return e;
+  }
+  return nullptr;
+}
+
 template <class S>
 __device__ __forceinline__ void ws_init(S& sm) {
   if (threadIdx.x == 0) {
@@ -151,7 +171,8 @@ __device__ __forceinline__ void ws_init(S& sm) {
 template <class A, class S>
 __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
                                            const double* const (&F)[2], const A (&arith)[2],
-                                           S& sm, unsigned& err, unsigned& g) {
+                                           S& sm, unsigned& err, unsigned& g,
+                                           const XgTab& xt) {
   using T = typename A::T;
   using T2 = typename A::T2;
   const int txh = it.txh;
@@ -185,11 +206,42 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
 #else
   auto ck = [](int i) { return i; };
 #endif
-  const int colOff = colLoad ? off0 + wr(gx, bx.nx) + wr(gy, bx.ny) * py : off0;
+  // Column and halo pairs are read at a plane-0 offset + k * pitch.  A pair
+  // in the x-face ghosts of a box with neighbours (gx or ax is -2 or nx, its
+  // row inside the box) is read from the box that owns it where the table
+  // holds its copy: the owner's offset and plane pitch.  The item's planes
+  // lie in that one copy (work items end their z-run where the owner
+  // changes); the column's two planes beyond on either side are not used and
+  // lie in the owner's padded block.
+  const bool xgt = xt.ofs != nullptr && !wrap;
+  int colOff = colLoad ? off0 + wr(gx, bx.nx) + wr(gy, bx.ny) * py : off0;
+  int cpz = pz, hpz = pz;
+  bool cN = false, hN = false;  // the column / halo pair reads another box
+  // the owner of ghost row y of face fg (2 box + side) over the item's
+  // planes: offset and pitch, or false (the row is gathered)
+  auto owner = [&](int fg, int y, int& off, int& pitch) -> bool {
+    const DXGhost* e = xg_find(xt, fg, y, it.z0, it.nzr);
+    if (!e) return false;
+    const int o = e->src + (y - e->y0) * e->spy - e->z0 * e->spz;
+#ifdef SC_BOUNDS_CHECK
+    const DBox& sb = xt.boxes[e->sbox];
+    const int s0 = (int)sb.off - 2 - 2 * (int)sb.py - 2 * (int)sb.pz;
+    const int s1 = (int)sb.off - 3 + (int)sb.py + (sb.ny + 1) * (int)sb.py + (sb.nz + 1) * (int)sb.pz;
+    if (o + (it.z0 - 2) * e->spz < s0 || o + (it.z0 + it.nzr + 1) * e->spz + 1 > s1) {
+      err |= kErrBounds;
+      return false;
+    }
+#endif
+    off = o;
+    pitch = e->spz;
+    return true;
+  };
+  if (xgt && colLoad && gx == bx.nx && gy < bx.ny) cN = owner(2 * it.box + 1, gy, colOff, cpz);
   const int oy = out_of(gy, bx.ny);
   const int ox0 = out_of(gx, bx.nx) + oy, ox1 = out_of(gx + 1, bx.nx) + oy;
   // this thread's halo pair of the plane tile, if any (at most one: the halo
-  // of a tile has 4 txh + 2 TY <= 256 pairs for every allowed shape)
+  // of a tile has 4 txh + 2 TY <= 256 pairs for every allowed shape): rows
+  // -2, -1, TY, TY+1 of the tile's columns, then columns -2 and TX of its rows
   const int nhalo = 4 * txh + 2 * TY;
   const bool hasH = tid < nhalo;
   int hs = 0, hg = off0, hx0 = 2, hx1 = 2;
@@ -212,8 +264,19 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
       const int o = out_of(ay, bx.ny);
       hx0 = out_of(ax, bx.nx) + o;
       hx1 = out_of(ax + 1, bx.nx) + o;
+      // (a pair of the rows above or below the tile is one too where the
+      // tile is ragged in x)
+      if (xgt && (ax == -2 || ax == bx.nx) && ay >= 0 && ay < bx.ny)
+        hN = owner(2 * it.box + (ax < 0 ? 0 : 1), ay, hg, hpz);
     }
   }
+#ifdef SC_BOUNDS_CHECK
+  auto ckc = [&](int i) { return cN ? i : ck(i); };
+  auto ckh = [&](int i) { return hN ? i : ck(i); };
+#else
+  auto ckc = ck;
+  auto ckh = ck;
+#endif
   auto conv_at = [&](int f, double2 raw, int k) -> T2 {
     const int oz = out_of(k, bx.nz);
     return arith[f].conv(raw, ox0 + oz <= 1, ox1 + oz <= 1, err);
@@ -227,26 +290,26 @@ __device__ __forceinline__ bool ws_produce(const DItem& it, const DBox& bx,
     return !zwrap ? k : (k < 0 ? k + bx.nz : (k >= bx.nz ? k - bx.nz : k));
   };
   const int ocLast = zwrap ? colOff + (bx.nz - 1) * pz : -1;
-  int oc = colOff + wz(it.z0 + 2) * pz;  // next column load (plane k+2)
-  int oh = hg + it.z0 * pz;              // next halo load (plane k)
+  int oc = colOff + wz(it.z0 + 2) * cpz;  // next column load (plane k+2)
+  int oh = hg + it.z0 * hpz;              // next halo load (plane k)
   // raw halo pairs of plane k and column pairs of plane k+2, by cp.async
   auto stage_raw = [&](int buf) {
 #pragma unroll
     for (int f = 0; f < 2; ++f)
-      if (hasH) cp_async16(&sm.hraw[buf][f][tid], F[f] + ck(oh));
+      if (hasH) cp_async16(&sm.hraw[buf][f][tid], F[f] + ckh(oh));
 #pragma unroll
-    for (int f = 0; f < 2; ++f) cp_async16(&sm.craw[buf][f][tid], F[f] + ck(oc));
-    oh += pz;
-    oc = oc == ocLast ? colOff : oc + pz;
+    for (int f = 0; f < 2; ++f) cp_async16(&sm.craw[buf][f][tid], F[f] + ckc(oc));
+    oh += hpz;
+    oc = oc == ocLast ? colOff : oc + cpz;
     cp_async_commit();
   };
   T2 qa[2], qb[2], qc[2], qd[2], qe[2];
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
-    qa[f] = conv_at(f, ld2(F[f] + ck(colOff + wz(it.z0 - 2) * pz)), it.z0 - 2);
-    qb[f] = conv_at(f, ld2(F[f] + ck(colOff + wz(it.z0 - 1) * pz)), it.z0 - 1);
-    qc[f] = conv_at(f, ld2(F[f] + ck(colOff + it.z0 * pz)), it.z0);
-    qd[f] = conv_at(f, ld2(F[f] + ck(colOff + wz(it.z0 + 1) * pz)), it.z0 + 1);
+    qa[f] = conv_at(f, ld2(F[f] + ckc(colOff + wz(it.z0 - 2) * cpz)), it.z0 - 2);
+    qb[f] = conv_at(f, ld2(F[f] + ckc(colOff + wz(it.z0 - 1) * cpz)), it.z0 - 1);
+    qc[f] = conv_at(f, ld2(F[f] + ckc(colOff + it.z0 * cpz)), it.z0);
+    qd[f] = conv_at(f, ld2(F[f] + ckc(colOff + wz(it.z0 + 1) * cpz)), it.z0 + 1);
   }
   stage_raw(g & 1);
   const int rowSelf = (ly + 2) * W + 2 * lx + 2;

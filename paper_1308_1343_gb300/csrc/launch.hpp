@@ -12,6 +12,7 @@ struct DRect;
 struct DChunk;
 struct DXfer;
 struct DPush;
+struct DXGhost;
 struct DProl;
 struct DRestr;
 
@@ -76,6 +77,10 @@ struct PairArgs {
   unsigned* err;
   int stall;                // warp-specialised kernels, failure-detection tests
                             // only: consumers never release a ring slot
+  // warp-specialised kernels: x-face ghosts read from their owners, per box
+  // and side entries [xg_ofs[2 b + side], xg_ofs[2 b + side + 1]) (or NULL)
+  const DXGhost* xg;
+  const int* xg_ofs;
 };
 
 struct LapArgs {
@@ -142,6 +147,8 @@ struct AdjWsArgs {
   unsigned* emax_clear;     // [2 ndom] zeroed by the kernel for a later launch
   unsigned* err;
   int stall;                // failure-detection tests only (as PairArgs)
+  const DXGhost* xg;        // as PairArgs
+  const int* xg_ofs;
 };
 
 struct AdjCombineArgs {

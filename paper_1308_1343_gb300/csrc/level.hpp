@@ -28,7 +28,8 @@ int upload_items(sc_level* L);
 // tx x ty points and z-runs of at most tz planes, z-major: the z extent is
 // cut into ceil(nz / tz) runs whose lengths differ by at most one plane.
 void append_box_items(std::vector<dev::DItem>& items, int b, int nx, int ny, int nz, int tx,
-                      int ty, int tz);
+                      int ty, int tz, const std::vector<int>* cut_lo = nullptr,
+                      const std::vector<int>* cut_hi = nullptr);
 // nsteps RK4 steps as sc_level_rk4_step; qprep = false reuses the pre-scaled
 // wave speeds of the previous call (same c2 and dt); bounds = true reuses
 // the exponent bounds of (u, pi) left by the previous call's last pass, which
@@ -90,6 +91,16 @@ struct DeviceState {
   // periodic images
   dev::DChunk* gchunks_nz = nullptr;
   int ngchunks_nz = 0;
+  // x-face ghost copies that the warp-specialised kernels read from their
+  // owners (dev::DXGhost; not in gchunks_nz), per box and side; and, per box
+  // and side, the planes where their z ranges start or end inside the box:
+  // work items at that x face end their z-run there, so that each thread of
+  // an item reads its ghosts from one source box (measured: 4 % on the pass
+  // kernels of the uneven level, where a switch of source inside the plane
+  // loop cost 5 % there and 2 % on levels without such ghosts)
+  dev::DXGhost* xg = nullptr;
+  int* xg_ofs = nullptr;  // [2 nboxes + 1], NULL if there are none
+  std::vector<std::vector<int>> xg_cuts;  // [2 nboxes]
   std::vector<char> box_wrap;
   // interior rectangles (one per box) + chunks
   dev::DRect* irects = nullptr;

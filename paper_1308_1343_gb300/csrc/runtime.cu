@@ -16,6 +16,7 @@ using dev::DBox;
 using dev::DChunk;
 using dev::DItem;
 using dev::DPush;
+using dev::DXGhost;
 using dev::DRect;
 using dev::DXfer;
 using dev::StageCoef;
@@ -72,8 +73,11 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
     const sc_box& B = L->boxes[b];
     const SizeClass& C = L->classes[L->box_class[b]];
     const sc_tile& t = one_role && C.has_one ? C.tile_one : C.tile;
+    const auto& cuts = L->dev->xg_cuts;
+    const bool cut = cuts.size() == 2 * L->boxes.size();
     append_box_items(items, (int)b, (int)(B.hi[0] - B.lo[0]), (int)(B.hi[1] - B.lo[1]),
-                     (int)(B.hi[2] - B.lo[2]), t.tile_x, t.tile_y, t.tile_z);
+                     (int)(B.hi[2] - B.lo[2]), t.tile_x, t.tile_y, t.tile_z,
+                     cut ? &cuts[2 * b] : nullptr, cut ? &cuts[2 * b + 1] : nullptr);
   }
   box_items[L->boxes.size()] = (int)items.size();
 }
@@ -81,13 +85,31 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
 }  // namespace
 
 void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, int tx, int ty,
-                      int tz) {
+                      int tz, const std::vector<int>* cut_lo, const std::vector<int>* cut_hi) {
   const int runs = (nz + tz - 1) / tz;
   const int base = nz / runs, extra = nz % runs;
+  std::vector<int> at;
   for (int r = 0, z0 = 0; r < runs; ++r) {
     const int len = base + (r < extra ? 1 : 0);
     for (int y0 = 0; y0 < ny; y0 += ty)
-      for (int x0 = 0; x0 < nx; x0 += tx) items.push_back(DItem{b, x0, y0, z0, len, tx / 2});
+      for (int x0 = 0; x0 < nx; x0 += tx) {
+        // a tile at an x face whose ghosts are read from their owners ends
+        // its z-run where the owner changes
+        at.clear();
+        for (const std::vector<int>* c : {x0 == 0 ? cut_lo : nullptr,
+                                          x0 + tx >= nx ? cut_hi : nullptr})
+          if (c)
+            for (int z : *c)
+              if (z > z0 && z < z0 + len) at.push_back(z);
+        std::sort(at.begin(), at.end());
+        at.erase(std::unique(at.begin(), at.end()), at.end());
+        int za = z0;
+        for (int z : at) {
+          items.push_back(DItem{b, x0, y0, za, z - za, tx / 2});
+          za = z;
+        }
+        items.push_back(DItem{b, x0, y0, za, z0 + len - za, tx / 2});
+      }
     z0 += len;
   }
 }
@@ -165,7 +187,7 @@ void release_device(sc_level* L) {
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
   void* ptrs[] = {D->boxes, D->items, D->items_one, D->grects, D->gchunks, D->gchunks_nw,
-                  D->gchunks_nz,
+                  D->gchunks_nz, D->xg, D->xg_ofs,
                   D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
                   D->emax_adj, D->err, D->partial, D->xsend, D->xsend_chunks, D->xrecv,
@@ -297,6 +319,8 @@ static int init_device(sc_level* L, int cur) {
   std::vector<DRect> grects;
   std::vector<DChunk> gchunks;
   std::vector<char> zface;  // per rect: it fills z ghosts of its box
+  std::vector<char> xread;  // per rect: the warp-specialised kernels read it from its owner
+  std::vector<std::vector<DXGhost>> xgl((size_t)2 * nb);
   D->box_gchunks.assign(nb + 1, 0);
   {
     size_t c = 0;
@@ -320,6 +344,25 @@ static int init_device(sc_level* L, int cur) {
         r.pairs = (C.ext[0] % 2 == 0 && r.src % 2 == 0 && r.dst % 2 == 0) ? 1 : 0;
         grects.push_back(r);
         zface.push_back(C.dst_lo[2] < L->boxes[b].lo[2] || C.dst_lo[2] >= L->boxes[b].hi[2]);
+        // a copy into the x-face ghost pair of a box of even x extent (not
+        // self-periodic), 16-byte pairs at both ends, rows and planes inside
+        // the box: the producers of the warp-specialised kernels read it from
+        // the source box (x-face rows are the costly part of a gather)
+        {
+          const sc_box& Bd = L->boxes[b];
+          const int side = C.dst_lo[0] == Bd.lo[0] - 2 ? 0 : (C.dst_lo[0] == Bd.hi[0] ? 1 : -1);
+          const bool xr = side >= 0 && C.ext[0] == 2 && r.pairs && !D->box_wrap[b] &&
+                          (Bd.hi[0] - Bd.lo[0]) % 2 == 0 && C.dst_lo[1] >= Bd.lo[1] &&
+                          C.dst_lo[1] + C.ext[1] <= Bd.hi[1] && C.dst_lo[2] >= Bd.lo[2] &&
+                          C.dst_lo[2] + C.ext[2] <= Bd.hi[2];
+          xread.push_back(xr);
+          if (xr) {
+            const int y0 = (int)(C.dst_lo[1] - Bd.lo[1]), z0 = (int)(C.dst_lo[2] - Bd.lo[2]);
+            xgl[(size_t)2 * b + side].push_back(DXGhost{y0, y0 + (int)C.ext[1], z0,
+                                                        z0 + (int)C.ext[2], (int)r.src,
+                                                        (int)r.spy, (int)r.spz, C.src_box});
+          }
+        }
         add_chunks((int)grects.size() - 1, (C.ext[0] >> r.pairs) * C.ext[1] * C.ext[2],
                    gchunks, dev::kGatherChunk);
       }
@@ -348,11 +391,40 @@ static int init_device(sc_level* L, int cur) {
     // a single plane)
     std::vector<DChunk> nzl;
     for (int b = 0; b < nb; ++b)
-      for (int c = D->box_gchunks[b]; c < D->box_gchunks[b + 1]; ++c)
-        if (!D->box_wrap[b] || (zface[gchunks[c].rect] && !(D->box_wrap[b] & 2)))
+      for (int c = D->box_gchunks[b]; c < D->box_gchunks[b + 1]; ++c) {
+        const int rr = gchunks[c].rect;
+        if ((!D->box_wrap[b] && !xread[rr]) || (zface[rr] && !(D->box_wrap[b] & 2)))
           nzl.push_back(gchunks[c]);
+      }
     D->ngchunks_nz = (int)nzl.size();
     if (!nzl.empty() && (rc = upload(&D->gchunks_nz, nzl))) return rc;
+    // the x-face copies read from their owners, per box and side, and the
+    // planes where their z ranges start or end inside the box
+    std::vector<DXGhost> xe;
+    std::vector<int> xo(1, 0);
+    D->xg_cuts.assign((size_t)2 * nb, {});
+    for (int g = 0; g < 2 * nb; ++g) {
+      const int nz = (int)(L->boxes[g / 2].hi[2] - L->boxes[g / 2].lo[2]);
+      for (const DXGhost& e : xgl[g]) {
+        xe.push_back(e);
+        for (int z : {e.z0, e.z1})
+          if (z > 0 && z < nz) D->xg_cuts[g].push_back(z);
+      }
+      std::sort(D->xg_cuts[g].begin(), D->xg_cuts[g].end());
+      D->xg_cuts[g].erase(std::unique(D->xg_cuts[g].begin(), D->xg_cuts[g].end()),
+                          D->xg_cuts[g].end());
+      xo.push_back((int)xe.size());
+    }
+    // the kernels read a source column over an item's planes and two more on
+    // each side: the copy's source rows are interior rows of the source box,
+    // so those planes lie in its padded block
+    for (const DXGhost& e : xe)
+      if (!rect_in_field((int64_t)e.src - 2 * (int64_t)e.spz, e.spy, e.spz, 2, e.y1 - e.y0,
+                         e.z1 - e.z0 + 4, L->field_size))
+        return list_error("x-face read");
+    if (!xe.empty()) {
+      if ((rc = upload(&D->xg, xe)) || (rc = upload(&D->xg_ofs, xo))) return rc;
+    }
   }
 
   // the same copies seen from their sources: a ghost on the low (high) side
@@ -765,6 +837,8 @@ static cudaError_t enq_pass(const Enq& q, double* u, double* pi, double* const* 
   a.q = W[4];
   a.coef = D->coef;
   a.err = D->err;
+  a.xg = D->xg;
+  a.xg_ofs = D->xg_ofs;
   if (pass == 0) {
     cudaError_t e = enq_fill2(q, u, pi, fixed ? Y : nullptr);
     if (e != cudaSuccess) return e;
@@ -1287,7 +1361,9 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
       // the recomputation runs the warp-specialised recording passes, which
       // need no gathers for those boxes; else the level's own pass kernels.
       // The level's choice is restored after
-      const bool rec_ws = ws && (L->pass_ws || D->ngchunks_nz < D->ngchunks_nw);
+      bool zw = false;
+      for (char w : D->box_wrap) zw = zw || (w & 2);
+      const bool rec_ws = ws && (L->pass_ws || zw);
       const int pass_ws = L->pass_ws;
       if (rec_ws) L->pass_ws = 1;
       Enq qr = q;
@@ -1323,6 +1399,8 @@ int sc_level_backward_tape(sc_level* L, const double* c2, const double* gu_T,
         w.q4 = lapw[4 * n + 3];
         w.coef = D->acoef;
         w.err = D->err;
+        w.xg = D->xg;
+        w.xg_ofs = D->xg_ofs;
         // exponent slots: the first pass writes slot 4+2p (zeroed by the
         // previous step's first pass) and zeroes 4+2pn for the next one; the
         // second writes 2pn (zeroed by the previous step's second pass) and

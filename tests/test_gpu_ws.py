@@ -76,6 +76,34 @@ def test_uneven_level_and_thin_boxes(orc, arith):
     assert _same(one, ws)
 
 
+def _owner_change_level():
+    """Four boxes of a 64 x 24 x 40 periodic domain: across both x faces of
+    box 0 the owner of the ghosts changes along y (box 1 below y = 10) and,
+    inside a z-run, along z (boxes 2 and 3 above y = 10, split at z = 17);
+    box widths 26 and 38 leave ragged tiles at the x faces."""
+    dom = W.Domain((64, 24, 40), 1.0 / 24)
+    inst = W.bumpy_instance(dom, 11)
+    inst.boxes = [((0, 0, 0), (26, 24, 40)), ((26, 0, 0), (64, 10, 40)),
+                  ((26, 10, 0), (64, 24, 17)), ((26, 10, 17), (64, 24, 40))]
+    return inst
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("tx,tz", [(16, 40), (32, 8), (64, 13)])
+def test_x_face_ghosts_read_from_their_owners(orc, arith, mode, tx, tz):
+    """The warp-specialised producers read x-face ghosts from the boxes that
+    own them (those rows are not gathered), with work items at an x face
+    ending their z-run where the owner changes: bit-identical to the
+    one-role kernels, which gather every ghost, in every launch mode and for
+    z-runs that the owner change cuts, and within the bar of the oracle."""
+    inst = _owner_change_level()
+    one, ws = _both([inst], 5, arith, mode, tiles={c: (tx, tz) for c in range(3)})
+    assert _same(one, ws)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, inst.dom.h, inst.dt, 5)
+    assert rel_err(ws[0][0], ou) <= TOL and rel_err(ws[1][0], op) <= TOL
+
+
 def test_ensemble_per_domain_dt_and_self_periodic_boxes():
     insts = [W.bumpy_instance(W.Domain((n, n, n), 1.0 / n), 5000 + i)
              for i, n in enumerate((24, 32, 40, 24, 56, 48))]
