@@ -86,31 +86,47 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
 
 void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, int tx, int ty,
                       int tz, const std::vector<int>* cut_lo, const std::vector<int>* cut_hi) {
-  const int runs = (nz + tz - 1) / tz;
-  const int base = nz / runs, extra = nz % runs;
-  std::vector<int> at;
-  for (int r = 0, z0 = 0; r < runs; ++r) {
-    const int len = base + (r < extra ? 1 : 0);
+  // z-runs of at most tz planes, of balanced lengths, over [a, b)
+  auto runs_of = [tz](int a, int b, std::vector<std::pair<int, int>>& out) {
+    const int n = b - a, k = (n + tz - 1) / tz, base = n / k, extra = n % k;
+    for (int r = 0, z = a; r < k; ++r) {
+      const int len = base + (r < extra ? 1 : 0);
+      out.emplace_back(z, len);
+      z += len;
+    }
+  };
+  std::vector<std::pair<int, int>> reg, edge[4];
+  runs_of(0, nz, reg);
+  // a column of tiles at an x face whose ghosts are read from their owners
+  // splits [0, nz) where the owner changes first, then into runs: no run
+  // crosses an owner change, and none is much shorter than it must be
+  // (kind: 1 low face, 2 high face, 3 both)
+  for (int kind = 1; kind < 4; ++kind) {
+    std::vector<int> at{0, nz};
+    for (const std::vector<int>* c : {kind & 1 ? cut_lo : nullptr, kind & 2 ? cut_hi : nullptr})
+      if (c)
+        for (int z : *c)
+          if (z > 0 && z < nz) at.push_back(z);
+    std::sort(at.begin(), at.end());
+    at.erase(std::unique(at.begin(), at.end()), at.end());
+    for (size_t i = 0; i + 1 < at.size(); ++i) runs_of(at[i], at[i + 1], edge[kind]);
+  }
+  // run-major order: a column's runs that start inside regular run r go
+  // with run r
+  for (size_t r = 0; r < reg.size(); ++r) {
+    const int z0 = reg[r].first, z1 = z0 + reg[r].second;
     for (int y0 = 0; y0 < ny; y0 += ty)
       for (int x0 = 0; x0 < nx; x0 += tx) {
-        // a tile at an x face whose ghosts are read from their owners ends
-        // its z-run where the owner changes
-        at.clear();
-        for (const std::vector<int>* c : {x0 == 0 ? cut_lo : nullptr,
-                                          x0 + tx >= nx ? cut_hi : nullptr})
-          if (c)
-            for (int z : *c)
-              if (z > z0 && z < z0 + len) at.push_back(z);
-        std::sort(at.begin(), at.end());
-        at.erase(std::unique(at.begin(), at.end()), at.end());
-        int za = z0;
-        for (int z : at) {
-          items.push_back(DItem{b, x0, y0, za, z - za, tx / 2});
-          za = z;
+        const int kind = (x0 == 0 && cut_lo && !cut_lo->empty() ? 1 : 0) |
+                         (x0 + tx >= nx && cut_hi && !cut_hi->empty() ? 2 : 0);
+        if (!kind) {
+          items.push_back(DItem{b, x0, y0, z0, z1 - z0, tx / 2});
+          continue;
         }
-        items.push_back(DItem{b, x0, y0, za, z0 + len - za, tx / 2});
+        for (const auto& run : edge[kind])
+          if (run.first >= z0 && run.first < z1)
+            items.push_back(DItem{b, x0, y0, run.first, run.second, tx / 2});
       }
-    z0 += len;
   }
 }
 
