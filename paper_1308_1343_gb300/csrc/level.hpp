@@ -68,9 +68,16 @@ struct DeviceState {
   cudaStream_t capture = nullptr;
 
   dev::DBox* boxes = nullptr;
+  // work items of the batched launches, ordered by the place of their tile
+  // in its domain (domain, z, y, x of the tile's first point): the tiles
+  // that run at the same time are neighbours also across box faces, so the
+  // halos they read from other boxes are still in L2 (measured: 1 % on the
+  // pass kernels of the uneven 64-box level; one box: the box-major order)
   dev::DItem* items = nullptr;
   int nitems = 0;
-  std::vector<int> box_items;  // per-box item ranges [b], [b+1]
+  // the same items box by box, for the launches of one box (per-box mode)
+  dev::DItem* items_box = nullptr;
+  std::vector<int> box_items;  // per-box item ranges [b], [b+1] of items_box
   // items of the adjoint's pass kernels: tiles tuned for one-role kernels
   // (SizeClass::tile_one), or NULL to use `items`
   dev::DItem* items_one = nullptr;

@@ -2,6 +2,7 @@
 // step (per-box launches, batched launches, or a CUDA graph per step), the
 // end-to-end host entry point, the misfit, and the checkpointed adjoint.
 #include <algorithm>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -167,8 +168,18 @@ int upload_items(sc_level* L) {
   D->graphs.clear();
   L->version++;
   D->nitems = 0;
-  int rc = upload(&D->items, items);
+  int rc = upload(&D->items_box, items);
   if (rc) return rc;
+  {
+    std::vector<DItem> g = items;
+    auto key = [L](const DItem& it) {
+      const sc_box& B = L->boxes[it.box];
+      return std::make_tuple(B.domain, B.lo[2] + it.z0, B.lo[1] + it.y0, B.lo[0] + it.x0);
+    };
+    std::stable_sort(g.begin(), g.end(),
+                     [&](const DItem& a, const DItem& b) { return key(a) < key(b); });
+    if ((rc = upload(&D->items, g))) return rc;
+  }
   D->nitems = (int)items.size();
   // the adjoint's pass kernels: their own list where the tuner found other
   // tiles for one-role kernels
@@ -202,7 +213,7 @@ void release_device(sc_level* L) {
     cudaEventDestroy(pr.second);
   }
   for (auto& kv : D->fields) cudaFree(kv.second);
-  void* ptrs[] = {D->boxes, D->items, D->items_one, D->grects, D->gchunks, D->gchunks_nw,
+  void* ptrs[] = {D->boxes, D->items, D->items_box, D->items_one, D->grects, D->gchunks, D->gchunks_nw,
                   D->gchunks_nz, D->xg, D->xg_ofs,
                   D->irects, D->ichunks,
                   D->srects, D->schunks, D->pchunks, D->push, D->push_gofs, D->coef, D->acoef, D->inv12h2, D->qfac, D->h3, D->emax,
@@ -718,7 +729,7 @@ static cudaError_t enq_fwd(const Enq& q, dev::FwdArgs a, bool record) {
                                  D->grid_stage_s[q.L->staging], q.s);
   }
   for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
-    a.items = D->items + D->box_items[b];
+    a.items = D->items_box + D->box_items[b];
     a.nitems = D->box_items[b + 1] - D->box_items[b];
     (*q.count)++;
     TimedLaunch t(q, record ? SC_KERNEL_STAGE_RECORD : SC_KERNEL_STAGE);
@@ -823,7 +834,7 @@ static cudaError_t enq_pair(const Enq& q, dev::PairArgs a, bool second) {
     return launch_pass(q.L, second, a, q.s);
   }
   for (size_t b = 0; b + 1 < D->box_items.size(); ++b) {
-    a.items = D->items + D->box_items[b];
+    a.items = D->items_box + D->box_items[b];
     a.nitems = D->box_items[b + 1] - D->box_items[b];
     (*q.count)++;
     TimedLaunch t(q, kind);
