@@ -460,10 +460,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
   ws_init(sm);
   unsigned err = 0, g = 0;
   bool ok = true;
-  // registers: producers take 96 and consumers give back to 48 of the 80
-  // per thread the CTA was launched with
+  // registers: producers take 96 and consumers give back to what is left of
+  // the CTA's (48 of 80 per thread with 4 consumer warps)
   if (threadIdx.x < kWsProducers) {
-    ws_producer_regs<96, 48>();
+    ws_producer_regs<96>();
     const double* const F[2] = {a.s0, a.s1};
     const XgTab xt{a.xg, a.xg_ofs, a.boxes};
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) pair_ws_kernel(PairArgs a) {
       ok = ws_produce(it, bx, F, ar, sm, err, g, xt);
     }
   } else {
-    ws_consumer_regs<96, 48>();
+    ws_consumer_regs<96>();
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
       const DBox bx = a.boxes[it.box];
@@ -728,10 +728,11 @@ __global__ void __launch_bounds__(kWsThreads, 2) adj_ws_kernel(AdjWsArgs a) {
   ws_init(sm);
   unsigned err = 0, g = 0;
   bool ok = true;
-  // the first pass's consumers hold eight pointwise fields: 88 / 64 there
-  constexpr int kP = SECOND ? 96 : 88, kC = SECOND ? 48 : 64;
+  // the first pass's consumers hold eight pointwise fields: producers 88 there
+  // (consumers 64 with 4 consumer warps)
+  constexpr int kP = SECOND ? 96 : 88;
   if (threadIdx.x < kWsProducers) {
-    ws_producer_regs<kP, kC>();
+    ws_producer_regs<kP>();
     const double* const F[2] = {a.z0_in, a.z1_in};
     const XgTab xt{a.xg, a.xg_ofs, a.boxes};
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) adj_ws_kernel(AdjWsArgs a) {
       ok = ws_produce(it, bx, F, ar, sm, err, g, xt);
     }
   } else {
-    ws_consumer_regs<kP, kC>();
+    ws_consumer_regs<kP>();
     for (int i = blockIdx.x; i < a.nitems && ok; i += gridDim.x) {
       const DItem it = a.items[i];
       const DBox bx = a.boxes[it.box];
@@ -1257,7 +1258,7 @@ cudaError_t launch_pair(int arith, bool second, const PairArgs& a, int grid, cud
 template <class K>
 static bool ws_regs_ok(K kernel) {
   cudaFuncAttributes at{};
-  return cudaFuncGetAttributes(&at, kernel) == cudaSuccess && at.numRegs == 80 &&
+  return cudaFuncGetAttributes(&at, kernel) == cudaSuccess && at.numRegs == kWsLaunchRegs &&
          at.maxThreadsPerBlock >= kWsThreads;
 }
 static bool ws_kernels_ok() {

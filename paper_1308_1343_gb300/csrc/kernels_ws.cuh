@@ -118,18 +118,24 @@ struct WsSmem {
   int abort;
 };
 
-// Register budgets of the two roles (setmaxnreg): the CTA is launched with 80
-// per thread (two CTAs of 384 threads per SM), so 256 P + 128 C must equal
-// 384 * 80 = 30720 (checked at compile time).
-template <int P, int C>
+// Register budgets of the two roles (setmaxnreg): the CTA is launched with
+// kWsLaunchRegs per thread (two CTAs per SM: 80 for 384 threads), the
+// producers take P and the consumers give back to what is left of the CTA's
+// registers (P = 96: 48; P = 88: 64), rounded down to a multiple of 8.
+constexpr int kWsLaunchRegs = 65536 / (2 * kWsThreads) / 8 * 8;
+template <int P>
+struct WsBudget {
+  static constexpr int kConsumer =
+      (kWsThreads * kWsLaunchRegs - kWsProducers * P) / kWsConsumers / 8 * 8;
+  static_assert(kConsumer >= 24 && P <= 256, "register split");
+};
+template <int P>
 __device__ __forceinline__ void ws_producer_regs() {
-  static_assert(kWsProducers * P + kWsConsumers * C == kWsThreads * 80, "register split");
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(P) : "memory");
 }
-template <int P, int C>
+template <int P>
 __device__ __forceinline__ void ws_consumer_regs() {
-  static_assert(kWsProducers * P + kWsConsumers * C == kWsThreads * 80, "register split");
-  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(C) : "memory");
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(WsBudget<P>::kConsumer) : "memory");
 }
 
 // x-face ghost copies read from their owners (DXGhost): per box b, entries
