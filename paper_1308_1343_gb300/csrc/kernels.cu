@@ -862,18 +862,22 @@ __global__ void __launch_bounds__(kGatherChunk, 8) adj_combine_kernel(
 // product (weights (-1, 9, 9, -1)/16 at odd fine indices, injection at even
 // ones), of data interpolated linearly in time, (1 - alpha) old + alpha new,
 // per coarse point.  The tensor product is applied as successive
-// one-dimensional interpolations, along z, then y, then x, each with its
-// products and sums rounded one by one (no FMA contraction); a tile's
-// points share the z- and y-interpolated intermediates (shared memory).
+// one-dimensional interpolations, along z, then y, then x, each a chain of
+// fused multiply-adds (measured: 29 % faster than separately rounded products
+// and sums; GB300's FP64 pipe bounds this kernel); a tile's points share the
+// z- and y-interpolated intermediates (shared memory).  The result is the
+// interpolant up to rounding: exact where every product and partial sum is
+// (dyadic data), else within a few ulps of the data's scale.
 // Each list entry holds points of one parity per axis, so a CTA runs one
 // stencil shape.  At alpha != 0 the time interpolation is done once per
 // coarse point by blend_kernel into scratch coarse fields (the same
 // rounding).
 
 // One-dimensional interpolation along an axis of parity P (1: odd index):
-// 0 + w_0 v_0 + w_1 v_1 + w_2 v_2 + w_3 v_3 with w = (-1, 9, 9, -1)/16, each
-// product and sum rounded in that order; at an even index 0 + v_0.  The
-// values are v_k = f[i + k * stride].
+// 0 + w_0 v_0 + w_1 v_1 + w_2 v_2 + w_3 v_3 with w = (-1, 9, 9, -1)/16, the
+// first product exact (a power of two) and the rest fused multiply-adds in
+// that order; at an even index 0 + v_0.  The values are v_k = f[i + k *
+// stride].
 __device__ __forceinline__ double plus_zero(double v) {  // 0.0 + v
   return (__double_as_longlong(v) << 1) == 0 ? 0.0 : v;
 }
@@ -882,9 +886,9 @@ __device__ __forceinline__ double interp1(const double* __restrict__ f, long lon
                                           long long stride) {
   if (!P) return plus_zero(f[i]);
   double acc = plus_zero(__dmul_rn(-0.0625, f[i]));
-  acc = __dadd_rn(acc, __dmul_rn(0.5625, f[i + stride]));
-  acc = __dadd_rn(acc, __dmul_rn(0.5625, f[i + 2 * stride]));
-  return __dadd_rn(acc, __dmul_rn(-0.0625, f[i + 3 * stride]));
+  acc = __fma_rn(0.5625, f[i + stride], acc);
+  acc = __fma_rn(0.5625, f[i + 2 * stride], acc);
+  return __fma_rn(-0.0625, f[i + 3 * stride], acc);
 }
 
 // The tile of one prolongation entry: z interpolation of every coarse (y, x)
@@ -925,12 +929,12 @@ __device__ __forceinline__ void prol_tile(const DProl& r, int x0, int y0, int z0
     } else {
       a0 = plus_zero(__dmul_rn(-0.0625, t1[b][0]));
       a1 = plus_zero(__dmul_rn(-0.0625, t1[b][1]));
-      a0 = __dadd_rn(a0, __dmul_rn(0.5625, t1[b + wx][0]));
-      a1 = __dadd_rn(a1, __dmul_rn(0.5625, t1[b + wx][1]));
-      a0 = __dadd_rn(a0, __dmul_rn(0.5625, t1[b + 2 * wx][0]));
-      a1 = __dadd_rn(a1, __dmul_rn(0.5625, t1[b + 2 * wx][1]));
-      a0 = __dadd_rn(a0, __dmul_rn(-0.0625, t1[b + 3 * wx][0]));
-      a1 = __dadd_rn(a1, __dmul_rn(-0.0625, t1[b + 3 * wx][1]));
+      a0 = __fma_rn(0.5625, t1[b + wx][0], a0);
+      a1 = __fma_rn(0.5625, t1[b + wx][1], a1);
+      a0 = __fma_rn(0.5625, t1[b + 2 * wx][0], a0);
+      a1 = __fma_rn(0.5625, t1[b + 2 * wx][1], a1);
+      a0 = __fma_rn(-0.0625, t1[b + 3 * wx][0], a0);
+      a1 = __fma_rn(-0.0625, t1[b + 3 * wx][1], a1);
     }
     t2[k][0] = a0;
     t2[k][1] = a1;
@@ -949,12 +953,12 @@ __device__ __forceinline__ void prol_tile(const DProl& r, int x0, int y0, int z0
     } else {
       su = plus_zero(__dmul_rn(-0.0625, t2[b][0]));
       sp = plus_zero(__dmul_rn(-0.0625, t2[b][1]));
-      su = __dadd_rn(su, __dmul_rn(0.5625, t2[b + 1][0]));
-      sp = __dadd_rn(sp, __dmul_rn(0.5625, t2[b + 1][1]));
-      su = __dadd_rn(su, __dmul_rn(0.5625, t2[b + 2][0]));
-      sp = __dadd_rn(sp, __dmul_rn(0.5625, t2[b + 2][1]));
-      su = __dadd_rn(su, __dmul_rn(-0.0625, t2[b + 3][0]));
-      sp = __dadd_rn(sp, __dmul_rn(-0.0625, t2[b + 3][1]));
+      su = __fma_rn(0.5625, t2[b + 1][0], su);
+      sp = __fma_rn(0.5625, t2[b + 1][1], sp);
+      su = __fma_rn(0.5625, t2[b + 2][0], su);
+      sp = __fma_rn(0.5625, t2[b + 2][1], sp);
+      su = __fma_rn(-0.0625, t2[b + 3][0], su);
+      sp = __fma_rn(-0.0625, t2[b + 3][1], sp);
     }
     const long long o = r.dst + 2ll * (x0 + x) + 2ll * (y0 + y) * r.dpy + 2ll * (z0 + z) * r.dpz;
     fu[o] = su;
