@@ -103,6 +103,7 @@ struct Timer {
       append_box_items(items, (int)b, nx, ny, nz, tx, 2 * dev_threads() / tx, tz,
                        cut ? &cuts[2 * b] : nullptr, cut ? &cuts[2 * b + 1] : nullptr);
     }
+    order_items(L, items);  // as the level's batched launches run them
     if (items.size() > cap) {
       if (ditems) cudaFree(ditems);
       cap = items.size() * 2;
@@ -233,6 +234,8 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
   // the budget, so that each class starts its own search from it.
   size_t uncached = 0;
   int64_t nzmax = 1;
+  std::vector<sc_tile> shared;     // every class's tile after the shared phase
+  std::vector<char> refined_here;  // the class is tuned here (not from the cache)
   for (const auto& C : L->classes) {
     if (!cache.count(cache_key(L, C))) ++uncached;
     nzmax = std::max(nzmax, C.ext[2]);
@@ -281,6 +284,11 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
         C.tile.tile_z = (int)std::min<int64_t>(best.tz, C.ext[2]);
       }
     per_class *= 0.5;
+    shared.reserve(L->classes.size());
+    for (const auto& C : L->classes) {
+      shared.push_back(C.tile);
+      refined_here.push_back(!cache.count(cache_key(L, C)));
+    }
   }
   for (size_t ci = 0; ci < L->classes.size(); ++ci) {
     SizeClass& C = L->classes[ci];
@@ -361,6 +369,29 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
   // the whole level with every class at its tuned tile
   double t = T.time(-1, Cand{0, 0}, 1e30);
   if (t >= 1e30) return -1.0;
+  // With many classes each class holds a small share of the level's time, and
+  // one class's candidates differ by less than the timing noise of the whole
+  // level: the per-class refinement may end slower than the shared tile it
+  // started from (measured on the uneven 64-box level: 31.5-32.6 against
+  // 32.7 G updates/s).  Keep whichever of the two assignments is faster.
+  if (!shared.empty()) {
+    std::vector<sc_tile> refined;
+    for (const auto& C : L->classes) refined.push_back(C.tile);
+    for (size_t i = 0; i < L->classes.size(); ++i)
+      if (refined_here[i]) L->classes[i].tile = shared[i];
+    const double t0 = T.time(-1, Cand{0, 0}, 1e30);
+    if (t0 < t) {
+      t = t0;
+      for (size_t i = 0; i < L->classes.size(); ++i) {
+        const SizeClass& C = L->classes[i];
+        auto it = cache.find(cache_key(L, C));
+        if (refined_here[i] && it != cache.end())
+          it->second.first = Cand{C.tile.tile_x, C.tile.tile_z};
+      }
+    } else {
+      for (size_t i = 0; i < L->classes.size(); ++i) L->classes[i].tile = refined[i];
+    }
+  }
   // one stage per pass: the staging of the raw column and halo values too
   // (registers or cp.async), for the whole level with the tuned tiles
   if (L->fuse == 1 && !L->staging_fixed) {

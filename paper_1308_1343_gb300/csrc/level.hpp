@@ -27,6 +27,9 @@ int upload_items(sc_level* L);
 // Append the work items of box b (interior nx x ny x nz) for a tile of
 // tx x ty points and z-runs of at most tz planes, z-major: the z extent is
 // cut into ceil(nz / tz) runs whose lengths differ by at most one plane.
+// the order of the batched launches' item list: by the place of the tile in
+// its domain (domain, z, y, x of its first point)
+void order_items(const sc_level* L, std::vector<dev::DItem>& items);
 void append_box_items(std::vector<dev::DItem>& items, int b, int nx, int ny, int nz, int tx,
                       int ty, int tz, const std::vector<int>* cut_lo = nullptr,
                       const std::vector<int>* cut_hi = nullptr);

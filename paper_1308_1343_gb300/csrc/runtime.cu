@@ -131,6 +131,15 @@ void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, 
   }
 }
 
+void order_items(const sc_level* L, std::vector<DItem>& items) {
+  auto key = [L](const DItem& it) {
+    const sc_box& B = L->boxes[it.box];
+    return std::make_tuple(B.domain, B.lo[2] + it.z0, B.lo[1] + it.y0, B.lo[0] + it.x0);
+  };
+  std::stable_sort(items.begin(), items.end(),
+                   [&](const DItem& a, const DItem& b) { return key(a) < key(b); });
+}
+
 int upload_items(sc_level* L) {
   DeviceState* D = L->dev;
   for (int st = 0; st < 2; ++st) {
@@ -172,12 +181,7 @@ int upload_items(sc_level* L) {
   if (rc) return rc;
   {
     std::vector<DItem> g = items;
-    auto key = [L](const DItem& it) {
-      const sc_box& B = L->boxes[it.box];
-      return std::make_tuple(B.domain, B.lo[2] + it.z0, B.lo[1] + it.y0, B.lo[0] + it.x0);
-    };
-    std::stable_sort(g.begin(), g.end(),
-                     [&](const DItem& a, const DItem& b) { return key(a) < key(b); });
+    order_items(L, g);
     if ((rc = upload(&D->items, g))) return rc;
   }
   D->nitems = (int)items.size();
