@@ -236,6 +236,21 @@ int sc_level_arm_wait_test(sc_level* level);
 int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
                           int32_t* class_of_box /* nboxes entries or NULL */);
 
+/* The work items of the level's batched launches, in their launch order:
+ * out[6 i .. 6 i + 5] = box, x0, y0, z0 (the item's first point, interior
+ * coordinates of its box), number of planes of its z-run, tile_x (the tile
+ * is tile_x x 512 / tile_x points), for i < min(cap, n); *n receives the
+ * count (cap = 0 sizes the buffer).  Built on the host from the size
+ * classes' current tiles (after sc_level_autotune or sc_level_set_tuning,
+ * the tiles the next launch uses), so no device is needed.  Each box is cut
+ * into tiles and z-runs of at most tile_z planes; a column of tiles at an x
+ * face whose ghosts the warp-specialised passes read from the box that owns
+ * them splits its z extent first where that owner changes, so that no item
+ * reads such a ghost row from two boxes.  The order is by the place of the
+ * tile in its domain (domain, then z, y, x of its first point).  Errors:
+ * SC_EINVAL for NULL n, or NULL out with cap > 0. */
+int sc_level_work_items(const sc_level* level, int32_t* out, int64_t cap, int64_t* n);
+
 /* Run-time tuning of the batched stencil kernels (GPU counterpart of the
  * paper's random-restart hill climbing, Sec. 3.2): for every size class,
  * times candidate tiles on scratch fields of this level (in the launch of

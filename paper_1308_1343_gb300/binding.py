@@ -61,6 +61,7 @@ _SIGS = {
     "sc_level_box_layout": (_i32, [_vp, _i32, _p64, _p64, _p64]),
     "sc_level_num_boxes": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "sc_level_exchange_list": (_i32, [_vp, ctypes.POINTER(ScCopy), _i64, _p64]),
+    "sc_level_work_items": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32), _i64, _p64]),
     "sc_level_set_arith": (_i32, [_vp, _i32]),
     "sc_level_set_tuning": (_i32, [_vp, _i32, ctypes.POINTER(ScTile), _i32]),
     "sc_level_size_classes": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),

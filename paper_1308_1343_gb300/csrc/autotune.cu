@@ -98,7 +98,7 @@ struct Timer {
       const bool mine = cls == kAll || L->box_class[b] == cls;
       const int tx = mine ? c.tx : L->classes[L->box_class[b]].tile.tile_x;
       const int tz = mine ? c.tz : L->classes[L->box_class[b]].tile.tile_z;
-      const auto& cuts = L->dev->xg_cuts;
+      const auto& cuts = L->xcuts;
       const bool cut = cuts.size() == 2 * L->boxes.size();
       append_box_items(items, (int)b, nx, ny, nz, tx, 2 * dev_threads() / tx, tz,
                        cut ? &cuts[2 * b] : nullptr, cut ? &cuts[2 * b + 1] : nullptr);

@@ -24,6 +24,13 @@ int get_field(sc_level* L, const std::string& name, double** p);
 int set_coef(sc_level* L, const double* dt, int ndt, cudaStream_t s);
 int scratch4(sc_level* L, double* W[6]);
 int upload_items(sc_level* L);
+// DBox::wrap of box b: bit 0 the box alone tiles a domain periodic on every
+// axis (x extent even, x and y extents >= 2), bit 1 also z extent >= 2
+int wrap_bits(const sc_level* L, int b);
+// Host plan of the x-face ghost copies that the warp-specialised producers
+// read from the boxes that own them (sc_level::xread, xfaces, xcuts); called
+// when the level's layout and exchange list are built
+void plan_xface_reads(sc_level* L);
 // Append the work items of box b (interior nx x ny x nz) for a tile of
 // tx x ty points and z-runs of at most tz planes, z-major: the z extent is
 // cut into ceil(nz / tz) runs whose lengths differ by at most one plane.
@@ -102,15 +109,9 @@ struct DeviceState {
   dev::DChunk* gchunks_nz = nullptr;
   int ngchunks_nz = 0;
   // x-face ghost copies that the warp-specialised kernels read from their
-  // owners (dev::DXGhost; not in gchunks_nz), per box and side; and, per box
-  // and side, the planes where their z ranges start or end inside the box:
-  // work items at that x face end their z-run there, so that each thread of
-  // an item reads its ghosts from one source box (measured: 4 % on the pass
-  // kernels of the uneven level, where a switch of source inside the plane
-  // loop cost 5 % there and 2 % on levels without such ghosts)
+  // owners (sc_level::xfaces, uploaded; not in gchunks_nz), per box and side
   dev::DXGhost* xg = nullptr;
   int* xg_ofs = nullptr;  // [2 nboxes + 1], NULL if there are none
-  std::vector<std::vector<int>> xg_cuts;  // [2 nboxes]
   std::vector<char> box_wrap;
   // interior rectangles (one per box) + chunks
   dev::DRect* irects = nullptr;
@@ -174,6 +175,18 @@ struct sc_level {
   std::vector<int64_t> off, py, pz, storage;
   int64_t field_size = 0;
   std::vector<sc_copy> copies;
+  // x-face ghost copies that the warp-specialised producers read from the
+  // boxes that own them instead of having them gathered (plan_xface_reads):
+  // per copy whether it is one; per box and side (2 b + side) those copies
+  // as the kernels look them up; and per box and side the planes where their
+  // z ranges start or end inside the box: work items at that x face end
+  // their z-run there, so that each thread of an item reads its ghosts from
+  // one box (measured: 1.6 % on the uneven level's pass kernels, where a
+  // switch of source inside the plane loop cost 5 % there and 2 % on levels
+  // without such ghosts)
+  std::vector<char> xread;
+  std::vector<std::vector<sc::dev::DXGhost>> xfaces;
+  std::vector<std::vector<int>> xcuts;
   std::vector<int> box_class;
   std::vector<sc::SizeClass> classes;
   int arith = SC_ARITH_FIXED;

@@ -210,6 +210,7 @@ static int build_level(sc_level* L) {
     return set_error(SC_EINVAL, "level too large: a field must hold fewer than 2^31 doubles");
   build_exchange(L);
   build_classes(L);
+  sc::plan_xface_reads(L);
   return SC_OK;
 }
 

@@ -74,7 +74,7 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
     const sc_box& B = L->boxes[b];
     const SizeClass& C = L->classes[L->box_class[b]];
     const sc_tile& t = one_role && C.has_one ? C.tile_one : C.tile;
-    const auto& cuts = L->dev->xg_cuts;
+    const auto& cuts = L->xcuts;
     const bool cut = cuts.size() == 2 * L->boxes.size();
     append_box_items(items, (int)b, (int)(B.hi[0] - B.lo[0]), (int)(B.hi[1] - B.lo[1]),
                      (int)(B.hi[2] - B.lo[2]), t.tile_x, t.tile_y, t.tile_z,
@@ -84,6 +84,65 @@ void build_items(const sc_level* L, std::vector<DItem>& items, std::vector<int>&
 }
 
 }  // namespace
+
+int wrap_bits(const sc_level* L, int b) {
+  // self-periodic: the box is its domain, periodic on every axis; the
+  // kernels then read the owners of its x and y ghosts by wrapping the
+  // coordinates (pairs of x-points stay 16-byte aligned for an even x
+  // extent), the warp-specialised ones those of its z ghosts too (two
+  // planes or more); the one-role kernels have its z ghosts gathered
+  const sc_box& B = L->boxes[b];
+  const sc_domain& Dm = L->doms[B.domain];
+  bool self = Dm.periodic == 7u;
+  for (int d = 0; d < 3; ++d) self = self && B.lo[d] == Dm.lo[d] && B.hi[d] == Dm.hi[d];
+  self = self && B.hi[0] - B.lo[0] >= 2 && B.hi[1] - B.lo[1] >= 2 &&
+         (B.hi[0] - B.lo[0]) % 2 == 0;
+  if (!self) return 0;
+  return 1 | (B.hi[2] - B.lo[2] >= 2 ? 2 : 0);
+}
+
+void plan_xface_reads(sc_level* L) {
+  const int nb = (int)L->boxes.size();
+  L->xread.assign(L->copies.size(), 0);
+  L->xfaces.assign((size_t)2 * nb, {});
+  L->xcuts.assign((size_t)2 * nb, {});
+  auto index_of = [&](int b, const int64_t p[3]) {
+    const sc_box& B = L->boxes[b];
+    return L->off[b] + (p[0] - B.lo[0]) + (p[1] - B.lo[1]) * L->py[b] +
+           (p[2] - B.lo[2]) * L->pz[b];
+  };
+  for (size_t c = 0; c < L->copies.size(); ++c) {
+    const sc_copy& C = L->copies[c];
+    const int b = C.dst_box;
+    const sc_box& Bd = L->boxes[b];
+    // a copy into the x-face ghost pair of a box of even x extent (not
+    // self-periodic), 16-byte pairs at both ends, rows and planes inside
+    // the box (x-face rows are the costly part of a gather: 16 bytes, half
+    // of a 32-byte sector at both ends)
+    const int side = C.dst_lo[0] == Bd.lo[0] - 2 ? 0 : (C.dst_lo[0] == Bd.hi[0] ? 1 : -1);
+    const int64_t src = index_of(C.src_box, C.src_lo), dst = index_of(b, C.dst_lo);
+    const bool xr = side >= 0 && C.ext[0] == 2 && src % 2 == 0 && dst % 2 == 0 &&
+                    !wrap_bits(L, b) && (Bd.hi[0] - Bd.lo[0]) % 2 == 0 &&
+                    C.dst_lo[1] >= Bd.lo[1] && C.dst_lo[1] + C.ext[1] <= Bd.hi[1] &&
+                    C.dst_lo[2] >= Bd.lo[2] && C.dst_lo[2] + C.ext[2] <= Bd.hi[2];
+    if (!xr) continue;
+    L->xread[c] = 1;
+    const int y0 = (int)(C.dst_lo[1] - Bd.lo[1]), z0 = (int)(C.dst_lo[2] - Bd.lo[2]);
+    L->xfaces[(size_t)2 * b + side].push_back(
+        dev::DXGhost{y0, y0 + (int)C.ext[1], z0, z0 + (int)C.ext[2], (int)src,
+                     (int)L->py[C.src_box], (int)L->pz[C.src_box], C.src_box});
+  }
+  for (int g = 0; g < 2 * nb; ++g) {
+    const int nz = (int)(L->boxes[g / 2].hi[2] - L->boxes[g / 2].lo[2]);
+    auto& cuts = L->xcuts[g];
+    for (const dev::DXGhost& e : L->xfaces[g])
+      for (int z : {e.z0, e.z1})
+        if (z > 0 && z < nz) cuts.push_back(z);
+    std::sort(cuts.begin(), cuts.end());
+    cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+  }
+}
+
 
 void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, int tx, int ty,
                       int tz, const std::vector<int>* cut_lo, const std::vector<int>* cut_hi) {
@@ -322,18 +381,7 @@ static int init_device(sc_level* L, int cur) {
   D->box_wrap.assign(nb, 0);
   for (int b = 0; b < nb; ++b) {
     const sc_box& B = L->boxes[b];
-    const sc_domain& Dm = L->doms[B.domain];
-    // self-periodic: the box is its domain, periodic on every axis; the
-    // kernels then read the owners of its x and y ghosts by wrapping the
-    // coordinates (pairs of x-points stay 16-byte aligned for an even x
-    // extent), the warp-specialised ones those of its z ghosts too (two
-    // planes or more); the one-role kernels have its z ghosts gathered
-    bool self = Dm.periodic == 7u;
-    for (int d = 0; d < 3; ++d) self = self && B.lo[d] == Dm.lo[d] && B.hi[d] == Dm.hi[d];
-    self = self && B.hi[0] - B.lo[0] >= 2 && B.hi[1] - B.lo[1] >= 2 &&
-           (B.hi[0] - B.lo[0]) % 2 == 0;
-    const int zw = self && B.hi[2] - B.lo[2] >= 2 ? 2 : 0;
-    D->box_wrap[b] = self ? 1 | zw : 0;
+    D->box_wrap[b] = (char)wrap_bits(L, b);
     boxes[b] = DBox{L->off[b], L->py[b], L->pz[b], (int)(B.hi[0] - B.lo[0]),
                     (int)(B.hi[1] - B.lo[1]), (int)(B.hi[2] - B.lo[2]), B.domain,
                     D->box_wrap[b]};
@@ -351,7 +399,6 @@ static int init_device(sc_level* L, int cur) {
   std::vector<DChunk> gchunks;
   std::vector<char> zface;  // per rect: it fills z ghosts of its box
   std::vector<char> xread;  // per rect: the warp-specialised kernels read it from its owner
-  std::vector<std::vector<DXGhost>> xgl((size_t)2 * nb);
   D->box_gchunks.assign(nb + 1, 0);
   {
     size_t c = 0;
@@ -375,25 +422,7 @@ static int init_device(sc_level* L, int cur) {
         r.pairs = (C.ext[0] % 2 == 0 && r.src % 2 == 0 && r.dst % 2 == 0) ? 1 : 0;
         grects.push_back(r);
         zface.push_back(C.dst_lo[2] < L->boxes[b].lo[2] || C.dst_lo[2] >= L->boxes[b].hi[2]);
-        // a copy into the x-face ghost pair of a box of even x extent (not
-        // self-periodic), 16-byte pairs at both ends, rows and planes inside
-        // the box: the producers of the warp-specialised kernels read it from
-        // the source box (x-face rows are the costly part of a gather)
-        {
-          const sc_box& Bd = L->boxes[b];
-          const int side = C.dst_lo[0] == Bd.lo[0] - 2 ? 0 : (C.dst_lo[0] == Bd.hi[0] ? 1 : -1);
-          const bool xr = side >= 0 && C.ext[0] == 2 && r.pairs && !D->box_wrap[b] &&
-                          (Bd.hi[0] - Bd.lo[0]) % 2 == 0 && C.dst_lo[1] >= Bd.lo[1] &&
-                          C.dst_lo[1] + C.ext[1] <= Bd.hi[1] && C.dst_lo[2] >= Bd.lo[2] &&
-                          C.dst_lo[2] + C.ext[2] <= Bd.hi[2];
-          xread.push_back(xr);
-          if (xr) {
-            const int y0 = (int)(C.dst_lo[1] - Bd.lo[1]), z0 = (int)(C.dst_lo[2] - Bd.lo[2]);
-            xgl[(size_t)2 * b + side].push_back(DXGhost{y0, y0 + (int)C.ext[1], z0,
-                                                        z0 + (int)C.ext[2], (int)r.src,
-                                                        (int)r.spy, (int)r.spz, C.src_box});
-          }
-        }
+        xread.push_back(L->xread[c]);
         add_chunks((int)grects.size() - 1, (C.ext[0] >> r.pairs) * C.ext[1] * C.ext[2],
                    gchunks, dev::kGatherChunk);
       }
@@ -429,21 +458,11 @@ static int init_device(sc_level* L, int cur) {
       }
     D->ngchunks_nz = (int)nzl.size();
     if (!nzl.empty() && (rc = upload(&D->gchunks_nz, nzl))) return rc;
-    // the x-face copies read from their owners, per box and side, and the
-    // planes where their z ranges start or end inside the box
+    // the x-face copies read from their owners, per box and side
     std::vector<DXGhost> xe;
     std::vector<int> xo(1, 0);
-    D->xg_cuts.assign((size_t)2 * nb, {});
     for (int g = 0; g < 2 * nb; ++g) {
-      const int nz = (int)(L->boxes[g / 2].hi[2] - L->boxes[g / 2].lo[2]);
-      for (const DXGhost& e : xgl[g]) {
-        xe.push_back(e);
-        for (int z : {e.z0, e.z1})
-          if (z > 0 && z < nz) D->xg_cuts[g].push_back(z);
-      }
-      std::sort(D->xg_cuts[g].begin(), D->xg_cuts[g].end());
-      D->xg_cuts[g].erase(std::unique(D->xg_cuts[g].begin(), D->xg_cuts[g].end()),
-                          D->xg_cuts[g].end());
+      xe.insert(xe.end(), L->xfaces[g].begin(), L->xfaces[g].end());
       xo.push_back((int)xe.size());
     }
     // the kernels read a source column over an item's planes and two more on
@@ -1021,6 +1040,23 @@ int level_steps(sc_level* L, double* u, double* pi, const double* c2, double dt,
 using namespace sc;
 
 extern "C" {
+
+int sc_level_work_items(const sc_level* L, int32_t* out, int64_t cap, int64_t* n) {
+  if (!L || !n) return set_error(SC_EINVAL, "NULL argument");
+  if (cap > 0 && !out) return set_error(SC_EINVAL, "out is NULL");
+  std::vector<DItem> items;
+  std::vector<int> box_items;
+  build_items(L, items, box_items);
+  order_items(L, items);
+  *n = (int64_t)items.size();
+  const int64_t m = std::min<int64_t>(cap, *n);
+  for (int64_t i = 0; i < m; ++i) {
+    const DItem& it = items[(size_t)i];
+    const int32_t row[6] = {it.box, it.x0, it.y0, it.z0, it.nzr, 2 * it.txh};
+    std::memcpy(out + 6 * i, row, sizeof(row));
+  }
+  return SC_OK;
+}
 
 int sc_level_fill_ghosts(sc_level* L, double* field, void* stream) {
   if (!L) return set_error(SC_EINVAL, "NULL level");

@@ -216,6 +216,18 @@ class Level:
             rows[i] = [c.src_box, c.dst_box, *c.src_lo, *c.dst_lo, *c.ext]
         return rows
 
+    def work_items(self) -> np.ndarray:
+        """(n, 6) int32 rows of the batched launches' work items in launch
+        order: box, x0, y0, z0, planes of the z-run, tile_x."""
+        lib = B.lib()
+        n = ctypes.c_int64()
+        B.check(lib.sc_level_work_items(self._h, None, 0, ctypes.byref(n)))
+        arr = np.zeros((max(n.value, 1), 6), dtype=np.int32)
+        B.check(lib.sc_level_work_items(
+            self._h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
+            ctypes.byref(n)))
+        return arr[:n.value]
+
     def size_classes(self):
         lib = B.lib()
         n = ctypes.c_int32()

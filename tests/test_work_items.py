@@ -1,0 +1,153 @@
+"""Host logic of the work items (sc_level_work_items, no GPU): the items of
+the batched launches tile every box exactly once; a column of tiles at an x
+face whose ghosts the warp-specialised passes read from the box that owns
+them never runs a z-run across a change of that owner (the copies are
+re-derived here from the exchange list and the layout); z-runs keep at most
+tile_z planes; the order is the place of the tile in its domain."""
+import numpy as np
+import pytest
+
+from paper_1308_1343_gb300 import workloads as W
+
+
+def _level(inst):
+    from paper_1308_1343_gb300.level import Level
+    return Level.from_instances([inst])
+
+
+def _owner_change():
+    dom = W.Domain((64, 24, 40), 1.0 / 24)
+    inst = W.bumpy_instance(dom, 11)
+    inst.boxes = [((0, 0, 0), (26, 24, 40)), ((26, 0, 0), (64, 10, 40)),
+                  ((26, 10, 0), (64, 24, 17)), ((26, 10, 17), (64, 24, 40))]
+    return inst
+
+
+def _owner_reads(lev):
+    """(box, side) -> list of (y0, y1, z0, z1) of the x-face copies that are
+    read from their owners: two ghost columns of an even-wide box that does
+    not tile its domain alone, both ends 16-byte aligned, rows and planes
+    inside the box."""
+    out = {}
+    boxes = lev.boxes
+    for c in lev.exchange_list():
+        sb, db = int(c[0]), int(c[1])
+        slo, dlo, ext = c[2:5], c[5:8], c[8:11]
+        lo, hi, _ = boxes[db]
+        side = 0 if dlo[0] == lo[0] - 2 else (1 if dlo[0] == hi[0] else -1)
+        if side < 0 or ext[0] != 2 or (hi[0] - lo[0]) % 2:
+            continue
+        dom = lev.domains[boxes[db][2]]
+        alone = sum(1 for b in boxes if b[2] == boxes[db][2]) == 1
+        if alone and dom.get("periodic", 7) == 7:
+            continue  # a box alone in its periodic domain wraps its ghosts
+        soff, _, (_, spy, spz) = lev.layout[sb]
+        doff, _, (_, dpy, dpz) = lev.layout[db]
+        slo_b = boxes[sb][0]
+        src = soff + (slo[0] - slo_b[0]) + (slo[1] - slo_b[1]) * spy + (slo[2] - slo_b[2]) * spz
+        dst = doff + (dlo[0] - lo[0]) + (dlo[1] - lo[1]) * dpy + (dlo[2] - lo[2]) * dpz
+        if src % 2 or dst % 2:
+            continue
+        if not (lo[1] <= dlo[1] and dlo[1] + ext[1] <= hi[1] and
+                lo[2] <= dlo[2] and dlo[2] + ext[2] <= hi[2]):
+            continue
+        out.setdefault((db, side), []).append(
+            (dlo[1] - lo[1], dlo[1] - lo[1] + ext[1], dlo[2] - lo[2], dlo[2] - lo[2] + ext[2]))
+    return out
+
+
+def _check(lev, tiles):
+    items = lev.work_items()
+    assert items.dtype == np.int32 and items.shape[1] == 6
+    boxes = lev.boxes
+    ncls, cls_of = lev.size_classes()
+    reads = _owner_reads(lev)
+    seen = {}
+    for box, x0, y0, z0, nz_run, tx in items.tolist():
+        lo, hi, _ = boxes[box]
+        n = [hi[d] - lo[d] for d in range(3)]
+        t = lev.get_tuning(cls_of[box])
+        assert tx == t[0] and x0 % tx == 0 and y0 % t[1] == 0
+        assert 0 <= x0 < n[0] and 0 <= y0 < n[1] and 0 <= z0 and z0 + nz_run <= n[2]
+        assert 1 <= nz_run <= t[2]
+        for z in range(z0, z0 + nz_run):
+            key = (box, x0, y0, z)
+            assert key not in seen, key
+            seen[key] = True
+        # no owner change of a read x-face row inside the run
+        for side, at_face in ((0, x0 == 0), (1, x0 + tx >= n[0])):
+            if not at_face:
+                continue
+            for (ya, yb, za, zb) in reads.get((box, side), []):
+                for zc in (za, zb):
+                    assert not (z0 < zc < z0 + nz_run), (box, side, z0, nz_run, zc)
+    # every (box, tile column, plane) exactly once
+    for b, (lo, hi, _) in enumerate(boxes):
+        n = [hi[d] - lo[d] for d in range(3)]
+        tx, ty, _ = lev.get_tuning(cls_of[b])
+        for x0 in range(0, n[0], tx):
+            for y0 in range(0, n[1], ty):
+                for z in range(n[2]):
+                    assert (b, x0, y0, z) in seen, (b, x0, y0, z)
+    assert len(seen) == sum(((hi[0] - lo[0] + lev.get_tuning(cls_of[b])[0] - 1)
+                             // lev.get_tuning(cls_of[b])[0]) *
+                            ((hi[1] - lo[1] + lev.get_tuning(cls_of[b])[1] - 1)
+                             // lev.get_tuning(cls_of[b])[1]) * (hi[2] - lo[2])
+                            for b, (lo, hi, _) in enumerate(boxes))
+    # launch order: domain, then z, y, x of the tile's first point
+    keys = []
+    for box, x0, y0, z0, _, _ in items.tolist():
+        lo, _, d = boxes[box]
+        keys.append((d, lo[2] + z0, lo[1] + y0, lo[0] + x0))
+    assert keys == sorted(keys)
+    return items, reads
+
+
+@pytest.mark.parametrize("tiles", [None, (16, 40), (32, 8), (64, 13), (32, 5)])
+def test_owner_change_level(tiles):
+    inst = _owner_change()
+    lev = _level(inst)
+    if tiles:
+        for c in range(lev.size_classes()[0]):
+            lev.set_tuning(c, *tiles)
+    items, reads = _check(lev, tiles)
+    # box 0's faces are read from boxes 1-3, whose owner changes at z = 17:
+    # its edge columns have a run boundary there
+    assert reads.get((0, 1)) and any(z0 == 17 for b, x0, _, z0, _, _ in items.tolist()
+                                     if b == 0)
+
+
+@pytest.mark.parametrize("tiles", [None, (32, 32), (16, 64)])
+def test_uneven_levels(tiles):
+    for inst in (W.uneven_level(n=(64, 48, 40), h=1.0 / 48, levels=4, seed=6, box_seed=31),
+                 W.uneven_level()):
+        lev = _level(inst)
+        if tiles:
+            for c in range(lev.size_classes()[0]):
+                lev.set_tuning(c, *tiles)
+        _, reads = _check(lev, tiles)
+        assert reads  # the level has x faces read from their owners
+
+
+def test_single_box_and_ensemble():
+    lev = _level(W.single_box(64, 2))
+    items, reads = _check(lev, None)
+    assert not reads
+    insts = [W.bumpy_instance(W.Domain((n, n, n), 1.0 / n), 5000 + i)
+             for i, n in enumerate((24, 40, 32))]
+    from paper_1308_1343_gb300.level import Level
+    lev = Level.from_instances(insts)
+    items, reads = _check(lev, None)
+    assert not reads
+    assert sorted(set(items[:, 0].tolist())) == [0, 1, 2]
+
+
+def test_work_items_errors():
+    import ctypes
+    from paper_1308_1343_gb300 import binding as B
+    lev = _level(_owner_change())
+    n = ctypes.c_int64()
+    with pytest.raises(B.ScError):
+        B.check(B.lib().sc_level_work_items(lev._h, None, 4, ctypes.byref(n)))
+    with pytest.raises(B.ScError):
+        B.check(B.lib().sc_level_work_items(lev._h, None, 0, None))
