@@ -38,7 +38,7 @@ def _owner_reads(lev):
         if side < 0 or ext[0] != 2 or (hi[0] - lo[0]) % 2:
             continue
         dom = lev.domains[boxes[db][2]]
-        alone = sum(1 for b in boxes if b[2] == boxes[db][2]) == 1
+        alone = tuple(lo) == tuple(dom["lo"]) and tuple(hi) == tuple(dom["hi"])
         if alone and dom.get("periodic", 7) == 7:
             continue  # a box alone in its periodic domain wraps its ghosts
         soff, _, (_, spy, spz) = lev.layout[sb]
@@ -127,6 +127,26 @@ def test_uneven_levels(tiles):
                 lev.set_tuning(c, *tiles)
         _, reads = _check(lev, tiles)
         assert reads  # the level has x faces read from their owners
+
+
+@pytest.mark.parametrize("nranks,method", [(2, 1), (3, 0)])
+def test_distributed_ranks(nranks, method):
+    """Every rank's part of a distributed uneven level: its own items and
+    its own x-face reads (copies from boxes of other ranks arrive through
+    the exchange and are not among them)."""
+    from paper_1308_1343_gb300.dist import DistLevel, partition
+    inst = W.uneven_level(n=(64, 48, 40), h=1.0 / 48, levels=4, seed=6, box_seed=31)
+    boxes = [(lo, hi, 0) for lo, hi in inst.boxes]
+    doms = [dict(hi=inst.dom.n, h=inst.dom.h, periodic=7)]
+    owner = partition(boxes, nranks, method)
+    total = 0
+    for r in range(nranks):
+        lev = DistLevel(boxes, doms, nranks, r, owner)
+        for c in range(lev.size_classes()[0]):
+            lev.set_tuning(c, 32, 8)
+        items, _ = _check(lev, (32, 8))
+        total += len(items)
+    assert total > 0
 
 
 def test_single_box_and_ensemble():
