@@ -297,9 +297,10 @@ int sc_level_apply_laplacian(sc_level* level, const double* u, double* out,
  * kernels read the periodic images of its interior for its x and y ghosts,
  * which are not written, and only its z ghosts are gathered; the
  * warp-specialised two-stage passes (SC_PASS_WARP_SPECIALISED) read its z
- * ghosts the same way when its z extent is >= 2, and gather nothing for it
- * (in SC_MODE_PER_BOX every ghost is gathered).  sc_level_fill_ghosts always
- * fills every ghost.
+ * ghosts the same way when its z extent is >= 2, and gather nothing for it.
+ * SC_MODE_PER_BOX gathers the same ghosts as the other modes, one launch per
+ * box; with the one-role pass kernels (SC_PASS_ONE_ROLE) it gathers every
+ * ghost.  sc_level_fill_ghosts always fills every ghost.
  * mode is one of SC_MODE_*.  Scratch stage arrays are allocated on the first
  * call.
  * A level with a domain that is not periodic on every axis takes ONE step

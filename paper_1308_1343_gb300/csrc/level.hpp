@@ -108,6 +108,7 @@ struct DeviceState {
   // periodic images
   dev::DChunk* gchunks_nz = nullptr;
   int ngchunks_nz = 0;
+  std::vector<int> box_gchunks_nz;  // per-box ranges [b], [b+1] of gchunks_nz
   // x-face ghost copies that the warp-specialised kernels read from their
   // owners (sc_level::xfaces, uploaded; not in gchunks_nz), per box and side
   dev::DXGhost* xg = nullptr;

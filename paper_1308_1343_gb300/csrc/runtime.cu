@@ -450,12 +450,16 @@ static int init_device(sc_level* L, int cur) {
     // ordinary box, none of a self-periodic one (but the z ghosts of one of
     // a single plane)
     std::vector<DChunk> nzl;
-    for (int b = 0; b < nb; ++b)
+    D->box_gchunks_nz.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+      D->box_gchunks_nz[b] = (int)nzl.size();
       for (int c = D->box_gchunks[b]; c < D->box_gchunks[b + 1]; ++c) {
         const int rr = gchunks[c].rect;
         if ((!D->box_wrap[b] && !xread[rr]) || (zface[rr] && !(D->box_wrap[b] & 2)))
           nzl.push_back(gchunks[c]);
       }
+    }
+    D->box_gchunks_nz[nb] = (int)nzl.size();
     D->ngchunks_nz = (int)nzl.size();
     if (!nzl.empty() && (rc = upload(&D->gchunks_nz, nzl))) return rc;
     // the x-face copies read from their owners, per box and side
@@ -831,12 +835,17 @@ static cudaError_t enq_fill2(const Enq& q, double* f, double* g, unsigned* clear
       cleared = true;
     }
   } else {
-    for (size_t b = 0; b + 1 < D->box_gchunks.size(); ++b) {
-      const int n = D->box_gchunks[b + 1] - D->box_gchunks[b];
-      if (n <= 0) continue;  // per box: every ghost (simplest; not the fast path)
+    // one launch per box: the box's part of the same list (every ghost of
+    // the box where the one-role kernels follow or every ghost is wanted)
+    const bool ws = q.L->pass_ws && !q.all_ghosts;
+    const std::vector<int>& off = ws ? D->box_gchunks_nz : D->box_gchunks;
+    const DChunk* list = ws ? D->gchunks_nz : D->gchunks;
+    for (size_t b = 0; b + 1 < off.size(); ++b) {
+      const int n = off[b + 1] - off[b];
+      if (n <= 0) continue;
       (*q.count)++;
       TimedLaunch t(q, SC_KERNEL_GATHER);
-      cudaError_t e = dev::launch_gather2(D->grects, D->gchunks + D->box_gchunks[b], n, f, g,
+      cudaError_t e = dev::launch_gather2(D->grects, list + off[b], n, f, g,
                                           cleared ? nullptr : clear, nclear, q.s);
       if (e != cudaSuccess) return e;
       cleared = true;
