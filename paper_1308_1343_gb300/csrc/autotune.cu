@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <fstream>
+#include <functional>
 #include <map>
 #include <random>
 #include <sstream>
@@ -39,6 +40,26 @@ std::string cache_key(const sc_level* L, const SizeClass& c) {
   k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|f" << L->fuse
     << (L->fuse == 2 && L->pass_ws ? "w" : "") << "|" << c.ext[0] << "," << c.ext[1] << ","
     << c.ext[2];
+  return k.str();
+}
+
+// The whole level in one form (two stages per pass with the warp-specialised
+// or the one-role kernels, or one stage with either staging): its boxes and
+// domains hashed, so that a level's whole-level timings are found again only
+// for the same level.
+std::string level_key(const sc_level* L) {
+  std::ostringstream d;
+  for (const auto& B : L->boxes)
+    d << B.lo[0] << "," << B.lo[1] << "," << B.lo[2] << ":" << B.hi[0] << "," << B.hi[1] << ","
+      << B.hi[2] << "@" << B.domain << ";";
+  for (const auto& D : L->doms) d << D.h << "/" << D.periodic << ";";
+  std::ostringstream k;
+  k << L->dev->gpu_name << "|" << L->dev->sms << "|" << L->arith << "|level"
+    << std::hex << std::hash<std::string>{}(d.str()) << "|f" << std::dec << L->fuse;
+  if (L->fuse == 2)
+    k << (L->pass_ws ? "w" : "o");
+  else
+    k << "s" << L->staging;
   return k.str();
 }
 
@@ -366,8 +387,22 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
     C.fixed = true;
     cache[key] = {best, tbest};
   }
-  // the whole level with every class at its tuned tile
-  double t = T.time(-1, Cand{0, 0}, 1e30);
+  // the whole level with every class at its tuned tile.  When every class's
+  // tile came from the cache, the whole level's time in this form is taken
+  // from the cache too, so that a warm cache reproduces the choice between
+  // forms without timing again (a timing taken under a profiler, with its
+  // per-launch overhead, could otherwise flip it)
+  const bool all_cached = uncached == 0;
+  auto level_time = [&]() {
+    const std::string key = level_key(L);
+    auto it = cache.find(key);
+    if (all_cached && it != cache.end()) return it->second.second;
+    const double tl = T.time(-1, Cand{0, 0}, 1e30);
+    if (tl < 1e30)
+      cache[key] = {Cand{L->classes[0].tile.tile_x, L->classes[0].tile.tile_z}, tl};
+    return tl;
+  };
+  double t = level_time();
   if (t >= 1e30) return -1.0;
   // With many classes each class holds a small share of the level's time, and
   // one class's candidates differ by less than the timing noise of the whole
@@ -382,6 +417,7 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
     const double t0 = T.time(-1, Cand{0, 0}, 1e30);
     if (t0 < t) {
       t = t0;
+      cache[level_key(L)].second = t0;
       for (size_t i = 0; i < L->classes.size(); ++i) {
         const SizeClass& C = L->classes[i];
         auto it = cache.find(cache_key(L, C));
@@ -397,7 +433,7 @@ double tune_form(sc_level* L, Timer& T, std::map<std::string, std::pair<Cand, do
   if (L->fuse == 1 && !L->staging_fixed) {
     const int s0 = L->staging;
     L->staging = 1 - s0;
-    const double t1 = T.time(-1, Cand{0, 0}, 1e30);
+    const double t1 = level_time();
     if (t1 < t)
       t = t1;
     else

@@ -197,6 +197,29 @@ def test_autotune_keeps_results(tmp_path):
     torch.cuda.synchronize()
 
 
+def test_autotune_warm_cache_reproduces_choices(tmp_path):
+    """A second level of the same boxes, tuned from the first one's cache,
+    ends with the same form (stages per pass, pass kernels, staging) and the
+    same tiles: whole-level timings are cached as well as per-class ones."""
+    import torch
+    inst = W.uneven_level(n=(64, 64, 32), h=1.0 / 32, levels=3, seed=3, box_seed=30)
+    cache = str(tmp_path / "tune.txt")
+
+    def tuned():
+        lev = make_level([inst])
+        lev.set_arith(1)
+        lev.autotune(seed=1, budget_ms=300.0, abort_factor=2.0, cache_path=cache)
+        torch.cuda.synchronize()
+        tiles = [lev.get_tuning(c) for c in range(lev.size_classes()[0])]
+        return (lev.get_fusion(), lev.get_pass_kernel(), lev.get_staging(), tiles)
+
+    first = tuned()
+    lines = open(cache).read().splitlines()
+    assert any("|level" in ln for ln in lines)
+    assert tuned() == first
+    assert sorted(open(cache).read().splitlines()) == sorted(lines)
+
+
 def test_nonfinite_input_is_reported(B):
     import torch
     inst = W.plane_wave(16)
