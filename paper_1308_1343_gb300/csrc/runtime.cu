@@ -171,22 +171,41 @@ void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, 
     at.erase(std::unique(at.begin(), at.end()), at.end());
     for (size_t i = 0; i + 1 < at.size(); ++i) runs_of(at[i], at[i + 1], edge[kind]);
   }
+  // Tile columns: the class's width tx while a whole tile fits, then the
+  // rest of the box's width in narrower tiles of the same thread count
+  // (width halved while it does not fit, down to 8 points; the last one may
+  // be ragged), each tx * ty / w rows tall.  A remainder of 8 points under a
+  // 32-wide tile would otherwise leave three quarters of the tile's threads
+  // idle on every plane: on the 64-box uneven level a third of the tile
+  // planes were ragged so.
+  std::vector<std::pair<int, int>> cols;  // (x0, width)
+  for (int x0 = 0; x0 < nx;) {
+    int w = tx;
+    while (w > 8 && x0 + w > nx) w /= 2;
+    cols.emplace_back(x0, w);
+    x0 += w;
+  }
+  auto emit = [&](int x0, int w, int y0, int z0, int z1) {
+    const int kind = (x0 == 0 && cut_lo && !cut_lo->empty() ? 1 : 0) |
+                     (x0 + w >= nx && cut_hi && !cut_hi->empty() ? 2 : 0);
+    if (!kind) {
+      items.push_back(DItem{b, x0, y0, z0, z1 - z0, w / 2});
+      return;
+    }
+    for (const auto& run : edge[kind])
+      if (run.first >= z0 && run.first < z1)
+        items.push_back(DItem{b, x0, y0, run.first, run.second, w / 2});
+  };
   // run-major order: a column's runs that start inside regular run r go
-  // with run r
+  // with run r; the full-width tiles row by row, then the narrower ones
   for (size_t r = 0; r < reg.size(); ++r) {
     const int z0 = reg[r].first, z1 = z0 + reg[r].second;
     for (int y0 = 0; y0 < ny; y0 += ty)
-      for (int x0 = 0; x0 < nx; x0 += tx) {
-        const int kind = (x0 == 0 && cut_lo && !cut_lo->empty() ? 1 : 0) |
-                         (x0 + tx >= nx && cut_hi && !cut_hi->empty() ? 2 : 0);
-        if (!kind) {
-          items.push_back(DItem{b, x0, y0, z0, z1 - z0, tx / 2});
-          continue;
-        }
-        for (const auto& run : edge[kind])
-          if (run.first >= z0 && run.first < z1)
-            items.push_back(DItem{b, x0, y0, run.first, run.second, tx / 2});
-      }
+      for (const auto& c : cols)
+        if (c.second == tx) emit(c.first, tx, y0, z0, z1);
+    for (const auto& c : cols)
+      if (c.second != tx)
+        for (int y0 = 0; y0 < ny; y0 += ty * tx / c.second) emit(c.first, c.second, y0, z0, z1);
   }
 }
 

@@ -1,9 +1,11 @@
 """Host logic of the work items (sc_level_work_items, no GPU): the items of
-the batched launches tile every box exactly once; a column of tiles at an x
-face whose ghosts the warp-specialised passes read from the box that owns
-them never runs a z-run across a change of that owner (the copies are
-re-derived here from the exchange list and the layout); z-runs keep at most
-tile_z planes; the order is the place of the tile in its domain."""
+the batched launches tile every box exactly once; tiles are the size
+class's width where a whole one fits and narrower ones (same thread count,
+taller) for the rest of a box's width; a column of tiles at an x face whose
+ghosts the warp-specialised passes read from the box that owns them never
+runs a z-run across a change of that owner (the copies are re-derived here
+from the exchange list and the layout); z-runs keep at most tile_z planes;
+the order is the place of the tile in its domain."""
 import numpy as np
 import pytest
 
@@ -63,36 +65,42 @@ def _check(lev, tiles):
     ncls, cls_of = lev.size_classes()
     reads = _owner_reads(lev)
     seen = {}
-    for box, x0, y0, z0, nz_run, tx in items.tolist():
+    cols = {b: set() for b in range(len(boxes))}  # tile columns (x0, y0, width, rows)
+    for box, x0, y0, z0, nz_run, w in items.tolist():
         lo, hi, _ = boxes[box]
         n = [hi[d] - lo[d] for d in range(3)]
         t = lev.get_tuning(cls_of[box])
-        assert tx == t[0] and x0 % tx == 0 and y0 % t[1] == 0
+        # the class's width, or a narrower one (512 threads' worth of points
+        # in a taller tile) only where a tile twice as wide would not fit
+        assert w in (8, 16, 32, 64) and w <= t[0] and x0 % 8 == 0
+        assert w == t[0] or x0 + 2 * w > n[0], (box, x0, w, n[0])
+        rows = t[1] * t[0] // w
+        assert y0 % rows == 0
         assert 0 <= x0 < n[0] and 0 <= y0 < n[1] and 0 <= z0 and z0 + nz_run <= n[2]
         assert 1 <= nz_run <= t[2]
+        cols[box].add((x0, y0, w, rows))
         for z in range(z0, z0 + nz_run):
             key = (box, x0, y0, z)
             assert key not in seen, key
             seen[key] = True
         # no owner change of a read x-face row inside the run
-        for side, at_face in ((0, x0 == 0), (1, x0 + tx >= n[0])):
+        for side, at_face in ((0, x0 == 0), (1, x0 + w >= n[0])):
             if not at_face:
                 continue
             for (ya, yb, za, zb) in reads.get((box, side), []):
                 for zc in (za, zb):
                     assert not (z0 < zc < z0 + nz_run), (box, side, z0, nz_run, zc)
-    # every (box, tile column, plane) exactly once
+    # the tile columns cover every box's (x, y) extent exactly once, each over
+    # all of its planes
     for b, (lo, hi, _) in enumerate(boxes):
         n = [hi[d] - lo[d] for d in range(3)]
-        tx, ty, _ = lev.get_tuning(cls_of[b])
-        for x0 in range(0, n[0], tx):
-            for y0 in range(0, n[1], ty):
-                for z in range(n[2]):
-                    assert (b, x0, y0, z) in seen, (b, x0, y0, z)
-    assert len(seen) == sum(((hi[0] - lo[0] + lev.get_tuning(cls_of[b])[0] - 1)
-                             // lev.get_tuning(cls_of[b])[0]) *
-                            ((hi[1] - lo[1] + lev.get_tuning(cls_of[b])[1] - 1)
-                             // lev.get_tuning(cls_of[b])[1]) * (hi[2] - lo[2])
+        cover = np.zeros((n[1], n[0]), dtype=np.int32)
+        for (x0, y0, w, rows) in cols[b]:
+            cover[y0:y0 + rows, x0:x0 + w] += 1
+            for z in range(n[2]):
+                assert (b, x0, y0, z) in seen, (b, x0, y0, z)
+        assert (cover == 1).all(), b
+    assert len(seen) == sum(len(cols[b]) * (hi[2] - lo[2])
                             for b, (lo, hi, _) in enumerate(boxes))
     # launch order: domain, then z, y, x of the tile's first point
     keys = []
@@ -125,8 +133,12 @@ def test_uneven_levels(tiles):
         if tiles:
             for c in range(lev.size_classes()[0]):
                 lev.set_tuning(c, *tiles)
-        _, reads = _check(lev, tiles)
+        items, reads = _check(lev, tiles)
         assert reads  # the level has x faces read from their owners
+        # extents that are multiples of 8: no tile runs past its box in x
+        for box, x0, _, _, _, w in items.tolist():
+            lo, hi, _ = lev.boxes[box]
+            assert (hi[0] - lo[0]) % 8 or x0 + w <= hi[0] - lo[0]
 
 
 @pytest.mark.parametrize("nranks,method", [(2, 1), (3, 0)])
@@ -160,6 +172,29 @@ def test_single_box_and_ensemble():
     items, reads = _check(lev, None)
     assert not reads
     assert sorted(set(items[:, 0].tolist())) == [0, 1, 2]
+
+
+@pytest.mark.parametrize("nx,tx,want", [
+    (40, 32, [(0, 32), (32, 8)]),
+    (104, 32, [(0, 32), (32, 32), (64, 32), (96, 8)]),
+    (56, 32, [(0, 32), (32, 16), (48, 8)]),
+    (120, 64, [(0, 64), (64, 32), (96, 16), (112, 8)]),
+    (64, 32, [(0, 32), (32, 32)]),
+    (5, 16, [(0, 8)]),
+    (21, 16, [(0, 16), (16, 8)]),
+])
+def test_tile_columns(nx, tx, want):
+    """The tile columns of one box: whole tiles of the class's width, then
+    the narrowest power-of-two widths down to 8 that cover the rest."""
+    inst = W.bumpy_instance(W.Domain((nx, 24, 6), 1.0 / 24), 3)
+    lev = _level(inst)
+    lev.set_tuning(0, tx, 8)
+    items, _ = _check(lev, (tx, 8))
+    got = sorted({(x0, w) for _, x0, _, _, _, w in items.tolist()})
+    assert got == want
+    # rows: 512 threads' worth of points per tile plane
+    for _, x0, y0, _, _, w in items.tolist():
+        assert y0 % (512 // w) == 0
 
 
 def test_work_items_errors():
