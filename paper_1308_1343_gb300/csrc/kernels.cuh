@@ -290,7 +290,7 @@ struct FixedI : Fixed {
 // ---------------------------------------------------------------------------
 
 // Shared memory of one CTA: two (TX+4) x (TY+4) stencil tiles, TX = 2*txh,
-// TY = NT/txh, txh in {4, 8, 16, 32} (the 64 x 8 and 8 x 64 tiles bound the size), and
+// TY = NT/txh, txh in {8, 16, 32} (the 64 x 8 tile bounds the size), and
 // two planes of NF pointwise fields (one 16-byte pair per thread and field).
 template <int NT>
 struct TileSmem {

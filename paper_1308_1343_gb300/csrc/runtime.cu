@@ -177,13 +177,31 @@ void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, 
   // be ragged), each tx * ty / w rows tall.  A remainder of 8 points under a
   // 32-wide tile would otherwise leave three quarters of the tile's threads
   // idle on every plane: on the 64-box uneven level a third of the tile
-  // planes were ragged so.
+  // planes were ragged so.  (An 8 x 64 tile has the 64 x 8 tile's halo
+  // buffer size, the largest the kernels hold.)
   std::vector<std::pair<int, int>> cols;  // (x0, width)
   for (int x0 = 0; x0 < nx;) {
     int w = tx;
     while (w > 8 && x0 + w > nx) w /= 2;
     cols.emplace_back(x0, w);
     x0 += w;
+  }
+  // The last band of rows under the full-width columns, where it is at most
+  // half a tile tall: wider, flatter tiles (height halved while the band
+  // still fits, width doubled up to 64), each as wide as fits in the
+  // columns' extent, down to the class's tile (ragged in y).
+  const int fullRows = ny / ty * ty, band = ny - fullRows;
+  int xm = 0;  // extent of the full-width columns
+  for (const auto& c : cols)
+    if (c.second == tx) xm = c.first + tx;
+  int bh = ty, bw = tx;
+  if (band > 0 && 2 * band <= ty && tx < 64 && xm > 0) {
+    bh = ty / 2;
+    bw = 2 * tx;
+    while (bh / 2 >= band && bw < 64) {
+      bh /= 2;
+      bw *= 2;
+    }
   }
   auto emit = [&](int x0, int w, int y0, int z0, int z1) {
     const int kind = (x0 == 0 && cut_lo && !cut_lo->empty() ? 1 : 0) |
@@ -197,12 +215,21 @@ void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, 
         items.push_back(DItem{b, x0, y0, run.first, run.second, w / 2});
   };
   // run-major order: a column's runs that start inside regular run r go
-  // with run r; the full-width tiles row by row, then the narrower ones
+  // with run r; the full-width tiles row by row, the band, then the
+  // narrower columns
   for (size_t r = 0; r < reg.size(); ++r) {
     const int z0 = reg[r].first, z1 = z0 + reg[r].second;
-    for (int y0 = 0; y0 < ny; y0 += ty)
+    const int yEnd = bw != tx ? fullRows : ny;
+    for (int y0 = 0; y0 < yEnd; y0 += ty)
       for (const auto& c : cols)
         if (c.second == tx) emit(c.first, tx, y0, z0, z1);
+    if (bw != tx)
+      for (int x0 = 0; x0 < xm;) {
+        int w = bw;
+        while (w > tx && x0 + w > xm) w /= 2;
+        emit(x0, w, fullRows, z0, z1);
+        x0 += w;
+      }
     for (const auto& c : cols)
       if (c.second != tx)
         for (int y0 = 0; y0 < ny; y0 += ty * tx / c.second) emit(c.first, c.second, y0, z0, z1);

@@ -70,12 +70,20 @@ def _check(lev, tiles):
         lo, hi, _ = boxes[box]
         n = [hi[d] - lo[d] for d in range(3)]
         t = lev.get_tuning(cls_of[box])
-        # the class's width, or a narrower one (512 threads' worth of points
-        # in a taller tile) only where a tile twice as wide would not fit
-        assert w in (8, 16, 32, 64) and w <= t[0] and x0 % 8 == 0
-        assert w == t[0] or x0 + 2 * w > n[0], (box, x0, w, n[0])
+        # the class's tile (512 threads' worth of points per plane), a
+        # narrower and taller one only where a tile twice as wide would not
+        # fit, a wider and flatter one only over the last band of rows when
+        # that band is at most half a tile tall
+        assert w in (8, 16, 32, 64) and x0 % 8 == 0
         rows = t[1] * t[0] // w
-        assert y0 % rows == 0
+        if w < t[0]:
+            assert x0 + 2 * w > n[0], (box, x0, w, n[0])
+            assert y0 % rows == 0
+        elif w > t[0]:
+            full = n[1] // t[1] * t[1]
+            assert y0 == full and 0 < n[1] - full <= rows < t[1], (box, y0, w, n[1])
+        else:
+            assert y0 % rows == 0
         assert 0 <= x0 < n[0] and 0 <= y0 < n[1] and 0 <= z0 and z0 + nz_run <= n[2]
         assert 1 <= nz_run <= t[2]
         cols[box].add((x0, y0, w, rows))
@@ -186,7 +194,7 @@ def test_single_box_and_ensemble():
 def test_tile_columns(nx, tx, want):
     """The tile columns of one box: whole tiles of the class's width, then
     the narrowest power-of-two widths down to 8 that cover the rest."""
-    inst = W.bumpy_instance(W.Domain((nx, 24, 6), 1.0 / 24), 3)
+    inst = W.bumpy_instance(W.Domain((nx, 64, 6), 1.0 / 64), 3)
     lev = _level(inst)
     lev.set_tuning(0, tx, 8)
     items, _ = _check(lev, (tx, 8))
@@ -195,6 +203,28 @@ def test_tile_columns(nx, tx, want):
     # rows: 512 threads' worth of points per tile plane
     for _, x0, y0, _, _, w in items.tolist():
         assert y0 % (512 // w) == 0
+
+
+@pytest.mark.parametrize("nx,ny,tx,want", [
+    (64, 24, 32, [(0, 0, 32), (0, 16, 64), (32, 0, 32)]),
+    (96, 40, 32, [(0, 0, 32), (0, 16, 32), (0, 32, 64), (32, 0, 32), (32, 16, 32),
+                  (64, 0, 32), (64, 16, 32), (64, 32, 32)]),
+    (40, 24, 32, [(0, 0, 32), (0, 16, 32), (32, 0, 8)]),
+    (48, 36, 16, [(0, 0, 16), (0, 32, 32), (16, 0, 16), (32, 0, 16), (32, 32, 16)]),
+    (128, 36, 16, [(0, 0, 16), (0, 32, 64), (16, 0, 16), (32, 0, 16), (48, 0, 16), (64, 0, 16),
+                   (64, 32, 64), (80, 0, 16), (96, 0, 16), (112, 0, 16)]),
+    (48, 44, 16, [(0, 0, 16), (0, 32, 32), (16, 0, 16), (32, 0, 16), (32, 32, 16)]),
+    (64, 28, 32, [(0, 0, 32), (0, 16, 32), (32, 0, 32), (32, 16, 32)]),
+])
+def test_last_row_band(nx, ny, tx, want):
+    """The last band of rows under the full-width columns, when at most half
+    a tile tall: the flattest tiles that hold it (up to 64 wide), each as
+    wide as fits, down to the class's tile (tile_y = 512 / tile_x)."""
+    inst = W.bumpy_instance(W.Domain((nx, ny, 6), 1.0 / ny), 3)
+    lev = _level(inst)
+    lev.set_tuning(0, tx, 8)
+    items, _ = _check(lev, (tx, 8))
+    assert sorted({(x0, y0, w) for _, x0, y0, _, _, w in items.tolist()}) == want
 
 
 def test_work_items_errors():
