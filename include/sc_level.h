@@ -114,7 +114,9 @@ typedef struct sc_level sc_level;
 /* Kernel configuration of one box-size class (chosen by sc_level_autotune or
  * set explicitly).  tile_x, tile_y: points per CTA tile in x and y
  * (tile_x/2 * tile_y == threads per CTA, see sc_level_set_tuning); tile_z:
- * depth of the z-run one work item marches through. */
+ * depth of the z-run one work item marches through.  Where a box's extent
+ * leaves less than a whole tile, other shapes of the same thread count
+ * cover the rest (see sc_level_work_items). */
 typedef struct sc_tile {
     int32_t tile_x, tile_y, tile_z, reserved;
 } sc_tile;
@@ -243,7 +245,13 @@ int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
  * count (cap = 0 sizes the buffer).  Built on the host from the size
  * classes' current tiles (after sc_level_autotune or sc_level_set_tuning,
  * the tiles the next launch uses), so no device is needed.  Each box is cut
- * into tiles and z-runs of at most tile_z planes; a column of tiles at an x
+ * into tiles and z-runs of at most tile_z planes.  The class's tile covers
+ * the box where a whole one fits; the width left at the box's high x end is
+ * covered by narrower, taller tiles (width halved while it does not fit,
+ * down to 8; only the last may reach past the box), and the last band of
+ * rows under the full-width tiles, when at most half a tile tall, by wider,
+ * flatter ones (up to 64 wide, each as wide as fits, down to the class's
+ * tile); every tile is tile_x x 512 / tile_x points.  A column of tiles at an x
  * face whose ghosts the warp-specialised passes read from the box that owns
  * them splits its z extent first where that owner changes, so that no item
  * reads such a ghost row from two boxes.  The order is by the place of the
