@@ -227,6 +227,32 @@ def test_last_row_band(nx, ny, tx, want):
     assert sorted({(x0, y0, w) for _, x0, y0, _, _, w in items.tolist()}) == want
 
 
+def test_item_shapes_fit_the_kernels():
+    """Every item's tile fits what the traversal kernels hold: a (TX + 4) x
+    (TY + 4) halo tile of at most 816 elements (the 64 x 8 tile's, the size of
+    their shared-memory tile buffers) and at most one halo pair per thread
+    (4 TX/2 + 2 TY <= 256), with TY = 512 / TX."""
+    insts = [W.uneven_level(), W.uneven_level(n=(64, 48, 40), h=1.0 / 48, levels=4, seed=6,
+                                              box_seed=31)]
+    thin = W.bumpy_instance(W.Domain((13, 11, 9), 1.0 / 11), 7)
+    thin.boxes = [((0, 0, 0), (2, 11, 9)), ((2, 0, 0), (5, 11, 9)), ((5, 0, 0), (13, 4, 9)),
+                  ((5, 4, 0), (13, 11, 2)), ((5, 4, 2), (13, 11, 9))]
+    insts.append(thin)
+    levels = [[i] for i in insts] + [W.ensemble(count=12)]
+    for group in levels:
+        from paper_1308_1343_gb300.level import Level
+        lev = Level.from_instances(group)
+        for tiles in (None, (16, 32), (32, 32), (64, 32)):
+            if tiles:
+                for c in range(lev.size_classes()[0]):
+                    lev.set_tuning(c, *tiles)
+            shapes = {int(w) for w in lev.work_items()[:, 5]}
+            for w in shapes:
+                ty = 512 // w
+                assert w in (8, 16, 32, 64)
+                assert (w + 4) * (ty + 4) <= 816 and 4 * (w // 2) + 2 * ty <= 256
+
+
 def test_work_items_errors():
     import ctypes
     from paper_1308_1343_gb300 import binding as B
