@@ -218,7 +218,9 @@ class Level:
 
     def work_items(self) -> np.ndarray:
         """(n, 6) int32 rows of the batched launches' work items in launch
-        order: box, x0, y0, z0, planes of the z-run, tile_x."""
+        order: box, x0, y0, z0, planes of the z-run, tile_x (the item's tile
+        is tile_x x 512 / tile_x points: the size class's tile, or a
+        narrower or flatter one at a box's remainder)."""
         lib = B.lib()
         n = ctypes.c_int64()
         B.check(lib.sc_level_work_items(self._h, None, 0, ctypes.byref(n)))
