@@ -76,6 +76,30 @@ def test_uneven_level_and_thin_boxes(orc, arith):
     assert _same(one, ws)
 
 
+@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_boundary_tile_shapes(orc, arith, mode):
+    """Two boxes whose extents leave remainders under 32 x 16 tiles: a band of
+    64 x 8 tiles under the first box's full tiles and an 8-wide column of
+    8 x 64 tiles at its high x end (whose x-face ghosts come from the second
+    box); both pass kernels bit-identical, the oracle's values within the
+    bar."""
+    dom = W.Domain((104, 40, 20), 1.0 / 40)
+    inst = W.bumpy_instance(dom, 9)
+    inst.boxes = [((0, 0, 0), (72, 40, 20)), ((72, 0, 0), (104, 40, 20))]
+    lev = make_level([inst])
+    ncls = lev.size_classes()[0]
+    for c in range(ncls):
+        lev.set_tuning(c, 32, 8)
+    shapes = {(int(r[0]), int(r[5])) for r in lev.work_items()}
+    assert (0, 64) in shapes and (0, 8) in shapes
+    lev.close()
+    one, ws = _both([inst], 4, arith, mode, tiles={c: (32, 8) for c in range(ncls)})
+    assert _same(one, ws)
+    ou, op = orc.rk4_periodic(inst.u, inst.pi, inst.c2, dom.h, inst.dt, 4)
+    assert rel_err(ws[0][0], ou) <= TOL and rel_err(ws[1][0], op) <= TOL
+
+
 def _owner_change_level():
     """Four boxes of a 64 x 24 x 40 periodic domain: across both x faces of
     box 0 the owner of the ghosts changes along y (box 1 below y = 10) and,
