@@ -248,7 +248,9 @@ int sc_level_size_classes(const sc_level* level, int32_t* nclasses,
  * into tiles and z-runs of at most tile_z planes.  The class's tile covers
  * the box where a whole one fits; the width left at the box's high x end is
  * covered by narrower, taller tiles (width halved while it does not fit,
- * down to 8; only the last may reach past the box), and the last band of
+ * down to 8, only the last reaching past the box; or one tile of the
+ * narrowest width that holds the rest, when that takes fewer tiles over the
+ * box's rows), and the last band of
  * rows under the full-width tiles, when at most half a tile tall, by wider,
  * flatter ones (up to 64 wide, each as wide as fits, down to the class's
  * tile); every tile is tile_x x 512 / tile_x points.  A column of tiles at an x

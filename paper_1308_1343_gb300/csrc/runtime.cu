@@ -172,19 +172,35 @@ void append_box_items(std::vector<DItem>& items, int b, int nx, int ny, int nz, 
     for (size_t i = 0; i + 1 < at.size(); ++i) runs_of(at[i], at[i + 1], edge[kind]);
   }
   // Tile columns: the class's width tx while a whole tile fits, then the
-  // rest of the box's width in narrower tiles of the same thread count
-  // (width halved while it does not fit, down to 8 points; the last one may
-  // be ragged), each tx * ty / w rows tall.  A remainder of 8 points under a
+  // rest of the box's width in narrower tiles of the same thread count,
+  // each tx * ty / w rows tall: either width halved while it does not fit,
+  // down to 8 points (the last one may be ragged), or one tile of the
+  // narrowest width that holds the rest, whichever takes fewer tiles over
+  // the box's rows (the first, on a tie).  A remainder of 8 points under a
   // 32-wide tile would otherwise leave three quarters of the tile's threads
   // idle on every plane: on the 64-box uneven level a third of the tile
   // planes were ragged so.  (An 8 x 64 tile has the 64 x 8 tile's halo
   // buffer size, the largest the kernels hold.)
   std::vector<std::pair<int, int>> cols;  // (x0, width)
-  for (int x0 = 0; x0 < nx;) {
-    int w = tx;
-    while (w > 8 && x0 + w > nx) w /= 2;
-    cols.emplace_back(x0, w);
-    x0 += w;
+  const int xfull = nx / tx * tx;
+  for (int x0 = 0; x0 < xfull; x0 += tx) cols.emplace_back(x0, tx);
+  if (xfull < nx) {
+    auto tiles_over_rows = [&](int w) { return (ny + ty * tx / w - 1) / (ty * tx / w); };
+    std::vector<std::pair<int, int>> halved;
+    int nh = 0;
+    for (int x0 = xfull; x0 < nx;) {
+      int w = tx;
+      while (w > 8 && x0 + w > nx) w /= 2;
+      halved.emplace_back(x0, w);
+      nh += tiles_over_rows(w);
+      x0 += w;
+    }
+    int w1 = 8;
+    while (w1 < nx - xfull) w1 *= 2;
+    if (tiles_over_rows(w1) < nh)
+      cols.emplace_back(xfull, w1);
+    else
+      cols.insert(cols.end(), halved.begin(), halved.end());
   }
   // The last band of rows under the full-width columns, where it is at most
   // half a tile tall: wider, flatter tiles (height halved while the band

@@ -143,10 +143,6 @@ def test_uneven_levels(tiles):
                 lev.set_tuning(c, *tiles)
         items, reads = _check(lev, tiles)
         assert reads  # the level has x faces read from their owners
-        # extents that are multiples of 8: no tile runs past its box in x
-        for box, x0, _, _, _, w in items.tolist():
-            lo, hi, _ = lev.boxes[box]
-            assert (hi[0] - lo[0]) % 8 or x0 + w <= hi[0] - lo[0]
 
 
 @pytest.mark.parametrize("nranks,method", [(2, 1), (3, 0)])
@@ -182,25 +178,33 @@ def test_single_box_and_ensemble():
     assert sorted(set(items[:, 0].tolist())) == [0, 1, 2]
 
 
-@pytest.mark.parametrize("nx,tx,want", [
-    (40, 32, [(0, 32), (32, 8)]),
-    (104, 32, [(0, 32), (32, 32), (64, 32), (96, 8)]),
-    (56, 32, [(0, 32), (32, 16), (48, 8)]),
-    (120, 64, [(0, 64), (64, 32), (96, 16), (112, 8)]),
-    (64, 32, [(0, 32), (32, 32)]),
-    (5, 16, [(0, 8)]),
-    (21, 16, [(0, 16), (16, 8)]),
+@pytest.mark.parametrize("nx,ny,tx,want", [
+    (40, 64, 32, [(0, 32), (32, 8)]),
+    (104, 64, 32, [(0, 32), (32, 32), (64, 32), (96, 8)]),
+    (56, 64, 32, [(0, 32), (32, 16), (48, 8)]),
+    (120, 64, 64, [(0, 64), (64, 32), (96, 16), (112, 8)]),
+    (64, 64, 32, [(0, 32), (32, 32)]),
+    (5, 64, 16, [(0, 8)]),
+    (21, 64, 16, [(0, 16), (16, 8)]),
+    # few rows: one tile of the narrowest width that holds the rest takes
+    # fewer tiles than the halved widths (1 against 2)
+    (56, 16, 32, [(0, 32), (32, 32)]),
+    (24, 16, 32, [(0, 32)]),
+    (88, 8, 64, [(0, 64), (64, 32)]),
+    # a tie keeps the halved widths
+    (56, 32, 32, [(0, 32), (32, 16), (48, 8)]),
 ])
-def test_tile_columns(nx, tx, want):
+def test_tile_columns(nx, ny, tx, want):
     """The tile columns of one box: whole tiles of the class's width, then
-    the narrowest power-of-two widths down to 8 that cover the rest."""
-    inst = W.bumpy_instance(W.Domain((nx, 64, 6), 1.0 / 64), 3)
+    for the rest the halved widths down to 8 or one tile of the narrowest
+    width that holds it, whichever takes fewer tiles over the box's rows."""
+    inst = W.bumpy_instance(W.Domain((nx, ny, 6), 1.0 / ny), 3)
     lev = _level(inst)
     lev.set_tuning(0, tx, 8)
     items, _ = _check(lev, (tx, 8))
     got = sorted({(x0, w) for _, x0, _, _, _, w in items.tolist()})
     assert got == want
-    # rows: 512 threads' worth of points per tile plane
+    # rows: 512 threads' worth of points per tile plane (no short last band here)
     for _, x0, y0, _, _, w in items.tolist():
         assert y0 % (512 // w) == 0
 
