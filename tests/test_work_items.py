@@ -257,6 +257,25 @@ def test_item_shapes_fit_the_kernels():
                 assert (w + 4) * (ty + 4) <= 816 and 4 * (w // 2) + 2 * ty <= 256
 
 
+@pytest.mark.parametrize("tx,floor_unev,floor_ens", [(16, 0.96, 0.93), (32, 0.97, 0.95),
+                                                     (64, 0.97, 0.95)])
+def test_tile_slots_hold_points(tx, floor_unev, floor_ens):
+    """The share of tile slots (512 points per tile plane) that hold points of
+    a box, on the benchmark's 64-box level and 256-cube ensemble: with one
+    ragged tile per remainder it was 0.87 on the level (32-wide tiles); the
+    boundary tile shapes keep it near 0.98."""
+    from paper_1308_1343_gb300.level import Level
+    for insts, floor in (([W.uneven_level()], floor_unev), (W.ensemble(count=256), floor_ens)):
+        lev = Level.from_instances(insts)
+        for c in range(lev.size_classes()[0]):
+            lev.set_tuning(c, tx, 32)
+        items = lev.work_items()
+        slots = 512 * int(items[:, 4].astype(np.int64).sum())
+        pts = sum((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]) for lo, hi, _ in lev.boxes)
+        assert pts / slots >= floor, (tx, pts / slots)
+        lev.close()
+
+
 def test_work_items_errors():
     import ctypes
     from paper_1308_1343_gb300 import binding as B
